@@ -1,0 +1,319 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(quadrature exactness, element invariants, the strong form of Sec. 2, exact reproduction
+of P2/P1 fields, H = h, a brute-force global Newton step, closed-form interface sums,
+discrete mass balance, and the convergence rates of Theorem 5.4 / Table T1)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fe, quad
+from oracle.mesh import Mesh2D, region_breaks
+from oracle.mms import MMS
+from oracle.scheme import TwoGridOracle, Ops, region_whole
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ quadrature
+def _monomial_exact(a, b):
+    return math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+
+
+def test_triangle_rule_degree5_exact_and_not_degree6():
+    P, Wq = quad.triangle_rule7()
+    assert abs(Wq.sum() - 0.5) < 1e-15
+    for a in range(6):
+        for b in range(6 - a):
+            v = np.sum(Wq * P[:, 0] ** a * P[:, 1] ** b)
+            assert abs(v - _monomial_exact(a, b)) < 1e-15
+    worst = max(abs(np.sum(Wq * P[:, 0] ** a * P[:, 1] ** (6 - a)) - _monomial_exact(a, 6 - a))
+                for a in range(7))
+    assert worst > 1e-6          # a degree-5 rule must miss some degree-6 monomial
+
+
+def test_duffy_rule_agrees():
+    P, Wq = quad.duffy_rule(4, 4)
+    for a in range(6):
+        for b in range(6 - a):
+            assert abs(np.sum(Wq * P[:, 0] ** a * P[:, 1] ** b) - _monomial_exact(a, b)) < 1e-15
+
+
+# ------------------------------------------------------------------ elements
+def _rand_tris(n=5, seed=1):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, size=(n, 3, 2))
+    det = (X[:, 1, 0] - X[:, 0, 0]) * (X[:, 2, 1] - X[:, 0, 1]) - (X[:, 2, 0] - X[:, 0, 0]) * (X[:, 1, 1] - X[:, 0, 1])
+    X[det < 0] = X[det < 0][:, [0, 2, 1]]
+    return X
+
+
+def test_p2_basis_nodal_and_partition_of_unity():
+    nodes = np.array([[0, 0], [1, 0], [0, 1], [0.5, 0], [0.5, 0.5], [0, 0.5]], dtype=float)
+    N, dN = fe.p2_basis(nodes)
+    assert np.allclose(N, np.eye(6), atol=1e-15)
+    N, dN = fe.p2_basis(fe.QP)
+    assert np.allclose(N.sum(1), 1) and np.allclose(dN.sum(1), 0)
+
+
+def test_element_invariants():
+    X = _rand_tris()
+    det, Jinv, xq, Wt = fe.geometry(X)
+    G = fe.grads(Jinv, fe.DPHI)
+    M = fe.mass_p2(Wt)
+    K = fe.stiff_p2(Wt, G)
+    assert np.allclose(M.sum((1, 2)), 0.5 * np.abs(det), rtol=1e-14)
+    assert np.allclose(K.sum(2), 0, atol=1e-12)
+    assert np.allclose(K, np.swapaxes(K, 1, 2), atol=1e-13)
+    prm = W.Params(nu=0.7, eta=1.3)
+    rng = np.random.default_rng(3)
+    w = rng.normal(size=(len(X), 6, 2))
+    wq, Gw = fe.at_qp(w), fe.grad_at_qp(G, w)
+    Kvv, Kvp, Kpv = fe.oseen_blocks(Wt, G, None, wq, Gw, 1e30, prm)
+    xn = np.concatenate([X, 0.5 * (X[:, [0, 1, 2]] + X[:, [1, 2, 0]])], axis=1)
+    # rigid motion r(x) = (a - c y, b + c x): no viscous energy; the convection part
+    # b_N(r, w) + b_N(w, r) is not zero, so test the viscous part alone with w = 0
+    Kvv0, _, _ = fe.oseen_blocks(Wt, G, None, 0 * wq, 0 * Gw, 1e30, prm)
+    r = np.stack([0.3 - 1.7 * xn[..., 1], -0.2 + 1.7 * xn[..., 0]], axis=-1)
+    assert np.abs(np.einsum("eiajb,ejb->eia", Kvv0, r)).max() < 1e-12
+    # b_N(w, const, v) = 0: convection of a constant field by w vanishes
+    const = np.broadcast_to(np.array([0.4, -1.1]), (len(X), 6, 2))
+    # (e.grad)w term is not zero for a constant e, remove it by using w = 0 gradient
+    Kc, _, _ = fe.oseen_blocks(Wt, G, None, wq, 0 * Gw, 1e30, prm)
+    assert np.abs(np.einsum("eiajb,ejb->eia", Kc - Kvv0, const)).max() < 1e-12
+    # pressure rows: eta (q, div u) for u = (x, 2y): div u = 3 -> 3 eta |K|/3 per vertex
+    u = np.stack([xn[..., 0], 2 * xn[..., 1]], axis=-1)
+    got = np.einsum("ekjb,ejb->ek", Kpv, u)
+    assert np.allclose(got, prm.eta * 3 * (0.5 * np.abs(det))[:, None] / 3, rtol=1e-13)
+    # velocity-pressure block is minus the transpose of the pressure rows
+    assert np.allclose(Kvp, -np.transpose(Kpv, (0, 2, 3, 1)), atol=1e-14)
+
+
+# ------------------------------------------------------------------ manufactured data
+@pytest.mark.parametrize("mms_id", [1, 3])
+def test_mms_forcing_matches_strong_form_by_finite_differences(mms_id):
+    prm = W.Params(nu=0.7, rho=1.3, mu=1.1, alpha=0.9, sigma=0.8, sigma_star=1.2,
+                   phiC=(0.5, 0.7, 0.9), k=(1.5, 0.6, 0.25))
+    m = MMS(mms_id, prm)
+    rng = np.random.default_rng(5)
+    x, y, t = rng.uniform(0.1, 0.9), rng.uniform(1.1, 1.9), 0.3
+    h = 1e-4
+
+    def d(fn, var, *args):
+        if var == "x":
+            return (fn(x + h, y, t) - fn(x - h, y, t)) / (2 * h)
+        if var == "y":
+            return (fn(x, y + h, t) - fn(x, y - h, t)) / (2 * h)
+        return (fn(x, y, t + h) - fn(x, y, t - h)) / (2 * h)
+
+    def lap(fn):
+        return ((fn(x + h, y, t) - 2 * fn(x, y, t) + fn(x - h, y, t)) +
+                (fn(x, y + h, t) - 2 * fn(x, y, t) + fn(x, y - h, t))) / h ** 2
+    u = lambda a: (lambda X_, Y_, T_: m.u(X_, Y_, T_)[..., a])
+    divu = lambda X_, Y_, T_: (m.u(X_ + h, Y_, T_)[..., 0] - m.u(X_ - h, Y_, T_)[..., 0]) / (2 * h) + \
+        (m.u(X_, Y_ + h, T_)[..., 1] - m.u(X_, Y_ - h, T_)[..., 1]) / (2 * h)
+    uu = m.u(x, y, t)
+    for a, var in enumerate("xy"):
+        conv = uu[0] * d(u(a), "x") + uu[1] * d(u(a), "y")
+        expect = d(u(a), "t") - prm.nu * (lap(u(a)) + d(divu, var)) + d(m.p, var) + conv
+        assert abs(m.f(x, y, t)[a] - expect) < 2e-5 * max(1, abs(expect))
+    yp = y - 1.0
+    pd = [lambda X_, Y_, T_, i=i: m.pd(i, X_, Y_, T_) for i in range(3)]
+    kF, kf, km = prm.k
+    cFf, cfm = prm.sigma_star * kf / prm.mu, prm.sigma * km / prm.mu
+    y = yp
+    P = [m.pd(i, x, y, t) for i in range(3)]
+    ex = [prm.phiC[0] * d(pd[0], "t") - kF / prm.mu * lap(pd[0]) + cFf * (P[0] - P[1]),
+          prm.phiC[1] * d(pd[1], "t") - kf / prm.mu * lap(pd[1]) + cFf * (P[1] - P[0]) + cfm * (P[1] - P[2]),
+          prm.phiC[2] * d(pd[2], "t") - km / prm.mu * lap(pd[2]) + cfm * (P[2] - P[1])]
+    for i in range(3):
+        assert abs(m.q(i, x, y, t) - ex[i]) < 2e-5 * max(1, abs(ex[i]))
+
+
+def test_interface_defects_closed_form():
+    json.load(open(os.path.join(GOLD, "interface_closed_forms.json")))
+    m = MMS(1, W.Params())
+    x = np.linspace(0, 1, 9)
+    t = 0.37
+    e = math.exp(-t)
+    assert np.allclose(m.gN(x, t), (-(2 * np.pi + 1) + 3) * np.cos(np.pi * x) * e, atol=1e-14)
+    assert np.allclose(m.gT(x, t), (1 - 3 * np.pi) * np.sin(np.pi * x) * e, atol=1e-13)
+    assert np.allclose(m.gd(0, x, t), 0, atol=1e-14)
+
+
+# ------------------------------------------------------------------ meshes
+def test_mesh_counts_and_nesting():
+    w = W.config_small()
+    b = region_breaks(w)
+    mc = Mesh2D(b["xs_h"], b["c"]["ys_h"])
+    mp = Mesh2D(b["xs_h"], b["p"]["ys_h"])
+    assert 2 * mc.nn + mc.nv == 2467 and 3 * mp.nn == 3267
+    assert set(b["xs_H"]).issubset(set(b["xs_h"]))
+    assert set(b["c"]["ys_H"]).issubset(set(b["c"]["ys_h"]))
+    # edge nodes are midpoints, edges sorted lexicographically
+    assert (np.diff(mc.edges[:, 0]) >= 0).all()
+    for m in (mc, mp):
+        t6 = m.tri6
+        assert np.allclose(m.node[t6[:, 3]], 0.5 * (m.node[t6[:, 0]] + m.node[t6[:, 1]]))
+        X = m.tri_coords()
+        det, *_ = fe.geometry(X)
+        assert (det > 0).all()
+    g = W.config_graded()
+    bg = region_breaks(g)
+    assert len(bg["c"]["ys_h"]) == 49 and abs(bg["c"]["ys_h"][1] - 1 - 1 / 128) < 1e-15
+    assert abs(bg["p"]["ys_h"][1] - 1 / 32) < 1e-15
+
+
+# ------------------------------------------------------------------ exact reproduction
+@pytest.mark.parametrize("graded", [False, True])
+def test_patch_field_reproduced_exactly(graded):
+    """A steady field with P2 velocity, P1 pressure and P2 Darcy pressures is reproduced
+    by Algorithm 3 at every step (backward Euler and all lagging are exact for it)."""
+    w = W.config_patch(nx_coarse=2, r=2, nsub=(2, 2), nsteps=3)
+    if graded:
+        w.nx_coarse, w.ny_coarse, w.fine_per_coarse_x = 4, 4, 2
+        w.fine_rows_from_gamma = [4, 2, 1, 1]
+    o = TwoGridOracle(w)
+    o.run(3)
+    ex = o.exact_fine()
+    for k in o.fine:
+        assert np.abs(o.fine[k] - ex[k]).max() < 1e-11, k
+
+
+def test_H_equals_h_gives_zero_correction():
+    w = W.config_uniform(4, 1, nsub=(2, 2), overlap=1, nsteps=2)
+    o = TwoGridOracle(w)
+    o.run(2)
+    assert max(np.abs(e).max() for e in o.ec) < 1e-12
+    assert max(np.abs(e).max() for e in o.ep) < 1e-12
+    assert max(np.abs(d).max() for d in o.dc) < 1e-11
+
+
+# ------------------------------------------------------------------ brute force
+def test_single_subdomain_equals_global_newton_step():
+    """With one subdomain per region, u_H + e is one Newton step of the global fine
+    backward-Euler problem about the coarse solution (coarse Gamma data).  The Jacobian
+    is formed by central differences of the residual (exact for a quadratic residual) and
+    the step solved densely with numpy.linalg.solve."""
+    w = W.config_uniform(2, 2, nsub=(1, 1), overlap=1, nsteps=1, dt=0.05)
+    o = TwoGridOracle(w)
+    prev = dict(o.fine)
+    uH0, pdH0 = o.uH.copy(), o.pdH.copy()
+    o.step()
+    t = o.dt
+    m = o.mms
+    R = region_whole(o.mch, "c")
+    O = Ops(R, o.prm, o.dt)
+    nn = o.mch.nn
+    un = np.stack([prev["ux"], prev["uy"]], axis=1)
+    pF = np.zeros(nn)
+    pF[o.gam_c_h] = (o.Pp2 @ pdH0[0])[o.gam_p_h]
+    # linearisation point: the fine interpolant of the new coarse solution
+    x0 = np.concatenate([np.stack([o.Pc2 @ o.uH[:, a] for a in range(2)], 1).ravel(), o.Pc1 @ o.pH])
+    d = o._region_dirichlet(o.mch, "c")
+    ub = m.u(o.mch.node[d, 0], o.mch.node[d, 1], t)
+    fixed = np.concatenate([2 * d, 2 * d + 1])
+    dB = np.concatenate([ub[:, 0], ub[:, 1]]) - x0[fixed]      # boundary step to the fine data
+    free = np.setdiff1d(np.arange(O.ntot), fixed)
+
+    def F(x):
+        return O.ns_residual(x[:2 * nn].reshape(nn, 2), un, x[2 * nn:], t, m, pF)
+    J = np.zeros((O.ntot, O.ntot))
+    hstep = 1e-3
+    for k in range(O.ntot):
+        xp, xm = x0.copy(), x0.copy()
+        xp[k] += hstep
+        xm[k] -= hstep
+        J[:, k] = (F(xp) - F(xm)) / (2 * hstep)
+    x = x0.copy()
+    x[fixed] += dB
+    x[free] += np.linalg.solve(J[np.ix_(free, free)], -F(x0)[free] - J[np.ix_(free, fixed)] @ dB)
+    u_bf = x[:2 * nn].reshape(nn, 2)
+    assert np.abs(u_bf[:, 0] - o.fine["ux"]).max() < 1e-10
+    assert np.abs(u_bf[:, 1] - o.fine["uy"]).max() < 1e-10
+    assert np.abs(x[2 * nn:] - o.fine["p"]).max() < 1e-9
+    # Darcy: the fine backward-Euler step with partners lagged at the fine state
+    Rp = region_whole(o.mph, "p")
+    Op = Ops(Rp, o.prm, o.dt)
+    Mf = Op.mass_matrix().toarray()
+    pn = np.stack([prev["pF"], prev["pf"], prev["pm"]])
+    prm = o.prm
+    kF, kf, km = prm.k
+    cFf, cfm = prm.sigma_star * kf / prm.mu, prm.sigma * km / prm.mu
+    partners = {0: [(cFf, 1)], 1: [(cfm, 2), (cFf, 0)], 2: [(cfm, 1)]}
+    ucn = np.zeros(o.mph.nn)
+    ucn[o.gam_p_h] = -(o.Pc2 @ uH0[:, 1])[o.gam_c_h]
+    dp = o._region_dirichlet(o.mph, "p")
+    freep = np.setdiff1d(np.arange(o.mph.nn), dp)
+    for i, key in enumerate(("pF", "pf", "pm")):
+        A = Op.darcy_matrix(i).toarray()
+        b = Op.darcy_load(m.q(i, Rp.xq[..., 0], Rp.xq[..., 1], t)) + prm.phiC[i] / o.dt * Mf @ pn[i]
+        for c, k in partners[i]:
+            b += c * Mf @ pn[k]
+        if i == 0:
+            b += Op.gamma_vec(Rp.gamma_load(Rp.gamma_trace_qp(ucn)))
+        b -= Op.gamma_vec(Rp.gamma_load(m.gd(i, Rp.exq, t)))
+        x = np.zeros(o.mph.nn)
+        x[dp] = m.pd(i, o.mph.node[dp, 0], o.mph.node[dp, 1], t)
+        x[freep] = np.linalg.solve(A[np.ix_(freep, freep)], b[freep] - A[np.ix_(freep, dp)] @ x[dp])
+        assert np.abs(x - o.fine[key]).max() < 1e-11, key
+
+
+# ------------------------------------------------------------------ closed-form interface sums
+def test_gamma_loads_closed_forms():
+    w = W.config_uniform(2, 4, nsub=(1, 1))
+    o = TwoGridOracle(w)
+    R = region_whole(o.mph, "p")
+    O = Ops(R, o.prm, o.dt)
+    xs = o.mph.node[:, 0]
+    # sum over all P2 basis functions of <g, v> is int_Gamma g (partition of unity)
+    g = 1 + xs + xs ** 2                                      # a P2 trace on Gamma
+    v = O.gamma_vec(R.gamma_load(R.gamma_trace_qp(g)))
+    assert abs(v.sum() - (1 + 0.5 + 1 / 3)) < 1e-14
+    # BJS coupling: sum over tangential components of <d_tau p, v.tau> = p(1,1) - p(0,1)
+    Rc = region_whole(o.mch, "c")
+    pFg = np.zeros(o.mch.nn)
+    xc = o.mch.node[:, 0]
+    pFg[:] = np.cos(1.3 * xc) * 0 + xc ** 2 - 0.7 * xc
+    dv = Rc.gamma_load(Rc.gamma_dtau_qp(pFg))
+    assert abs(dv.sum() - ((1 - 0.7) - 0.0)) < 1e-14
+    # normal traction: sum of <p_F, v.n_c> over v_y = -int p_F
+    tv = Rc.gamma_load(Rc.gamma_trace_qp(pFg))
+    assert abs(tv.sum() - (1 / 3 - 0.35)) < 1e-14
+
+
+# ------------------------------------------------------------------ discrete mass balance
+def test_local_discrete_divergence():
+    w = W.config_small(nsteps=2)
+    o = TwoGridOracle(w)
+    o.run(1)
+    uH1 = np.stack([o.Pc2 @ o.uH[:, a] for a in range(2)], 1)
+    for (s, O), e in zip(o.sub_c, o.ec):
+        utot = (uH1[s.gnode] + e)[O.R.tri6]
+        wq = fe.at_qp(utot)
+        _, _, Kpv = fe.oseen_blocks(O.R.W, O.R.G, None, wq, fe.grad_at_qp(O.R.G, utot), o.dt, o.prm)
+        div = np.zeros(len(s.vloc))
+        np.add.at(div, O.R.tri3, np.einsum("ekjb,ejb->ek", Kpv, utot))
+        test = ~s.art[s.vloc]                   # pressure tests of Q_0^h(Omega_j)
+        assert np.abs(div[test]).max() < 1e-12
+
+
+# ------------------------------------------------------------------ convergence rates
+@pytest.mark.slow
+def test_convergence_rates_theorem_5_4():
+    """Rates of Algorithm 3 with h = H^2 and the paper's overlap of 1/4 (Example 1
+    layout), small dt so that the time error stays below the spatial error."""
+    gold = json.load(open(os.path.join(GOLD, "paper_rates.json")))
+    res = []
+    for H, r in [(4, 4), (8, 8)]:
+        w = W.config_uniform(H, r, nsub=(2, 2), overlap=(H * r) // 4, nsteps=2, dt=1e-4)
+        o = TwoGridOracle(w)
+        o.run(2)
+        res.append(o.errors())
+    rate = lambda k: math.log(res[0][k] / res[1][k]) / math.log(4)
+    assert rate("u_H1") >= gold["min_velocity_H1_rate"]
+    for k in ("pF_L2", "pf_L2", "pm_L2"):
+        assert rate(k) >= gold["min_darcy_L2_rate"]
