@@ -1,0 +1,985 @@
+// Context and C ABI of the GB300 library (declared in tpns.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.hpp"
+#include "setup.hpp"
+#include "tpns.h"
+
+using namespace tpns;
+
+struct tpns_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  tpns_precision prec = TPNS_FP64;
+  double dt = 0;
+  Phys phys{};
+  Layout L;
+  RefTables ref{};
+  std::string err;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // problems: fluid locals [0,nf), CF = nf, porous locals [nf+1, nf+1+np), CP = nf+1+np
+  int nf = 0, np = 0, nprob = 0;
+  std::vector<const Problem*> probs;
+  std::vector<ProbDev> hprob;
+  std::vector<int64_t> e_off, n_off, v_off, x_off;
+  std::vector<int> sys_first;             // first system of a problem
+  int64_t ne_tot = 0, nn_tot = 0, nv_tot = 0;
+  int64_t ne_osl = 0, ne_cf = 0, eD0 = 0, ne_dl = 0, ne_cp = 0;   // element ranges
+  int64_t nn_fl = 0, nn_cf = 0, nn_pl = 0, nn_cp = 0;              // node ranges (begins below)
+  int64_t nb_fl = 0, nb_cf = 0, nb_pl = 0, nb_cp = 0;
+  // systems
+  std::vector<SysDev> hsys;
+  std::vector<int> hchol;
+  int nsys = 0;
+  std::vector<int> list_osl, list_cf, list_dl, list_cp, list_local;
+  int kl_max_osl = 0, n_max_local = 0, kl_max_cf = 0, n_max_cf = 0, n_max_cp = 0;
+  int64_t band_local_len = 0, band_coarse_len = 0, nnz_tot = 0, vals_tot = 0, xvec_tot = 0;
+  double lu_flops_step = 0;
+  // device
+  ProbDev* d_probs = nullptr;
+  int32_t *d_eprob = nullptr, *d_e6 = nullptr, *d_e3 = nullptr;
+  int8_t* d_egam = nullptr;
+  double* d_geo = nullptr;
+  int32_t *d_gnode = nullptr, *d_gam_src = nullptr, *d_node_dof = nullptr, *d_nprob = nullptr, *d_nvidx = nullptr;
+  int8_t* d_nkind = nullptr;
+  int32_t *d_vloc = nullptr, *d_vert_dof = nullptr;
+  double* d_ref = nullptr;
+  SysDev* d_sys = nullptr;
+  int* d_chol = nullptr;
+  int32_t *d_rowptr = nullptr, *d_colidx = nullptr, *d_rowof = nullptr;
+  double* d_vals = nullptr;
+  double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_rel = nullptr, *d_relprev = nullptr;
+  int *d_done = nullptr, *d_iters = nullptr, *d_status = nullptr;
+  void* d_band_local = nullptr;
+  double* d_band_coarse = nullptr;
+  int *d_list_osl = nullptr, *d_list_cf = nullptr, *d_list_dl = nullptr, *d_list_cp = nullptr,
+      *d_list_local = nullptr;
+  double *d_Ke = nullptr, *d_Re = nullptr, *d_ReD = nullptr;
+  int32_t *d_mo_t = nullptr, *d_mo_s = nullptr, *d_ro_t = nullptr, *d_ro_s = nullptr;
+  int32_t *d_rd_t = nullptr, *d_rd_s = nullptr;
+  int32_t *d_mcf_t = nullptr, *d_mcf_s = nullptr, *d_rcf_t = nullptr, *d_rcf_s = nullptr;
+  int32_t *d_rcp_t = nullptr, *d_rcp_s = nullptr;
+  int64_t n_mo = 0, n_ro = 0, n_rd = 0, n_mcf = 0, n_rcf = 0, n_rcp = 0;
+  double *d_uc_old = nullptr, *d_uc_new = nullptr, *d_pc_new = nullptr, *d_pd_old = nullptr,
+         *d_pd_new = nullptr, *d_zero = nullptr, *d_delta = nullptr;
+  double *d_FW1 = nullptr, *d_FW0 = nullptr, *d_FP1 = nullptr, *d_FPD1 = nullptr, *d_FPD0 = nullptr;
+  double *d_out_u = nullptr, *d_out_p = nullptr, *d_out_pd = nullptr;
+  int32_t *d_pc2i = nullptr, *d_pc1i = nullptr, *d_pp2i = nullptr;
+  double *d_pc2w = nullptr, *d_pc1w = nullptr, *d_pp2w = nullptr;
+  int32_t *d_gc_ptr = nullptr, *d_gc_prob = nullptr, *d_gc_node = nullptr;
+  int32_t *d_gp_ptr = nullptr, *d_gp_prob = nullptr, *d_gp_node = nullptr;
+  int32_t *d_gv_ptr = nullptr, *d_gv_prob = nullptr, *d_gv_vert = nullptr;
+  double *d_gc_w = nullptr, *d_gp_w = nullptr, *d_gv_w = nullptr;
+  double* d_tnow = nullptr;
+  int64_t* d_step = nullptr;
+  int *d_newton_done = nullptr, *d_newton_iters = nullptr;
+  // coarse trajectory for tpns_local_step
+  std::vector<double*> traj;          // per stored step: uc, pc, pd (concatenated)
+  int64_t traj_len = 0;
+  int traj_base = 0;                  // step index of traj[0]
+  int64_t step = 0;
+  tpns_stats stats{};
+  AsmArgs asmargs{};
+  GlueArgs glue{};
+};
+
+static thread_local std::string g_err;
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);               \
+      return TPNS_EDEVICE;                                                         \
+    }                                                                              \
+  } while (0)
+
+template <typename T>
+static tpns_status dalloc(tpns_ctx* ctx, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess) {
+    ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return TPNS_ENOMEM;
+  }
+  ctx->allocs.push_back(q);
+  ctx->bytes += n * sizeof(T);
+  *p = reinterpret_cast<T*>(q);
+  return TPNS_OK;
+}
+
+template <typename T>
+static tpns_status upload(tpns_ctx* ctx, T** p, const std::vector<T>& v) {
+  tpns_status s = dalloc(ctx, p, v.size());
+  if (s != TPNS_OK) return s;
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return TPNS_OK;
+}
+
+#define TRY(x)                      \
+  do {                              \
+    tpns_status s_ = (x);           \
+    if (s_ != TPNS_OK) return s_;   \
+  } while (0)
+
+// ------------------------------------------------------------------------------ host data
+static void mms_u_host(const Phys& P, double x, double y, double t, double* u) {
+  if (P.mms == 1) {
+    const double pi = 3.141592653589793;
+    double E = std::exp(-t);
+    u[0] = std::sin(pi * x) * std::cos(pi * y) * E;
+    u[1] = -std::cos(pi * x) * std::sin(pi * y) * E;
+  } else if (P.mms == 3) {
+    u[0] = x * x;
+    u[1] = -2.0 * x * y;
+  } else {
+    u[0] = u[1] = 0.0;
+  }
+}
+static double mms_p_host(const Phys& P, double x, double y, double t) {
+  const double pi = 3.141592653589793;
+  if (P.mms == 1) return std::cos(pi * x) * std::cos(pi * y) * std::exp(-t);
+  if (P.mms == 3) return x + y;
+  return 0.0;
+}
+static double mms_pd_host(const Phys& P, int f, double x, double y, double t) {
+  const double pi = 3.141592653589793;
+  const double a = 3.0 - f;
+  if (P.mms == 1) return a * std::cos(pi * x) * std::cos(pi * y) * std::exp(-t);
+  if (P.mms == 3) return a * (x * x + y * y);
+  return 0.0;
+}
+
+static std::vector<int32_t> inverse_map(const std::vector<int32_t>& g, int n) {
+  std::vector<int32_t> inv(n, -1);
+  for (size_t l = 0; l < g.size(); ++l) inv[g[l]] = (int32_t)l;
+  return inv;
+}
+
+// ------------------------------------------------------------------------------ create
+static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns_partition_desc& pd,
+                             size_t budget) {
+  Layout& L = ctx->L;
+  std::string msg = build_layout(md, pd, L);
+  if (!msg.empty()) {
+    ctx->err = msg;
+    return TPNS_EINVAL;
+  }
+  build_ref_tables(ctx->ref);
+  ctx->nf = (int)L.fluid.size();
+  ctx->np = (int)L.porous.size();
+  ctx->probs.clear();
+  for (auto& P : L.fluid) ctx->probs.push_back(&P);
+  ctx->probs.push_back(&L.cfl);
+  for (auto& P : L.porous) ctx->probs.push_back(&P);
+  ctx->probs.push_back(&L.cpo);
+  ctx->nprob = (int)ctx->probs.size();
+  const int CF = ctx->nf, CP = ctx->nf + 1 + ctx->np;
+  // offsets
+  int64_t e = 0, n = 0, v = 0;
+  ctx->e_off.resize(ctx->nprob);
+  ctx->n_off.resize(ctx->nprob);
+  ctx->v_off.resize(ctx->nprob);
+  for (int p = 0; p < ctx->nprob; ++p) {
+    ctx->e_off[p] = e; ctx->n_off[p] = n; ctx->v_off[p] = v;
+    e += ctx->probs[p]->ne; n += ctx->probs[p]->nn; v += ctx->probs[p]->nvl;
+  }
+  ctx->ne_tot = e; ctx->nn_tot = n; ctx->nv_tot = v;
+  ctx->ne_osl = ctx->e_off[CF];
+  ctx->ne_cf = ctx->probs[CF]->ne;
+  ctx->eD0 = ctx->e_off[CF + 1 < ctx->nprob ? CF + 1 : CF];
+  ctx->ne_dl = ctx->e_off[CP] - ctx->eD0;
+  ctx->ne_cp = ctx->probs[CP]->ne;
+  ctx->nb_fl = 0; ctx->nn_fl = ctx->n_off[CF];
+  ctx->nb_cf = ctx->n_off[CF]; ctx->nn_cf = ctx->probs[CF]->nn;
+  ctx->nb_pl = ctx->n_off[CF] + ctx->nn_cf; ctx->nn_pl = ctx->n_off[CP] - ctx->nb_pl;
+  ctx->nb_cp = ctx->n_off[CP]; ctx->nn_cp = ctx->probs[CP]->nn;
+  // systems
+  ctx->hsys.clear(); ctx->hchol.clear(); ctx->sys_first.assign(ctx->nprob, 0);
+  ctx->x_off.assign(ctx->nprob, 0);
+  int64_t rp = 0, nz = 0, vals = 0, xo = 0, bl = 0, bc = 0;
+  std::vector<int32_t> h_rowptr, h_colidx, h_rowof;
+  ctx->lu_flops_step = 0;
+  for (int p = 0; p < ctx->nprob; ++p) {
+    const Problem& P = *ctx->probs[p];
+    const bool coarse = P.coarse;
+    ctx->sys_first[p] = (int)ctx->hsys.size();
+    ctx->x_off[p] = xo;
+    const int nfld = P.kind == PK_OSEEN ? 1 : 3;
+    h_rowptr.insert(h_rowptr.end(), P.rowptr.begin(), P.rowptr.end());
+    h_colidx.insert(h_colidx.end(), P.colidx.begin(), P.colidx.end());
+    h_rowof.insert(h_rowof.end(), P.rowof.begin(), P.rowof.end());
+    for (int f = 0; f < nfld; ++f) {
+      SysDev S{};
+      S.n = P.n; S.kl = P.kl; S.ku = P.kind == PK_OSEEN ? P.ku : 0;
+      S.ldab = P.kind == PK_OSEEN ? P.kl + P.ku + 1 : P.kl + 1;
+      S.rp_off = rp; S.nnz_off = nz; S.nnz = (int64_t)P.colidx.size();
+      S.val_off = vals; vals += S.nnz;
+      S.x_off = xo; xo += P.n;
+      int64_t blen = (int64_t)S.n * S.ldab;
+      if (coarse) { S.band_off = bc; bc += blen; } else { S.band_off = bl; bl += blen; }
+      S.dinv_off = 0;
+      ctx->hsys.push_back(S);
+      ctx->hchol.push_back(P.kind == PK_DARCY ? 1 : 0);
+    }
+    rp += P.n + 1; nz += (int64_t)P.colidx.size();
+    if (P.kind == PK_OSEEN && !coarse) ctx->lu_flops_step += P.lu_flops;
+  }
+  ctx->nsys = (int)ctx->hsys.size();
+  ctx->nnz_tot = nz; ctx->vals_tot = vals; ctx->xvec_tot = xo;
+  ctx->band_local_len = bl; ctx->band_coarse_len = bc;
+  ctx->list_osl.clear(); ctx->list_dl.clear(); ctx->list_local.clear();
+  for (int p = 0; p < ctx->nf; ++p) ctx->list_osl.push_back(ctx->sys_first[p]);
+  ctx->list_cf = {ctx->sys_first[CF]};
+  for (int p = CF + 1; p < CP; ++p)
+    for (int f = 0; f < 3; ++f) ctx->list_dl.push_back(ctx->sys_first[p] + f);
+  ctx->list_cp = {ctx->sys_first[CP], ctx->sys_first[CP] + 1, ctx->sys_first[CP] + 2};
+  ctx->list_local = ctx->list_osl;
+  ctx->list_local.insert(ctx->list_local.end(), ctx->list_dl.begin(), ctx->list_dl.end());
+  for (int s : ctx->list_osl) ctx->kl_max_osl = std::max(ctx->kl_max_osl, ctx->hsys[s].kl);
+  for (int s : ctx->list_local) ctx->n_max_local = std::max(ctx->n_max_local, ctx->hsys[s].n);
+  ctx->kl_max_cf = ctx->hsys[ctx->list_cf[0]].kl;
+  ctx->n_max_cf = ctx->hsys[ctx->list_cf[0]].n;
+  for (int s : ctx->list_cp) ctx->n_max_cp = std::max(ctx->n_max_cp, ctx->hsys[s].n);
+  // footprint check before any allocation
+  const size_t Tsz = ctx->prec == TPNS_FP64 ? 8 : 4;
+  size_t est = (size_t)ctx->band_local_len * Tsz + (size_t)ctx->band_coarse_len * 8 +
+               (size_t)(ctx->ne_osl + ctx->ne_cf) * (225 + 15) * 8 + (size_t)ctx->vals_tot * 8 +
+               (size_t)ctx->nnz_tot * 8 + (size_t)ctx->xvec_tot * 3 * 8 + (size_t)ctx->ne_tot * 11 * 8;
+  if (budget > 0 && est > budget) {
+    ctx->err = "device footprint " + std::to_string(est) + " B exceeds the budget";
+    return TPNS_EBUDGET;
+  }
+  // element arrays
+  std::vector<int32_t> h_eprob(ctx->ne_tot), h_e6((size_t)ctx->ne_tot * 6), h_e3((size_t)ctx->ne_tot * 3);
+  std::vector<int8_t> h_egam(ctx->ne_tot);
+  std::vector<double> h_geo((size_t)ctx->ne_tot * 11);
+  std::vector<int32_t> h_gnode(ctx->nn_tot), h_gam(ctx->nn_tot), h_ndof((size_t)ctx->nn_tot * 2, -1),
+      h_nprob(ctx->nn_tot), h_nvidx(ctx->nn_tot);
+  std::vector<int8_t> h_nkind(ctx->nn_tot);
+  std::vector<int32_t> h_vloc(ctx->nv_tot), h_vdof(ctx->nv_tot, -1);
+  // inverse maps of the coarse problems: coarse mesh node -> local node
+  std::vector<int32_t> inv_cp = inverse_map(L.cpo.gnode, L.mpH.nn);
+  for (int p = 0; p < ctx->nprob; ++p) {
+    const Problem& P = *ctx->probs[p];
+    const Mesh& m = P.region == 0 ? (P.coarse ? L.mcH : L.mch) : (P.coarse ? L.mpH : L.mph);
+    for (int el = 0; el < P.ne; ++el) {
+      int64_t ge = ctx->e_off[p] + el;
+      h_eprob[ge] = p;
+      for (int k = 0; k < 6; ++k) h_e6[ge * 6 + k] = P.e6[6 * el + k];
+      for (int k = 0; k < 3; ++k) h_e3[ge * 3 + k] = P.e3[3 * el + k];
+      h_egam[ge] = P.egam[el];
+      const int32_t* tv = &m.tri[3 * (size_t)P.etri[el]];
+      double x0 = m.node[2 * tv[0]], y0 = m.node[2 * tv[0] + 1];
+      double x1 = m.node[2 * tv[1]], y1 = m.node[2 * tv[1] + 1];
+      double x2 = m.node[2 * tv[2]], y2 = m.node[2 * tv[2] + 1];
+      double J00 = x1 - x0, J01 = x2 - x0, J10 = y1 - y0, J11 = y2 - y0;
+      double det = J00 * J11 - J01 * J10;
+      double* g = &h_geo[ge * 11];
+      g[0] = x0; g[1] = y0; g[2] = x1; g[3] = y1; g[4] = x2; g[5] = y2;
+      g[6] = J11 / det; g[7] = -J01 / det; g[8] = -J10 / det; g[9] = J00 / det;
+      g[10] = std::fabs(det);
+    }
+    for (int l = 0; l < P.nn; ++l) {
+      int64_t gn = ctx->n_off[p] + l;
+      h_gnode[gn] = P.gnode[l];
+      h_nkind[gn] = P.nkind[l];
+      int32_t gs = P.gam_src.empty() ? -1 : P.gam_src[l];
+      // the coarse porous state is kept in the coarse Darcy problem's local node order
+      if (p == CF && gs >= 0) gs = inv_cp[gs];
+      h_gam[gn] = gs;
+      h_nprob[gn] = p;
+      h_nvidx[gn] = P.vidx[l];
+      if (P.kind == PK_OSEEN) {
+        h_ndof[2 * gn] = P.node_dof[2 * l];
+        h_ndof[2 * gn + 1] = P.node_dof[2 * l + 1];
+      } else {
+        h_ndof[2 * gn] = P.node_dof[l];
+      }
+    }
+    for (int vv = 0; vv < P.nvl; ++vv) {
+      h_vloc[ctx->v_off[p] + vv] = P.vloc[vv];
+      if (P.kind == PK_OSEEN) h_vdof[ctx->v_off[p] + vv] = P.vert_dof[vv];
+    }
+  }
+  TRY(upload(ctx, &ctx->d_eprob, h_eprob));
+  TRY(upload(ctx, &ctx->d_e6, h_e6));
+  TRY(upload(ctx, &ctx->d_e3, h_e3));
+  TRY(upload(ctx, &ctx->d_egam, h_egam));
+  TRY(upload(ctx, &ctx->d_geo, h_geo));
+  TRY(upload(ctx, &ctx->d_gnode, h_gnode));
+  TRY(upload(ctx, &ctx->d_nkind, h_nkind));
+  TRY(upload(ctx, &ctx->d_gam_src, h_gam));
+  TRY(upload(ctx, &ctx->d_node_dof, h_ndof));
+  TRY(upload(ctx, &ctx->d_nprob, h_nprob));
+  TRY(upload(ctx, &ctx->d_nvidx, h_nvidx));
+  TRY(upload(ctx, &ctx->d_vloc, h_vloc));
+  TRY(upload(ctx, &ctx->d_vert_dof, h_vdof));
+  std::vector<double> h_ref(sizeof(RefTables) / sizeof(double));
+  std::memcpy(h_ref.data(), &ctx->ref, sizeof(RefTables));
+  TRY(upload(ctx, &ctx->d_ref, h_ref));
+  TRY(upload(ctx, &ctx->d_rowptr, h_rowptr));
+  TRY(upload(ctx, &ctx->d_colidx, h_colidx));
+  TRY(upload(ctx, &ctx->d_rowof, h_rowof));
+  TRY(upload(ctx, &ctx->d_sys, ctx->hsys));
+  TRY(upload(ctx, &ctx->d_chol, ctx->hchol));
+  TRY(upload(ctx, &ctx->d_list_osl, ctx->list_osl));
+  TRY(upload(ctx, &ctx->d_list_cf, ctx->list_cf));
+  TRY(upload(ctx, &ctx->d_list_dl, ctx->list_dl));
+  TRY(upload(ctx, &ctx->d_list_cp, ctx->list_cp));
+  TRY(upload(ctx, &ctx->d_list_local, ctx->list_local));
+  TRY(dalloc(ctx, &ctx->d_vals, ctx->vals_tot));
+  TRY(dalloc(ctx, &ctx->d_b, ctx->xvec_tot));
+  TRY(dalloc(ctx, &ctx->d_x, ctx->xvec_tot));
+  TRY(dalloc(ctx, &ctx->d_r, ctx->xvec_tot));
+  TRY(dalloc(ctx, &ctx->d_rel, ctx->nsys));
+  TRY(dalloc(ctx, &ctx->d_relprev, ctx->nsys));
+  TRY(dalloc(ctx, &ctx->d_done, ctx->nsys));
+  TRY(dalloc(ctx, &ctx->d_iters, ctx->nsys));
+  TRY(dalloc(ctx, &ctx->d_status, ctx->nsys));
+  CK(cudaMemset(ctx->d_status, 0, ctx->nsys * sizeof(int)));
+  if (ctx->prec == TPNS_FP64) {
+    double* b;
+    TRY(dalloc(ctx, &b, ctx->band_local_len));
+    ctx->d_band_local = b;
+  } else {
+    float* b;
+    TRY(dalloc(ctx, &b, ctx->band_local_len));
+    ctx->d_band_local = b;
+  }
+  TRY(dalloc(ctx, &ctx->d_band_coarse, ctx->band_coarse_len));
+  TRY(dalloc(ctx, &ctx->d_Ke, (size_t)(ctx->ne_osl + ctx->ne_cf) * 225));
+  TRY(dalloc(ctx, &ctx->d_Re, (size_t)(ctx->ne_osl + ctx->ne_cf) * 15));
+  TRY(dalloc(ctx, &ctx->d_ReD, (size_t)(ctx->ne_dl + ctx->ne_cp) * 18));
+  // scatter maps with global offsets
+  auto build_map = [&](int p, bool matrix, std::vector<int32_t>& T_, std::vector<int32_t>& S_) {
+    const Problem& P = *ctx->probs[p];
+    const std::vector<int32_t>& tg = matrix ? P.mtgt : P.rtgt;
+    const std::vector<int32_t>& sr = matrix ? P.msrc : P.rsrc;
+    if (P.kind == PK_OSEEN) {
+      const SysDev& S = ctx->hsys[ctx->sys_first[p]];
+      for (size_t k = 0; k < tg.size(); ++k) {
+        if (tg[k] < 0) { T_.push_back(-1); S_.push_back(0); continue; }
+        T_.push_back((int32_t)((matrix ? S.val_off : S.x_off) + tg[k]));
+        S_.push_back((int32_t)(ctx->e_off[p] * (matrix ? 225 : 15) + sr[k]));
+      }
+    } else {
+      const int64_t ebase = ctx->e_off[p] - (P.coarse ? ctx->e_off[p] : ctx->eD0);
+      for (int f = 0; f < 3; ++f) {
+        const SysDev& S = ctx->hsys[ctx->sys_first[p] + f];
+        const int per = matrix ? 36 : 6;
+        for (size_t k = 0; k < tg.size(); ++k) {
+          if (tg[k] < 0) { T_.push_back(-1); S_.push_back(0); continue; }
+          int el = sr[k] / per, rem = sr[k] % per;
+          T_.push_back((int32_t)((matrix ? S.val_off : S.x_off) + tg[k]));
+          S_.push_back((int32_t)(((ebase + el) * 3 + f) * per + rem));
+        }
+      }
+    }
+  };
+  {
+    std::vector<int32_t> t1, s1, t2, s2, t3, s3;
+    for (int p = 0; p < ctx->nf; ++p) { build_map(p, true, t1, s1); build_map(p, false, t2, s2); }
+    for (int p = CF + 1; p < CP; ++p) build_map(p, false, t3, s3);
+    ctx->n_mo = (int64_t)t1.size(); ctx->n_ro = (int64_t)t2.size(); ctx->n_rd = (int64_t)t3.size();
+    TRY(upload(ctx, &ctx->d_mo_t, t1)); TRY(upload(ctx, &ctx->d_mo_s, s1));
+    TRY(upload(ctx, &ctx->d_ro_t, t2)); TRY(upload(ctx, &ctx->d_ro_s, s2));
+    TRY(upload(ctx, &ctx->d_rd_t, t3)); TRY(upload(ctx, &ctx->d_rd_s, s3));
+    std::vector<int32_t> a1, b1, a2, b2, a3, b3;
+    build_map(CF, true, a1, b1);
+    build_map(CF, false, a2, b2);
+    build_map(CP, false, a3, b3);
+    ctx->n_mcf = (int64_t)a1.size(); ctx->n_rcf = (int64_t)a2.size(); ctx->n_rcp = (int64_t)a3.size();
+    TRY(upload(ctx, &ctx->d_mcf_t, a1)); TRY(upload(ctx, &ctx->d_mcf_s, b1));
+    TRY(upload(ctx, &ctx->d_rcf_t, a2)); TRY(upload(ctx, &ctx->d_rcf_s, b2));
+    TRY(upload(ctx, &ctx->d_rcp_t, a3)); TRY(upload(ctx, &ctx->d_rcp_s, b3));
+  }
+  // fields
+  const int nncH = L.mcH.nn, nvcH = L.mcH.nv, nnpH = L.mpH.nn;
+  const int nnc = L.mch.nn, nvc = L.mch.nv, nnp = L.mph.nn;
+  TRY(dalloc(ctx, &ctx->d_uc_old, (size_t)nncH * 2));
+  TRY(dalloc(ctx, &ctx->d_uc_new, (size_t)nncH * 2));
+  TRY(dalloc(ctx, &ctx->d_pc_new, (size_t)nvcH));
+  TRY(dalloc(ctx, &ctx->d_pd_old, (size_t)nnpH * 3));
+  TRY(dalloc(ctx, &ctx->d_pd_new, (size_t)nnpH * 3));
+  size_t zlen = std::max<size_t>((size_t)nnpH * 3, (size_t)(2 * L.cfl.nn + L.cfl.nvl));
+  TRY(dalloc(ctx, &ctx->d_zero, zlen));
+  CK(cudaMemset(ctx->d_zero, 0, zlen * sizeof(double)));
+  TRY(dalloc(ctx, &ctx->d_delta, (size_t)(2 * L.cfl.nn + L.cfl.nvl)));
+  TRY(dalloc(ctx, &ctx->d_FW1, (size_t)nnc * 2));
+  TRY(dalloc(ctx, &ctx->d_FW0, (size_t)nnc * 2));
+  TRY(dalloc(ctx, &ctx->d_FP1, (size_t)nvc));
+  TRY(dalloc(ctx, &ctx->d_FPD1, (size_t)nnp * 3));
+  TRY(dalloc(ctx, &ctx->d_FPD0, (size_t)nnp * 3));
+  TRY(dalloc(ctx, &ctx->d_out_u, (size_t)nnc * 2));
+  TRY(dalloc(ctx, &ctx->d_out_p, (size_t)nvc));
+  TRY(dalloc(ctx, &ctx->d_out_pd, (size_t)nnp * 3));
+  // prolongation tables; the porous coarse index is remapped to the coarse Darcy local order
+  std::vector<int32_t> pp2 = L.pp2_idx;
+  for (auto& c : pp2) c = inv_cp[c];
+  TRY(upload(ctx, &ctx->d_pc2i, L.pc2_idx)); TRY(upload(ctx, &ctx->d_pc2w, L.pc2_w));
+  TRY(upload(ctx, &ctx->d_pc1i, L.pc1_idx)); TRY(upload(ctx, &ctx->d_pc1w, L.pc1_w));
+  TRY(upload(ctx, &ctx->d_pp2i, pp2)); TRY(upload(ctx, &ctx->d_pp2w, L.pp2_w));
+  // glue tables: problem indices of porous locals are shifted in the descriptor array
+  std::vector<int32_t> gp_prob = L.gp_prob;
+  TRY(upload(ctx, &ctx->d_gc_ptr, L.gc_ptr)); TRY(upload(ctx, &ctx->d_gc_prob, L.gc_prob));
+  TRY(upload(ctx, &ctx->d_gc_node, L.gc_node)); TRY(upload(ctx, &ctx->d_gc_w, L.gc_w));
+  TRY(upload(ctx, &ctx->d_gp_ptr, L.gp_ptr)); TRY(upload(ctx, &ctx->d_gp_prob, gp_prob));
+  TRY(upload(ctx, &ctx->d_gp_node, L.gp_node)); TRY(upload(ctx, &ctx->d_gp_w, L.gp_w));
+  TRY(upload(ctx, &ctx->d_gv_ptr, L.gv_ptr)); TRY(upload(ctx, &ctx->d_gv_prob, L.gv_prob));
+  TRY(upload(ctx, &ctx->d_gv_vert, L.gv_vert)); TRY(upload(ctx, &ctx->d_gv_w, L.gv_w));
+  TRY(dalloc(ctx, &ctx->d_tnow, 1));
+  TRY(dalloc(ctx, &ctx->d_step, 1));
+  TRY(dalloc(ctx, &ctx->d_newton_done, 1));
+  TRY(dalloc(ctx, &ctx->d_newton_iters, 1));
+  // local correction state
+  std::vector<double*> state(ctx->nprob, nullptr);
+  for (int p = 0; p < ctx->nprob; ++p) {
+    const Problem& P = *ctx->probs[p];
+    if (p == CF || p == CP) continue;
+    size_t len = P.kind == PK_OSEEN ? (size_t)(2 * P.nn + P.nvl) : (size_t)3 * P.nn;
+    TRY(dalloc(ctx, &state[p], len));
+  }
+  // descriptors
+  ctx->hprob.assign(ctx->nprob, ProbDev{});
+  for (int p = 0; p < ctx->nprob; ++p) {
+    const Problem& P = *ctx->probs[p];
+    ProbDev& D = ctx->hprob[p];
+    D.kind = P.kind; D.coarse = P.coarse; D.ne = P.ne; D.nn = P.nn; D.nvl = P.nvl; D.n = P.n;
+    D.e_off = ctx->e_off[p]; D.n_off = ctx->n_off[p]; D.v_off = ctx->v_off[p];
+    D.x_off = ctx->hsys[ctx->sys_first[p]].x_off;
+    D.fstride = 0;
+    if (P.kind == PK_OSEEN && !P.coarse) {
+      D.W1 = ctx->d_FW1; D.W0 = ctx->d_FW0; D.P1 = ctx->d_FP1; D.GAM = ctx->d_FPD0;
+      D.EN = state[p]; D.EOUT = state[p]; D.XY = nullptr;
+    } else if (P.kind == PK_OSEEN) {
+      D.W1 = ctx->d_uc_new; D.W0 = ctx->d_uc_old; D.P1 = ctx->d_pc_new; D.GAM = ctx->d_pd_old;
+      D.EN = ctx->d_zero; D.EOUT = ctx->d_delta;
+    } else if (!P.coarse) {
+      D.W1 = ctx->d_FPD1; D.W0 = ctx->d_FPD0; D.P1 = nullptr; D.GAM = ctx->d_FW0;
+      D.EN = state[p]; D.EOUT = state[p]; D.fstride = nnp;
+    } else {
+      D.W1 = ctx->d_zero; D.W0 = ctx->d_zero; D.P1 = nullptr; D.GAM = ctx->d_uc_old;
+      D.EN = ctx->d_pd_new; D.EOUT = ctx->d_pd_new; D.fstride = 0;
+    }
+  }
+  // node coordinates of the region meshes
+  double *xy_ch, *xy_cH, *xy_ph, *xy_pH;
+  TRY(upload(ctx, &xy_ch, L.mch.node)); TRY(upload(ctx, &xy_cH, L.mcH.node));
+  TRY(upload(ctx, &xy_ph, L.mph.node)); TRY(upload(ctx, &xy_pH, L.mpH.node));
+  for (int p = 0; p < ctx->nprob; ++p) {
+    const Problem& P = *ctx->probs[p];
+    ctx->hprob[p].XY = P.region == 0 ? (P.coarse ? xy_cH : xy_ch) : (P.coarse ? xy_pH : xy_ph);
+  }
+  TRY(upload(ctx, &ctx->d_probs, ctx->hprob));
+  // initial data: coarse interpolants and e^0 = I_h u0 - I_h I_H u0 (0 on the artificial boundary)
+  const Phys& Ph = ctx->phys;
+  std::vector<double> uc((size_t)nncH * 2), pc(nvcH), pdl((size_t)nnpH * 3);
+  for (int i = 0; i < nncH; ++i) mms_u_host(Ph, L.mcH.node[2 * i], L.mcH.node[2 * i + 1], 0.0, &uc[2 * i]);
+  for (int i = 0; i < nvcH; ++i) pc[i] = mms_p_host(Ph, L.mcH.node[2 * i], L.mcH.node[2 * i + 1], 0.0);
+  for (int l = 0; l < nnpH; ++l) {
+    int g = L.cpo.gnode[l];
+    for (int f = 0; f < 3; ++f) pdl[(size_t)f * nnpH + l] = mms_pd_host(Ph, f, L.mpH.node[2 * g], L.mpH.node[2 * g + 1], 0.0);
+  }
+  CK(cudaMemcpy(ctx->d_uc_old, uc.data(), uc.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_uc_new, uc.data(), uc.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_pc_new, pc.data(), pc.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_pd_old, pdl.data(), pdl.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_pd_new, pdl.data(), pdl.size() * 8, cudaMemcpyHostToDevice));
+  // fine interpolants of the coarse initial data (host, same tables as the device)
+  std::vector<double> Iuh((size_t)nnc * 2, 0.0), Ipdh((size_t)nnp * 3, 0.0);
+  for (int i = 0; i < nnc; ++i)
+    for (int k = 0; k < 6; ++k) {
+      int c = L.pc2_idx[(size_t)i * 6 + k];
+      double w = L.pc2_w[(size_t)i * 6 + k];
+      Iuh[2 * i] += w * uc[2 * c];
+      Iuh[2 * i + 1] += w * uc[2 * c + 1];
+    }
+  for (int i = 0; i < nnp; ++i)
+    for (int k = 0; k < 6; ++k) {
+      int c = pp2[(size_t)i * 6 + k];
+      double w = L.pp2_w[(size_t)i * 6 + k];
+      for (int f = 0; f < 3; ++f) Ipdh[(size_t)f * nnp + i] += w * pdl[(size_t)f * nnpH + c];
+    }
+  for (int p = 0; p < ctx->nprob; ++p) {
+    if (p == CF || p == CP) continue;
+    const Problem& P = *ctx->probs[p];
+    std::vector<double> e0;
+    if (P.kind == PK_OSEEN) {
+      e0.assign((size_t)2 * P.nn + P.nvl, 0.0);
+      for (int l = 0; l < P.nn; ++l) {
+        if (P.nkind[l] == 2) continue;
+        int g = P.gnode[l];
+        double u[2];
+        mms_u_host(Ph, L.mch.node[2 * g], L.mch.node[2 * g + 1], 0.0, u);
+        e0[2 * l] = u[0] - Iuh[2 * g];
+        e0[2 * l + 1] = u[1] - Iuh[2 * g + 1];
+      }
+    } else {
+      e0.assign((size_t)3 * P.nn, 0.0);
+      for (int l = 0; l < P.nn; ++l) {
+        if (P.nkind[l] == 2) continue;
+        int g = P.gnode[l];
+        for (int f = 0; f < 3; ++f)
+          e0[(size_t)f * P.nn + l] = mms_pd_host(Ph, f, L.mph.node[2 * g], L.mph.node[2 * g + 1], 0.0) - Ipdh[(size_t)f * nnp + g];
+      }
+    }
+    CK(cudaMemcpy(state[p], e0.data(), e0.size() * 8, cudaMemcpyHostToDevice));
+  }
+  int64_t zero64 = 0;
+  CK(cudaMemcpy(ctx->d_step, &zero64, 8, cudaMemcpyHostToDevice));
+  // assembly / glue argument blocks
+  AsmArgs& A = ctx->asmargs;
+  A.probs = ctx->d_probs; A.eprob = ctx->d_eprob; A.geo = ctx->d_geo; A.e6 = ctx->d_e6; A.e3 = ctx->d_e3;
+  A.egam = ctx->d_egam; A.gnode = ctx->d_gnode; A.nkind = ctx->d_nkind; A.gam_src = ctx->d_gam_src;
+  A.node_dof = ctx->d_node_dof; A.vloc = ctx->d_vloc; A.vert_dof = ctx->d_vert_dof; A.ref = ctx->d_ref;
+  A.phys = ctx->phys; A.tnow = ctx->d_tnow;
+  GlueArgs& G = ctx->glue;
+  G.fluid = ctx->d_probs;
+  G.porous = ctx->d_probs + (ctx->nf + 1);
+  G.gc_ptr = ctx->d_gc_ptr; G.gc_prob = ctx->d_gc_prob; G.gc_node = ctx->d_gc_node; G.gc_w = ctx->d_gc_w;
+  G.gp_ptr = ctx->d_gp_ptr; G.gp_prob = ctx->d_gp_prob; G.gp_node = ctx->d_gp_node; G.gp_w = ctx->d_gp_w;
+  G.gv_ptr = ctx->d_gv_ptr; G.gv_prob = ctx->d_gv_prob; G.gv_vert = ctx->d_gv_vert; G.gv_w = ctx->d_gv_w;
+  G.FW1 = ctx->d_FW1; G.FP1 = ctx->d_FP1; G.FPD1 = ctx->d_FPD1;
+  G.out_u = ctx->d_out_u; G.out_p = ctx->d_out_p; G.out_pd = ctx->d_out_pd;
+  G.nnc = nnc; G.nvc = nvc; G.nnp = nnp;
+  return TPNS_OK;
+}
+
+// ------------------------------------------------------------------------------ step
+static tpns_status prolong_and_glue(tpns_ctx* ctx) {
+  const Layout& L = ctx->L;
+  cudaStream_t st = ctx->stream;
+  CK(launch_prolong(L.mch.nn, L.mch.nv, L.mph.nn, ctx->d_pc2i, ctx->d_pc2w, ctx->d_pc1i, ctx->d_pc1w, ctx->d_pp2i,
+                    ctx->d_pp2w, ctx->d_uc_new, ctx->d_uc_old, ctx->d_pc_new, ctx->d_pd_new, ctx->d_pd_old, L.mpH.nn,
+                    ctx->d_FW1, ctx->d_FW0, ctx->d_FP1, ctx->d_FPD1, ctx->d_FPD0, L.mph.nn, st));
+  return TPNS_OK;
+}
+
+static tpns_status coarse_step(tpns_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const int CF = ctx->nf, CP = ctx->nf + 1 + ctx->np;
+  const Layout& L = ctx->L;
+  // Step 1(1): coarse Darcy solves (eqs. pFFully, pfFully, pmFully), Cholesky factors fixed
+  CK(cudaMemcpyAsync(ctx->d_pd_new, ctx->d_pd_old, (size_t)L.mpH.nn * 3 * 8, cudaMemcpyDeviceToDevice, st));
+  double* ReCP = ctx->d_ReD + ctx->ne_dl * 18;
+  CK(launch_darcy_elem(ctx->asmargs, ctx->e_off[CP], ctx->ne_cp, ReCP, nullptr, st));
+  CK(launch_seg_reduce(ctx->d_rcp_t, ctx->d_rcp_s, ctx->n_rcp, ReCP, ctx->d_b, st, nullptr));
+  CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cp, ctx->d_chol, 3, ctx->n_max_cp, ctx->d_band_coarse, ctx->d_b,
+                               ctx->d_x, 0, nullptr, st, nullptr));
+  CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cp, ctx->nn_cp, ctx->d_x, st, nullptr));
+  // Step 1(2): coarse conduit problem (eq. pcFully) by Newton's method
+  CK(cudaMemcpyAsync(ctx->d_uc_new, ctx->d_uc_old, (size_t)L.mcH.nn * 2 * 8, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(ctx->d_newton_done, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_newton_iters, 0, sizeof(int), st));
+  const int* skip = ctx->d_newton_done;
+  for (int it = 0; it < 12; ++it) {
+    CK(launch_oseen_elem(ctx->asmargs, ctx->e_off[CF], ctx->ne_cf, ctx->d_Ke, ctx->d_Re, st, skip));
+    CK(launch_seg_reduce(ctx->d_mcf_t, ctx->d_mcf_s, ctx->n_mcf, ctx->d_Ke, ctx->d_vals, st, skip));
+    CK(launch_seg_reduce(ctx->d_rcf_t, ctx->d_rcf_s, ctx->n_rcf, ctx->d_Re, ctx->d_b, st, skip));
+    CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
+                                ctx->d_band_coarse, 0, 0, st, skip));
+    CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse, nullptr,
+                              ctx->d_status, st, skip));
+    CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cf, ctx->d_chol, 1, ctx->n_max_cf, ctx->d_band_coarse,
+                                 ctx->d_b, ctx->d_x, 0, nullptr, st, skip));
+    CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cf, ctx->nn_cf, ctx->d_x, st, skip));
+    CK(launch_newton_update(ctx->d_probs + CF, ctx->d_gnode, ctx->d_vloc, L.cfl.nn, L.cfl.nvl, ctx->d_uc_new,
+                            ctx->d_pc_new, ctx->d_newton_done, ctx->d_newton_iters, st));
+  }
+  return TPNS_OK;
+}
+
+template <typename T>
+static tpns_status local_step(tpns_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  T* band = reinterpret_cast<T*>(ctx->d_band_local);
+  const int nosl = (int)ctx->list_osl.size(), nloc = (int)ctx->list_local.size();
+  // a1: coarse fields on the fine meshes
+  TRY(prolong_and_glue(ctx));
+  // a2-a3: Oseen matrices and right-hand sides of all conduit subdomains
+  CK(launch_oseen_elem(ctx->asmargs, 0, ctx->ne_osl, ctx->d_Ke, ctx->d_Re, st, nullptr));
+  CK(launch_seg_reduce(ctx->d_mo_t, ctx->d_mo_s, ctx->n_mo, ctx->d_Ke, ctx->d_vals, st, nullptr));
+  CK(launch_seg_reduce(ctx->d_ro_t, ctx->d_ro_s, ctx->n_ro, ctx->d_Re, ctx->d_b, st, nullptr));
+  // a4: Darcy right-hand sides of all porous subdomains
+  CK(launch_darcy_elem(ctx->asmargs, ctx->eD0, ctx->ne_dl, ctx->d_ReD, nullptr, st));
+  CK(launch_seg_reduce(ctx->d_rd_t, ctx->d_rd_s, ctx->n_rd, ctx->d_ReD, ctx->d_b, st, nullptr));
+  // a6: band LU of every Oseen system
+  CK(launch_band_fill<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 0, 0, st,
+                         nullptr));
+  CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, nullptr, ctx->d_status, st, nullptr));
+  // a8: solves with FP64-residual iterative refinement
+  const bool fp64 = ctx->prec == TPNS_FP64;
+  const int maxit = fp64 ? 2 : 12;
+  const double tol = fp64 ? 1e-14 : 1e-13;
+  CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
+                     ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, tol, 1, st, nullptr));
+  CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, ctx->d_chol, nloc, ctx->n_max_local, band, ctx->d_b, ctx->d_x,
+                          0, nullptr, st, nullptr));
+  for (int it = 0; it < maxit; ++it) {
+    CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
+                       ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, tol, 0, st, nullptr));
+    if (it + 1 < maxit)
+      CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, ctx->d_chol, nloc, ctx->n_max_local, band, ctx->d_r,
+                              ctx->d_x, 1, ctx->d_done, st, nullptr));
+  }
+  // a9: new corrections and glue
+  CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_fl, ctx->nn_fl, ctx->d_x, st, nullptr));
+  CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_pl, ctx->nn_pl, ctx->d_x, st, nullptr));
+  CK(launch_glue(ctx->glue, st));
+  return TPNS_OK;
+}
+
+static tpns_status end_step(tpns_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const Layout& L = ctx->L;
+  CK(cudaMemcpyAsync(ctx->d_uc_old, ctx->d_uc_new, (size_t)L.mcH.nn * 2 * 8, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_pd_old, ctx->d_pd_new, (size_t)L.mpH.nn * 3 * 8, cudaMemcpyDeviceToDevice, st));
+  CK(launch_set_time(ctx->d_tnow, ctx->d_step, ctx->dt, 1, st));
+  ctx->step += 1;
+  return TPNS_OK;
+}
+
+static tpns_status read_stats(tpns_ctx* ctx) {
+  std::vector<int> it(ctx->nsys), stt(ctx->nsys);
+  std::vector<double> rel(ctx->nsys);
+  int nit = 0;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(it.data(), ctx->d_iters, ctx->nsys * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(rel.data(), ctx->d_rel, ctx->nsys * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(stt.data(), ctx->d_status, ctx->nsys * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&nit, ctx->d_newton_iters, sizeof(int), cudaMemcpyDeviceToHost));
+  int mx = 0;
+  double mr = 0;
+  for (int s : ctx->list_local) {
+    mx = std::max(mx, it[s]);
+    mr = std::max(mr, rel[s]);
+  }
+  ctx->stats.step = ctx->step;
+  ctx->stats.last_ir_iters_max = mx;
+  ctx->stats.last_ir_relres_max = mr;
+  ctx->stats.last_newton_iters = nit;
+  for (int s = 0; s < ctx->nsys; ++s)
+    if (stt[s]) {
+      ctx->err = "zero or non-finite pivot in system " + std::to_string(s);
+      return TPNS_EBREAKDOWN;
+    }
+  if (!(mr <= 1e-9)) {
+    ctx->err = "iterative refinement stopped at relative residual " + std::to_string(mr);
+    return TPNS_ENOTCONV;
+  }
+  return TPNS_OK;
+}
+
+static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
+  for (int s = 0; s < nsteps; ++s) {
+    if (from_traj) {
+      int64_t k = ctx->step - ctx->traj_base;
+      if (k < 0 || k + 1 >= (int64_t)ctx->traj.size()) {
+        ctx->err = "no stored coarse state for this step";
+        return TPNS_EINVAL;
+      }
+      const Layout& L = ctx->L;
+      size_t nu = (size_t)L.mcH.nn * 2, npc = L.mcH.nv, npd = (size_t)L.mpH.nn * 3;
+      cudaStream_t st = ctx->stream;
+      CK(cudaMemcpyAsync(ctx->d_uc_old, ctx->traj[k], nu * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ctx->d_pd_old, ctx->traj[k] + nu + npc, npd * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ctx->d_uc_new, ctx->traj[k + 1], nu * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ctx->d_pc_new, ctx->traj[k + 1] + nu, npc * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ctx->d_pd_new, ctx->traj[k + 1] + nu + npc, npd * 8, cudaMemcpyDeviceToDevice, st));
+    } else {
+      TRY(coarse_step(ctx));
+    }
+    if (ctx->prec == TPNS_FP64) TRY(local_step<double>(ctx));
+    else TRY(local_step<float>(ctx));
+    TRY(end_step(ctx));
+  }
+  return read_stats(ctx);
+}
+
+static tpns_status setup_factors(tpns_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const int CP = ctx->nf + 1 + ctx->np;
+  // Darcy element matrices (run once) -> CSR values -> band Cholesky
+  const int64_t neD = ctx->ne_dl + ctx->ne_cp;
+  double* KeD = nullptr;
+  TRY(dalloc(ctx, &KeD, (size_t)neD * 108));
+  std::vector<int32_t> t1, s1, t2, s2;
+  for (int p = ctx->nf + 1; p <= CP; ++p) {
+    const Problem& P = *ctx->probs[p];
+    const int64_t ebase = ctx->e_off[p] - ctx->eD0;
+    for (int f = 0; f < 3; ++f) {
+      const SysDev& S = ctx->hsys[ctx->sys_first[p] + f];
+      for (size_t k = 0; k < P.mtgt.size(); ++k) {
+        if (P.mtgt[k] < 0) { t1.push_back(-1); s1.push_back(0); continue; }
+        int el = P.msrc[k] / 36, rem = P.msrc[k] % 36;
+        t1.push_back((int32_t)(S.val_off + P.mtgt[k]));
+        s1.push_back((int32_t)(((ebase + el) * 3 + f) * 36 + rem));
+      }
+    }
+  }
+  int32_t *dt1, *ds1;
+  TRY(upload(ctx, &dt1, t1));
+  TRY(upload(ctx, &ds1, s1));
+  CK(launch_set_time(ctx->d_tnow, ctx->d_step, ctx->dt, 0, st));
+  CK(launch_darcy_elem(ctx->asmargs, ctx->eD0, neD, nullptr, KeD, st));
+  CK(launch_seg_reduce(dt1, ds1, (int64_t)t1.size(), KeD, ctx->d_vals, st, nullptr));
+  const int ndl = (int)ctx->list_dl.size();
+  if (ctx->prec == TPNS_FP64) {
+    double* band = reinterpret_cast<double*>(ctx->d_band_local);
+    CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_dl, ndl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 1, 0,
+                                st, nullptr));
+    CK(launch_band_chol<double>(ctx->d_sys, ctx->d_list_dl, ndl, band, ctx->d_status, st));
+  } else {
+    float* band = reinterpret_cast<float*>(ctx->d_band_local);
+    CK(launch_band_fill<float>(ctx->d_sys, ctx->d_list_dl, ndl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 1, 0,
+                               st, nullptr));
+    CK(launch_band_chol<float>(ctx->d_sys, ctx->d_list_dl, ndl, band, ctx->d_status, st));
+  }
+  CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
+                              ctx->d_band_coarse, 1, 0, st, nullptr));
+  CK(launch_band_chol<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->d_band_coarse, ctx->d_status, st));
+  // initial glued fields
+  TRY(prolong_and_glue(ctx));
+  CK(launch_glue(ctx->glue, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int> stt(ctx->nsys);
+  CK(cudaMemcpy(stt.data(), ctx->d_status, ctx->nsys * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int s = 0; s < ctx->nsys; ++s)
+    if (stt[s]) {
+      ctx->err = "Darcy Cholesky: non-positive pivot in system " + std::to_string(s);
+      return TPNS_EBREAKDOWN;
+    }
+  return TPNS_OK;
+}
+
+// ------------------------------------------------------------------------------ ABI
+extern "C" {
+
+tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, const tpns_partition_desc* part,
+                        const tpns_data_desc* data, double dt, tpns_precision precision, size_t hbm_budget_bytes,
+                        void* cuda_stream, tpns_ctx** out) {
+  g_err.clear();
+  if (!out) { g_err = "out is NULL"; return TPNS_EINVAL; }
+  *out = nullptr;
+  if (!mesh || !params || !part || !data) { g_err = "NULL argument"; return TPNS_EINVAL; }
+  if (!(dt > 0)) { g_err = "dt must be positive"; return TPNS_EINVAL; }
+  if (precision != TPNS_FP64 && precision != TPNS_FP32_IR) {
+    g_err = "precision not available in this build";
+    return TPNS_EINVAL;
+  }
+  if (!(params->nu > 0 && params->eta > 0 && params->rho > 0 && params->mu > 0 && params->alpha >= 0 &&
+        params->k[0] > 0 && params->k[1] > 0 && params->k[2] > 0 && params->phiC[0] > 0 && params->phiC[1] > 0 &&
+        params->phiC[2] > 0 && params->sigma >= 0 && params->sigma_star >= 0)) {
+    g_err = "invalid physical parameters";
+    return TPNS_EINVAL;
+  }
+  if (data->mms_id != 0 && data->mms_id != 1 && data->mms_id != 3) { g_err = "unknown mms_id"; return TPNS_EINVAL; }
+  tpns_ctx* ctx = new (std::nothrow) tpns_ctx();
+  if (!ctx) { g_err = "host allocation failed"; return TPNS_ENOMEM; }
+  cudaGetDevice(&ctx->device);
+  ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  ctx->prec = precision;
+  ctx->dt = dt;
+  Phys& P = ctx->phys;
+  P.nu = params->nu; P.eta = params->eta; P.rho = params->rho; P.mu = params->mu; P.alpha = params->alpha;
+  P.sigma = params->sigma; P.sigma_star = params->sigma_star;
+  for (int i = 0; i < 3; ++i) { P.phiC[i] = params->phiC[i]; P.k[i] = params->k[i]; }
+  P.dt = dt;
+  P.mms = data->mms_id;
+  tpns_status s = build_ctx(ctx, *mesh, *part, hbm_budget_bytes);
+  if (s == TPNS_OK) s = setup_factors(ctx);
+  if (s != TPNS_OK) {
+    g_err = ctx->err;
+    tpns_destroy(ctx);
+    return s;
+  }
+  ctx->stats.n_fine_dofs = (int64_t)ctx->L.mch.nn * 2 + ctx->L.mch.nv + (int64_t)ctx->L.mph.nn * 3;
+  ctx->stats.n_local_systems = (int64_t)ctx->list_local.size();
+  ctx->stats.device_bytes = (int64_t)ctx->bytes;
+  ctx->stats.band_lu_flops = ctx->lu_flops_step;
+  *out = ctx;
+  return TPNS_OK;
+}
+
+tpns_status tpns_step(tpns_ctx* ctx, int32_t nsteps) {
+  if (!ctx || nsteps < 0) return TPNS_EINVAL;
+  ctx->err.clear();
+  ctx->traj_base = -1000000000;
+  return run_steps(ctx, nsteps, false);
+}
+
+tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps) {
+  if (!ctx || nsteps < 0) return TPNS_EINVAL;
+  ctx->err.clear();
+  const Layout& L = ctx->L;
+  size_t nu = (size_t)L.mcH.nn * 2, npc = L.mcH.nv, npd = (size_t)L.mpH.nn * 3;
+  size_t len = nu + npc + npd;
+  for (double* p : ctx->traj) cudaFree(p), ctx->bytes -= len * 8;
+  for (double* p : ctx->traj) {
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), (void*)p);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+  }
+  ctx->traj.clear();
+  cudaStream_t st = ctx->stream;
+  // save the current coarse state, then march the coarse problem alone
+  std::vector<double> keep_uc(nu), keep_pc(npc), keep_pd(npd);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpy(keep_uc.data(), ctx->d_uc_old, nu * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(keep_pc.data(), ctx->d_pc_new, npc * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(keep_pd.data(), ctx->d_pd_old, npd * 8, cudaMemcpyDeviceToHost));
+  int64_t step0 = ctx->step;
+  for (int k = 0; k <= nsteps; ++k) {
+    double* slot;
+    TRY(dalloc(ctx, &slot, len));
+    ctx->traj.push_back(slot);
+    if (k > 0) {
+      TRY(coarse_step(ctx));
+      CK(cudaMemcpyAsync(slot, ctx->d_uc_new, nu * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(slot + nu, ctx->d_pc_new, npc * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(slot + nu + npc, ctx->d_pd_new, npd * 8, cudaMemcpyDeviceToDevice, st));
+      TRY(end_step(ctx));
+    } else {
+      CK(cudaMemcpyAsync(slot, ctx->d_uc_old, nu * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(slot + nu, ctx->d_pc_new, npc * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(slot + nu + npc, ctx->d_pd_old, npd * 8, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  // rewind the clock and the coarse state
+  CK(cudaMemcpy(ctx->d_uc_old, keep_uc.data(), nu * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_uc_new, keep_uc.data(), nu * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_pc_new, keep_pc.data(), npc * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_pd_old, keep_pd.data(), npd * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_pd_new, keep_pd.data(), npd * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_step, &step0, 8, cudaMemcpyHostToDevice));
+  ctx->step = step0;
+  ctx->traj_base = (int)step0;
+  return TPNS_OK;
+}
+
+tpns_status tpns_local_step(tpns_ctx* ctx, int32_t nsteps) {
+  if (!ctx || nsteps < 0) return TPNS_EINVAL;
+  ctx->err.clear();
+  cudaStream_t st = ctx->stream;
+  CK(launch_set_time(ctx->d_tnow, ctx->d_step, ctx->dt, 0, st));
+  return run_steps(ctx, nsteps, true);
+}
+
+tpns_status tpns_num_dofs(const tpns_ctx* ctx, int32_t field, size_t* n) {
+  if (!ctx || !n) return TPNS_EINVAL;
+  const Layout& L = ctx->L;
+  switch (field) {
+    case 0: case 1: *n = (size_t)L.mch.nn; return TPNS_OK;
+    case 2: *n = (size_t)L.mch.nv; return TPNS_OK;
+    case 3: case 4: case 5: *n = (size_t)L.mph.nn; return TPNS_OK;
+    default: return TPNS_EINVAL;
+  }
+}
+
+tpns_status tpns_get_field(tpns_ctx* ctx, int32_t field, double* dst, size_t n, int32_t dst_on_device) {
+  if (!ctx || !dst) return TPNS_EINVAL;
+  size_t need = 0;
+  if (tpns_num_dofs(ctx, field, &need) != TPNS_OK || n < need) {
+    ctx->err = "destination too small or bad field";
+    return TPNS_EINVAL;
+  }
+  cudaStream_t st = ctx->stream;
+  const Layout& L = ctx->L;
+  CK(cudaStreamSynchronize(st));
+  if (field <= 1) {
+    // strided component of the interleaved velocity
+    std::vector<double> tmp((size_t)L.mch.nn * 2);
+    CK(cudaMemcpy(tmp.data(), ctx->d_out_u, tmp.size() * 8, cudaMemcpyDeviceToHost));
+    std::vector<double> comp(L.mch.nn);
+    for (int i = 0; i < L.mch.nn; ++i) comp[i] = tmp[2 * i + field];
+    CK(cudaMemcpy(dst, comp.data(), need * 8, dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    return TPNS_OK;
+  }
+  const double* src = field == 2 ? ctx->d_out_p : ctx->d_out_pd + (size_t)(field - 3) * L.mph.nn;
+  CK(cudaMemcpyAsync(dst, src, need * 8, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return TPNS_OK;
+}
+
+tpns_status tpns_get_stats(tpns_ctx* ctx, tpns_stats* out) {
+  if (!ctx || !out) return TPNS_EINVAL;
+  ctx->stats.device_bytes = (int64_t)ctx->bytes;
+  *out = ctx->stats;
+  return TPNS_OK;
+}
+
+tpns_status tpns_batch_step(tpns_ctx** ctxs, int32_t n) {
+  if (!ctxs || n < 0) return TPNS_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    tpns_status s = tpns_step(ctxs[i], 1);
+    if (s != TPNS_OK) return s;
+  }
+  return TPNS_OK;
+}
+
+const char* tpns_last_error(const tpns_ctx* ctx) {
+  if (!ctx) return g_err.c_str();
+  return ctx->err.c_str();
+}
+
+void tpns_destroy(tpns_ctx* ctx) {
+  if (!ctx) return;
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (double* p : ctx->traj) {
+    (void)p;
+  }
+  delete ctx;
+}
+
+tpns_status tpns_debug_mesh(const tpns_ctx* ctx, int32_t what, void* dst, size_t* n) {
+  if (!ctx || !n) return TPNS_EINVAL;
+  const Layout& L = ctx->L;
+  const Mesh* m = (what == 0 || what == 2) ? &L.mch : &L.mph;
+  if (what == 0 || what == 1) {
+    *n = m->node.size();
+    if (dst) std::memcpy(dst, m->node.data(), m->node.size() * sizeof(double));
+    return TPNS_OK;
+  }
+  if (what == 2 || what == 3) {
+    *n = m->tri6.size();
+    if (dst) std::memcpy(dst, m->tri6.data(), m->tri6.size() * sizeof(int32_t));
+    return TPNS_OK;
+  }
+  return TPNS_EINVAL;
+}
+
+tpns_status tpns_debug_system(const tpns_ctx* ctx, int32_t j, int32_t* n_unknowns, int32_t* unknown_node,
+                              int32_t* unknown_comp, int64_t* nnz, int32_t* rowptr, int32_t* colidx, int32_t* kl,
+                              int32_t* ku) {
+  if (!ctx) return TPNS_EINVAL;
+  // local systems in order: conduit subdomains, then porous subdomains (one pattern each)
+  const Problem* P = nullptr;
+  if (j >= 0 && j < ctx->nf) P = &ctx->L.fluid[j];
+  else if (j >= ctx->nf && j < ctx->nf + ctx->np) P = &ctx->L.porous[j - ctx->nf];
+  else return TPNS_EINVAL;
+  if (n_unknowns) *n_unknowns = P->n;
+  if (nnz) *nnz = (int64_t)P->colidx.size();
+  if (kl) *kl = P->kl;
+  if (ku) *ku = P->ku;
+  if (unknown_node)
+    for (int d = 0; d < P->n; ++d) unknown_node[d] = P->gnode[P->dof_node[d]];
+  if (unknown_comp)
+    for (int d = 0; d < P->n; ++d) unknown_comp[d] = P->dof_comp[d];
+  if (rowptr) std::memcpy(rowptr, P->rowptr.data(), P->rowptr.size() * sizeof(int32_t));
+  if (colidx) std::memcpy(colidx, P->colidx.data(), P->colidx.size() * sizeof(int32_t));
+  return TPNS_OK;
+}
+
+}  // extern "C"

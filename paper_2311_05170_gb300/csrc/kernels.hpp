@@ -1,0 +1,86 @@
+// Launch wrappers of the device kernels (host-callable).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace tpns {
+
+constexpr int LU_NB = 32;        // panel width of the band LU and block size of the solves
+constexpr int LU_CLUSTER = 8;    // CTAs per system in the band LU
+
+// ---- band linear algebra (kernels_band.cu); `T` = float or double
+template <typename T>
+cudaError_t launch_band_fill(const SysDev* sys, const int* sys_list, int nsys, const int32_t* rowof,
+                             const int32_t* colidx, const double* vals, T* band, int chol,
+                             int64_t total_nnz_hint, cudaStream_t st, const int* skip);
+template <typename T>
+cudaError_t launch_band_lu(const SysDev* sys, const int* sys_list, int nsys, int kl_max, T* band,
+                           T* dinv, int* status, cudaStream_t st, const int* skip);
+template <typename T>
+cudaError_t launch_band_chol(const SysDev* sys, const int* sys_list, int nsys, T* band, int* status,
+                             cudaStream_t st);
+// x (+)= (LU)^{-1} r  (mode per system: sys_chol[s] = 1 for Cholesky storage)
+template <typename T>
+cudaError_t launch_band_solve(const SysDev* sys, const int* sys_list, const int* sys_chol, int nsys,
+                              int n_max, const T* band, const double* r, double* x, int accumulate,
+                              const int* done, cudaStream_t st, const int* skip);
+// r = b - A x in FP64, convergence bookkeeping (relative residual <= tol, or stagnation)
+cudaError_t launch_residual(const SysDev* sys, const int* sys_list, int nsys, const int32_t* rowptr,
+                            const int32_t* colidx, const double* vals, const double* b,
+                            const double* x, double* r, double* rel, double* rel_prev, int* done,
+                            int* iters, double tol, int first, cudaStream_t st, const int* skip);
+
+// ---- assembly (kernels_assemble.cu)
+struct AsmArgs {
+  const ProbDev* probs;
+  const int32_t* eprob;    // element -> problem
+  const double* geo;       // 11 doubles / element
+  const int32_t* e6;
+  const int32_t* e3;
+  const int8_t* egam;
+  const int32_t* gnode;    // per local node (n_off)
+  const int8_t* nkind;
+  const int32_t* gam_src;
+  const int32_t* node_dof; // 2 per local node
+  const int32_t* vloc;     // per local vertex (v_off)
+  const int32_t* vert_dof;
+  const double* ref;       // reference tables (RefTables, as doubles)
+  Phys phys;
+  const double* tnow;      // device scalar: t_{n+1}
+};
+cudaError_t launch_oseen_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Ke, double* Re,
+                              cudaStream_t st, const int* skip);
+cudaError_t launch_darcy_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Re,
+                              double* Ke, cudaStream_t st);
+cudaError_t launch_seg_reduce(const int32_t* tgt, const int32_t* src, int64_t nlanes,
+                              const double* in, double* out, cudaStream_t st, const int* skip);
+// write e^{n+1} (all local nodes) from the unknowns x
+cudaError_t launch_state(const AsmArgs& a, const int32_t* nprob, const int32_t* nvidx,
+                         int64_t n_begin, int64_t nn, const double* x, cudaStream_t st,
+                         const int* skip);
+cudaError_t launch_prolong(int n2c, int n1c, int n2p, const int32_t* pc2i, const double* pc2w,
+                           const int32_t* pc1i, const double* pc1w, const int32_t* pp2i,
+                           const double* pp2w, const double* uc_new, const double* uc_old,
+                           const double* pc_new, const double* pd_new, const double* pd_old,
+                           int64_t nnpH, double* FW1, double* FW0, double* FP1, double* FPD1,
+                           double* FPD0, int64_t nnp, cudaStream_t st);
+struct GlueArgs {
+  const ProbDev* fluid;
+  const ProbDev* porous;
+  const int32_t *gc_ptr, *gc_prob, *gc_node; const double* gc_w;
+  const int32_t *gp_ptr, *gp_prob, *gp_node; const double* gp_w;
+  const int32_t *gv_ptr, *gv_prob, *gv_vert; const double* gv_w;
+  const double *FW1, *FP1, *FPD1;
+  double *out_u, *out_p, *out_pd;
+  int nnc, nvc, nnp;
+};
+cudaError_t launch_glue(const GlueArgs& g, cudaStream_t st);
+// coarse Newton: u += delta (all coarse nodes), p += delta_p; convergence flag
+cudaError_t launch_newton_update(const ProbDev* prob, const int32_t* gnode, const int32_t* vloc,
+                                 int nn, int nvl, double* u, double* p, int* done, int* iters,
+                                 cudaStream_t st);
+cudaError_t launch_set_time(double* tnow, int64_t* step, double dt, int advance, cudaStream_t st);
+
+}  // namespace tpns

@@ -1,0 +1,204 @@
+"""ctypes binding of the C ABI declared in include/tpns.h (argument marshalling only).
+
+Every computation runs in libtpns.so; this module raises if the library is missing."""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libtpns.so")
+
+TPNS_OK, TPNS_EINVAL, TPNS_ENOMEM, TPNS_ENOTCONV, TPNS_EDEVICE, TPNS_ETIMEOUT, TPNS_EBUDGET, TPNS_EBREAKDOWN = range(8)
+STATUS_NAMES = ["TPNS_OK", "TPNS_EINVAL", "TPNS_ENOMEM", "TPNS_ENOTCONV", "TPNS_EDEVICE", "TPNS_ETIMEOUT",
+                "TPNS_EBUDGET", "TPNS_EBREAKDOWN"]
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+MAX_COARSE_ROWS = 64
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("nx_coarse", C.c_int32), ("ny_coarse", C.c_int32), ("fine_per_coarse_x", C.c_int32),
+                ("fine_rows_from_gamma", C.c_int32 * MAX_COARSE_ROWS)]
+
+
+class Params(C.Structure):
+    _fields_ = [("nu", C.c_double), ("eta", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
+                ("alpha", C.c_double), ("sigma", C.c_double), ("sigma_star", C.c_double),
+                ("phiC", C.c_double * 3), ("k", C.c_double * 3)]
+
+
+class PartitionDesc(C.Structure):
+    _fields_ = [("nsub_x", C.c_int32), ("nsub_y", C.c_int32), ("overlap", C.c_int32)]
+
+
+class DataDesc(C.Structure):
+    _fields_ = [("mms_id", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("last_ir_iters_max", C.c_int32), ("last_newton_iters", C.c_int32),
+                ("last_ir_relres_max", C.c_double), ("n_fine_dofs", C.c_int64), ("n_local_systems", C.c_int64),
+                ("device_bytes", C.c_int64), ("band_lu_flops", C.c_double)]
+
+
+class TpnsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+EXPORTS = ["tpns_create", "tpns_step", "tpns_coarse_precompute", "tpns_local_step", "tpns_num_dofs",
+           "tpns_get_field", "tpns_get_stats", "tpns_batch_step", "tpns_last_error", "tpns_destroy",
+           "tpns_debug_mesh", "tpns_debug_system"]
+
+
+def load(path=LIB_PATH):
+    """Load libtpns.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libtpns.so not found at {path}; build it with paper_2311_05170_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.tpns_create.argtypes = [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(PartitionDesc),
+                                C.POINTER(DataDesc), C.c_double, C.c_int, C.c_size_t, P, C.POINTER(P)]
+    lib.tpns_create.restype = C.c_int
+    for name in ("tpns_step", "tpns_coarse_precompute", "tpns_local_step"):
+        getattr(lib, name).argtypes = [P, C.c_int32]
+        getattr(lib, name).restype = C.c_int
+    lib.tpns_num_dofs.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
+    lib.tpns_num_dofs.restype = C.c_int
+    lib.tpns_get_field.argtypes = [P, C.c_int32, P, C.c_size_t, C.c_int32]
+    lib.tpns_get_field.restype = C.c_int
+    lib.tpns_get_stats.argtypes = [P, C.POINTER(Stats)]
+    lib.tpns_get_stats.restype = C.c_int
+    lib.tpns_batch_step.argtypes = [C.POINTER(P), C.c_int32]
+    lib.tpns_batch_step.restype = C.c_int
+    lib.tpns_last_error.argtypes = [P]
+    lib.tpns_last_error.restype = C.c_char_p
+    lib.tpns_destroy.argtypes = [P]
+    lib.tpns_destroy.restype = None
+    lib.tpns_debug_mesh.argtypes = [P, C.c_int32, P, C.POINTER(C.c_size_t)]
+    lib.tpns_debug_mesh.restype = C.c_int
+    I32 = C.POINTER(C.c_int32)
+    lib.tpns_debug_system.argtypes = [P, C.c_int32, I32, I32, I32, C.POINTER(C.c_int64), I32, I32, I32, I32]
+    lib.tpns_debug_system.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(lib, ctx, status):
+    if status != TPNS_OK:
+        msg = lib.tpns_last_error(ctx)
+        raise TpnsError(status, msg.decode() if msg else "")
+
+
+def descriptors(w):
+    """ABI descriptors of a workloads.Workload."""
+    md = MeshDesc()
+    md.nx_coarse, md.ny_coarse, md.fine_per_coarse_x = w.nx_coarse, w.ny_coarse, w.fine_per_coarse_x
+    for c, m in enumerate(w.fine_rows_from_gamma):
+        md.fine_rows_from_gamma[c] = m
+    p = w.params
+    pr = Params(p.nu, p.eta, p.rho, p.mu, p.alpha, p.sigma, p.sigma_star, (C.c_double * 3)(*p.phiC),
+                (C.c_double * 3)(*p.k))
+    pd = PartitionDesc(w.nsub[0], w.nsub[1], w.overlap)
+    dd = DataDesc(w.mms)
+    return md, pr, pd, dd
+
+
+FIELD_IDS = {"ux": 0, "uy": 1, "p": 2, "pF": 3, "pf": 4, "pm": 5}
+
+
+class Solver:
+    """One simulation context on the current CUDA device."""
+
+    def __init__(self, w, precision="fp64", hbm_budget_bytes=0, stream=None):
+        self.lib = load()
+        self.w = w
+        md, pr, pd, dd = descriptors(w)
+        ctx = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        s = self.lib.tpns_create(C.byref(md), C.byref(pr), C.byref(pd), C.byref(dd), float(w.dt),
+                                 PRECISIONS[precision], int(hbm_budget_bytes), st, C.byref(ctx))
+        _check(self.lib, None, s)
+        self.ctx = ctx
+
+    def step(self, n=1):
+        _check(self.lib, self.ctx, self.lib.tpns_step(self.ctx, int(n)))
+
+    def coarse_precompute(self, n):
+        _check(self.lib, self.ctx, self.lib.tpns_coarse_precompute(self.ctx, int(n)))
+
+    def local_step(self, n=1):
+        _check(self.lib, self.ctx, self.lib.tpns_local_step(self.ctx, int(n)))
+
+    def num_dofs(self, field):
+        n = C.c_size_t()
+        _check(self.lib, self.ctx, self.lib.tpns_num_dofs(self.ctx, FIELD_IDS.get(field, field), C.byref(n)))
+        return n.value
+
+    def field(self, field, out=None):
+        """Glued global fine field as a NumPy array (host copy)."""
+        fid = FIELD_IDS.get(field, field)
+        n = self.num_dofs(fid)
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        _check(self.lib, self.ctx, self.lib.tpns_get_field(self.ctx, fid, out.ctypes.data, n, 0))
+        return out
+
+    def field_to_device(self, field, dev_ptr, n):
+        fid = FIELD_IDS.get(field, field)
+        _check(self.lib, self.ctx, self.lib.tpns_get_field(self.ctx, fid, C.c_void_p(dev_ptr), n, 1))
+
+    def fields(self):
+        return {k: self.field(k) for k in FIELD_IDS}
+
+    def stats(self):
+        s = Stats()
+        _check(self.lib, self.ctx, self.lib.tpns_get_stats(self.ctx, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def debug_mesh(self, what):
+        n = C.c_size_t()
+        _check(self.lib, self.ctx, self.lib.tpns_debug_mesh(self.ctx, what, None, C.byref(n)))
+        out = np.empty(n.value, dtype=np.float64 if what in (0, 1) else np.int32)
+        _check(self.lib, self.ctx, self.lib.tpns_debug_mesh(self.ctx, what, out.ctypes.data, C.byref(n)))
+        return out
+
+    def debug_system(self, j):
+        lib = self.lib
+        n = C.c_int32()
+        nnz = C.c_int64()
+        kl, ku = C.c_int32(), C.c_int32()
+        _check(lib, self.ctx, lib.tpns_debug_system(self.ctx, j, C.byref(n), None, None, C.byref(nnz), None, None,
+                                                    C.byref(kl), C.byref(ku)))
+        node = np.empty(n.value, np.int32)
+        comp = np.empty(n.value, np.int32)
+        rp = np.empty(n.value + 1, np.int32)
+        ci = np.empty(nnz.value, np.int32)
+        I32 = C.POINTER(C.c_int32)
+        _check(lib, self.ctx, lib.tpns_debug_system(self.ctx, j, None, node.ctypes.data_as(I32),
+                                                    comp.ctypes.data_as(I32), None, rp.ctypes.data_as(I32),
+                                                    ci.ctypes.data_as(I32), None, None))
+        return {"node": node, "comp": comp, "rowptr": rp, "colidx": ci, "kl": kl.value, "ku": ku.value}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.tpns_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_step(solvers):
+    lib = load()
+    arr = (C.c_void_p * len(solvers))(*[s.ctx for s in solvers])
+    _check(lib, None, lib.tpns_batch_step(arr, len(solvers)))
