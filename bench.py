@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the per-step hot path of the local parallel two-grid method (Algorithm 3,
+Steps 3-4 after the coarse solve) on the 2D workload graded toward the interface:
+H = 1/8, h_x = 1/128, h_y from 1/128 at Gamma to 1/32, 4 x 4 subdomains per region,
+overlap 2 fine layers, log-uniform permeabilities (seed 0), dt = 0.005 -- 130,966 fine
+dofs, 16 Oseen systems (3.3k-8.3k unknowns) and 48 Darcy systems per step.
+
+Metric: fine dof-steps per second of the hot path, mixed precision (FP32 band factors and
+solves, FP64 assembly and refinement residuals), valid only if every field is within
+relative L2 1e-8 of the FP64 GPU path on the same steps.  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine DOF-steps/s at relL2<=1e-8, mixed vs FP64 GPU"
+UNIT = "DOF-steps/s"
+WORKLOAD = "2d_graded_H8_h128_to_h32_4x4sub_overlap2h_dt0.005 (130,966 fine dofs)"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cpu-sample-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import workloads as W
+from oracle.scheme import TwoGridOracle
+w = W.config_graded(nsteps=%d)
+o = TwoGridOracle(w)
+for _ in range(%d):                       # warm-up steps
+    o.step()
+t0 = time.perf_counter()
+for _ in range(%d):
+    o.step()
+dt = time.perf_counter() - t0
+nd = 2 * o.mch.nn + o.mch.nv + 3 * o.mph.nn
+print(json.dumps({"secs": dt, "steps": %d, "dofs": int(nd)}))
+"""
+
+
+def oracle_sample(nsteps, warmup=1):
+    """Time the oracle (as it stands) single-threaded in a fresh process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET % (ROOT, nsteps + warmup, warmup, nsteps, nsteps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["dofs"] * d["steps"] / d["secs"], d
+
+
+def cpu_baseline_obj(value, d):
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['steps']} full time steps (coarse + all local solves + glue) of the same workload, "
+                      f"NumPy/SciPy FP64, one thread, after warm-up steps; {d['secs']:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- roofline
+def band_sizes(solver, n_fluid, n_porous):
+    out = []
+    for j in range(n_fluid + n_porous):
+        info = solver.debug_system(j)
+        n = len(info["node"])
+        reps = 1 if j < n_fluid else 3
+        kl = info["kl"]
+        ku = info["ku"] if j < n_fluid else kl
+        out += [(n, kl, ku, j < n_fluid)] * reps
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2311_05170_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    import workloads as W
+    from paper_2311_05170_gb300.native import Solver, launch_count
+    K, Wm = args.steps, args.warmup
+    w = W.config_graded(nsteps=Wm + K)
+    stream = torch.cuda.Stream()
+    handle = stream.cuda_stream
+
+    def timed_hot(prec, timing=False):
+        s = Solver(w, precision=prec, stream=handle)
+        s.coarse_precompute(Wm + K)
+        s.local_step(Wm)
+        if timing:
+            s.set_timing(True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        l0 = launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clk = Clocks(local)
+        if timing:
+            clk.start()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.local_step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop() if timing else None
+        ms = e0.elapsed_time(e1)
+        launches = launch_count() - l0
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return s, ms, launches, clocks
+
+    s64, ms64, _, _ = timed_hot("fp64")
+    f64 = s64.fields()
+    st64 = s64.stats()
+    s64.close()
+    s, ms, launches, clocks = timed_hot(args.precision, timing=True)
+    f = s.fields()
+    st = s.stats()
+    rel = {k: float(np.linalg.norm(f[k] - f64[k]) / np.linalg.norm(f64[k])) for k in f}
+    ph = {k: v[0] / K for k, v in s.timings().items()}
+    phn = {k: v[1] for k, v in s.timings().items()}
+    ndofs = st["n_fine_dofs"]
+    value = ndofs * K * world / (ms / 1e3)
+    value64 = ndofs * K * world / (ms64 / 1e3)
+    valid = max(rel.values()) <= 1e-8
+    # ---------------------------------------------------------------- roofline
+    peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    n_fluid = 16                      # 4 x 4 conduit subdomains
+    sizes = band_sizes(s, n_fluid, 16)
+    tsz = 4 if args.precision == "fp32" else 8
+    solve_bytes = sum(n * (kl + ku) * tsz + ((n + 31) // 32) * 2 * 1024 * tsz + n * 8 * 2 for n, kl, ku, _ in sizes)
+    lu_ms = ph["band_lu"]
+    lu_tflops = st["band_lu_flops"] / (lu_ms / 1e3) / 1e12
+    solve_launch_ms = ph["solve"] * K / max(phn["solve"], 1)
+    kernels = {
+        "band_lu": {"bound": "alu", "achieved": lu_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": lu_tflops / FP32_PEAK_TFLOPS, "ms_per_step": lu_ms},
+        "band_solve": {"bound": "hbm", "achieved": solve_bytes / (solve_launch_ms / 1e3) / 1e9, "peak": hbm_peak,
+                       "unit": "GB/s", "frac": solve_bytes / (solve_launch_ms / 1e3) / 1e9 / hbm_peak,
+                       "ms_per_step": ph["solve"]},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(dom)
+        except Exception:
+            traffic = None
+    roof = dict(kernels[dom])
+    roof.pop("ms_per_step")
+    roof["kernel"] = dom
+    roof["traffic"] = traffic
+    roof["peak_source"] = ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if roof["bound"] == "alu"
+                           else "measured hbm_gbs (MEASURED_PEAKS.json)")
+    s.close()
+    # ---------------------------------------------------------------- end to end (public API, host buffers)
+    torch.cuda.synchronize()
+    pinned = {}
+    t0 = time.perf_counter()
+    e = Solver(w, precision=args.precision, stream=handle)
+    d2h = 0
+    for _ in range(K):
+        e.step(1)
+        for k in ("ux", "uy", "p", "pF", "pf", "pm"):
+            if k not in pinned:
+                pinned[k] = torch.empty(e.num_dofs(k), dtype=torch.float64).pin_memory()
+            buf = pinned[k].numpy()
+            e.field(k, out=buf)
+            d2h += buf.nbytes
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    st_e = e.stats()
+    e.close()
+    e2e_val = ndofs * K * world / e2e_s
+    full_ms = e2e_s * 1e3 / K
+    # ---------------------------------------------------------------- CPU baseline (oracle)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            v, d = oracle_sample(args.cpu_sample_steps)
+            cpu = cpu_baseline_obj(v, d)
+        except Exception as ex:  # the line still reports the GPU numbers
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value if valid else None, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "fine_dofs": ndofs, "local_systems_per_step": st["n_local_systems"],
+                       "replicas": world, "l2": "inputs larger than L2 (band factors %.0f MB per replica)"
+                       % (sum(n * (kl + ku + 1) for n, kl, ku, _ in sizes) * tsz / 1e6),
+                       "parallelism": "independent replicas (no data-path collective)",
+                       "timed": "K hot-path steps (prolongation, assembly, band LU, solves + FP64 refinement, glue) "
+                                "on coarse states precomputed in HBM"},
+            "valid": valid, "relL2_vs_fp64_gpu": rel,
+            "fp64_gpu": {"value": value64, "ms_per_step": ms64 / K},
+            "speedup_vs_fp64_gpu": value / value64,
+            "roofline": roof, "kernels": kernels,
+            "phases_ms_per_step": ph,
+            "ir": {"iters_max": st["last_ir_iters_max"], "relres_max": st["last_ir_relres_max"]},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": st_e["h2d_bytes"] / K,
+                    "d2h_bytes_per_step": d2h / K,
+                    "what": "tpns_create from host descriptors + K x (tpns_step incl. coarse solve + "
+                            "tpns_get_field of all 6 fields into pinned host memory)",
+                    "full_step_ms": full_ms},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank):
+    """The oracle as the reference implementation, timed on the host cores."""
+    if rank != 0:
+        return
+    v, d = oracle_sample(args.steps, warmup=args.warmup)
+    cpu = cpu_baseline_obj(v, d)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": d["secs"] * 1e3 / d["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "impl": "reference", "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

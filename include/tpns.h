@@ -99,6 +99,7 @@ typedef struct {
   int64_t n_local_systems;        /* Oseen + Darcy local systems per step */
   int64_t device_bytes;           /* device footprint of the context */
   double band_lu_flops;           /* algorithmic flops of one step's Oseen band LUs */
+  int64_t h2d_bytes;              /* bytes copied host -> device by tpns_create */
 } tpns_stats;
 
 typedef struct tpns_ctx tpns_ctx;
@@ -144,6 +145,19 @@ tpns_status tpns_get_stats(tpns_ctx* ctx, tpns_stats* out);
  * the same device and share the precision; the work is enqueued on ctxs[0]'s stream. */
 tpns_status tpns_batch_step(tpns_ctx** ctxs, int32_t n);
 
+/* Per-phase device time, measured with CUDA events recorded on the context's stream
+ * around each phase of a step while timing is on (tpns_set_timing(ctx, 1) also clears
+ * the totals).  Phase ids: 0 coarse solves (Step 1), 1 prolongation, 2 Oseen element
+ * assembly, 3 scatter reductions of the Oseen systems, 4 Darcy right-hand sides, 5 band
+ * fill, 6 band LU, 7 band triangular solves, 8 FP64 residuals, 9 state update and glue,
+ * 10 end-of-step copies.  ms[i] = total milliseconds, count[i] = timed intervals; either
+ * array may be NULL; n = entries to write (at most 11). */
+tpns_status tpns_set_timing(tpns_ctx* ctx, int32_t on);
+tpns_status tpns_get_timings(const tpns_ctx* ctx, double* ms, int64_t* count, int32_t n);
+
+/* Kernel launches issued by the library since it was loaded (all contexts). */
+int64_t tpns_launch_count(void);
+
 /* Last error message of a context (never NULL; "" when none).  ctx may be NULL for errors
  * raised before a context existed. */
 const char* tpns_last_error(const tpns_ctx* ctx);
@@ -165,6 +179,17 @@ tpns_status tpns_debug_system(const tpns_ctx* ctx, int32_t j, int32_t* n_unknown
                               int32_t* unknown_node, int32_t* unknown_comp,
                               int64_t* nnz, int32_t* rowptr, int32_t* colidx,
                               int32_t* kl, int32_t* ku);
+
+/* Host-only context: builds meshes, subdomains, orderings and patterns (Algorithm 3 Step 2)
+ * without touching a GPU, for the introspection calls above.  Every other call on it
+ * returns TPNS_EINVAL.  Release with tpns_destroy. */
+tpns_status tpns_layout_create(const tpns_mesh_desc* mesh, const tpns_partition_desc* part,
+                               tpns_ctx** out);
+
+/* FP64 CSR values (nnz entries, pattern of tpns_debug_system) and right-hand side (n
+ * entries) of local system j as assembled in the last step (Darcy: field 0..2 selects the
+ * pressure; ignored for Oseen systems).  Host destination buffers. */
+tpns_status tpns_debug_values(tpns_ctx* ctx, int32_t j, int32_t field, double* vals, double* rhs);
 
 #ifdef __cplusplus
 }

@@ -395,7 +395,10 @@ class TwoGridOracle:
         return x[:2 * nn].reshape(nn, 2).copy(), x[2 * nn:].copy()
 
     # ------------------------------------------------------------------ Step 3
-    def local_fluid(self, j, t, uH1h, uH0h, pH1h, pFn_h_gamma):
+    def local_fluid_system(self, j, t, uH1h, uH0h, pH1h, pFn_h_gamma):
+        """Reduced system (A_ff, b, free, xfull) of the conduit correction on Omega_j
+        (eq. uclocalFully): Dirichlet values of the correction are in xfull[fixed] and
+        have been moved to the right-hand side."""
         s, O = self.sub_c[j]
         m, prm = self.mms, self.prm
         g = s.gnode
@@ -420,13 +423,18 @@ class TwoGridOracle:
         xfull = np.zeros(O.ntot)
         xfull[:2 * len(g)] = eB.ravel()
         b = r[free] - A[free][:, fixed] @ xfull[fixed]
-        sol = solve_sparse(A[free][:, free], b)
-        xfull[free] = sol
-        e = xfull[:2 * len(g)].reshape(-1, 2)
-        delta = xfull[2 * len(g):]
-        return e, delta
+        return A[free][:, free], b, free, xfull
 
-    def local_porous(self, j, t, pH1h, pH0h, ucn_h_gamma_n):
+    def local_fluid(self, j, t, uH1h, uH0h, pH1h, pFn_h_gamma):
+        s, O = self.sub_c[j]
+        Aff, b, free, xfull = self.local_fluid_system(j, t, uH1h, uH0h, pH1h, pFn_h_gamma)
+        xfull[free] = solve_sparse(Aff, b)
+        nn = len(s.gnode)
+        return xfull[:2 * nn].reshape(-1, 2), xfull[2 * nn:]
+
+    def local_porous_system(self, j, i, t, pH1h, pH0h, ucn_h_gamma_n):
+        """Reduced system (A_ff, b, free, x) of pressure i (0 = F, 1 = f, 2 = m) on Omega_j
+        (eqs. pFlocalFully, pflocalFully, pmlocalFully)."""
         s, O = self.sub_p[j]
         m, prm, dt = self.mms, self.prm, self.dt
         g = s.gnode
@@ -439,26 +447,48 @@ class TwoGridOracle:
         P1 = pH1h[:, g]
         P0 = pH0h[:, g]
         partners = {0: [(cFf, 1)], 1: [(cfm, 2), (cFf, 0)], 2: [(cfm, 1)]}
-        out = np.zeros((3, len(g)))
         fixed = np.nonzero(s.kind > 0)[0]
         free = np.nonzero(s.kind == 0)[0]
+        A = O.darcy_matrix(i)
+        qq = m.q(i, R.xq[..., 0], R.xq[..., 1], t)
+        r = O.darcy_load(qq) - A @ P1[i] + (prm.phiC[i] / dt) * (Mloc @ (P0[i] + en[i]))
+        for c, k in partners[i]:
+            r += c * (Mloc @ (P0[k] + en[k]))
+        if i == 0 and len(R.edge_nodes):
+            r += O.gamma_vec(R.gamma_load(R.gamma_trace_qp(ucn_h_gamma_n[g])))
+        if len(R.edge_nodes):
+            r -= O.gamma_vec(R.gamma_load(m.gd(i, R.exq, t)))
+        x = np.zeros(len(g))
+        gl = s.kind == 1
+        x[gl] = m.pd(i, R.xy[gl, 0], R.xy[gl, 1], t) - P1[i][gl]
+        b = r[free] - A[free][:, fixed] @ x[fixed]
+        return A[free][:, free], b, free, x
+
+    def local_porous(self, j, t, pH1h, pH0h, ucn_h_gamma_n):
+        s, _ = self.sub_p[j]
+        out = np.zeros((3, len(s.gnode)))
         for i in range(3):
-            A = O.darcy_matrix(i)
-            qq = m.q(i, R.xq[..., 0], R.xq[..., 1], t)
-            r = O.darcy_load(qq) - A @ P1[i] + (prm.phiC[i] / dt) * (Mloc @ (P0[i] + en[i]))
-            for c, k in partners[i]:
-                r += c * (Mloc @ (P0[k] + en[k]))
-            if i == 0 and len(R.edge_nodes):
-                r += O.gamma_vec(R.gamma_load(R.gamma_trace_qp(ucn_h_gamma_n[g])))
-            if len(R.edge_nodes):
-                r -= O.gamma_vec(R.gamma_load(m.gd(i, R.exq, t)))
-            x = np.zeros(len(g))
-            gl = s.kind == 1
-            x[gl] = m.pd(i, R.xy[gl, 0], R.xy[gl, 1], t) - P1[i][gl]
-            b = r[free] - A[free][:, fixed] @ x[fixed]
-            x[free] = solve_sparse(A[free][:, free], b)
+            Aff, b, free, x = self.local_porous_system(j, i, t, pH1h, pH0h, ucn_h_gamma_n)
+            x[free] = solve_sparse(Aff, b)
             out[i] = x
         return out
+
+    def step_inputs(self):
+        """Coarse step plus the fine-mesh inputs of the local problems of the next step
+        (used to inspect the local systems); does not advance the state."""
+        uH0, pdH0 = self.uH, self.pdH
+        t, u1, p1, pd1 = self.coarse_step()
+        uH1h = np.stack([self.Pc2 @ u1[:, a] for a in range(2)], axis=1)
+        uH0h = np.stack([self.Pc2 @ uH0[:, a] for a in range(2)], axis=1)
+        pH1h = self.Pc1 @ p1
+        pdH1h = np.stack([self.Pp2 @ pd1[i] for i in range(3)])
+        pdH0h = np.stack([self.Pp2 @ pdH0[i] for i in range(3)])
+        pFn_c = np.zeros(self.mch.nn)
+        pFn_c[self.gam_c_h] = pdH0h[0][self.gam_p_h]
+        ucn_p = np.zeros(self.mph.nn)
+        ucn_p[self.gam_p_h] = -uH0h[self.gam_c_h, 1]
+        return dict(t=t, u1=u1, p1=p1, pd1=pd1, uH1h=uH1h, uH0h=uH0h, pH1h=pH1h, pdH1h=pdH1h,
+                    pdH0h=pdH0h, pFn_c=pFn_c, ucn_p=ucn_p)
 
     # ------------------------------------------------------------------ Step 4
     def glue(self):
@@ -490,26 +520,16 @@ class TwoGridOracle:
         return t, u_new, p_new, pd_new
 
     def step(self):
-        uH0, pdH0 = self.uH, self.pdH
-        t, u1, p1, pd1 = self.coarse_step()
-        uH1h = np.stack([self.Pc2 @ u1[:, a] for a in range(2)], axis=1)
-        uH0h = np.stack([self.Pc2 @ uH0[:, a] for a in range(2)], axis=1)
-        pH1h = self.Pc1 @ p1
-        pdH1h = np.stack([self.Pp2 @ pd1[i] for i in range(3)])
-        pdH0h = np.stack([self.Pp2 @ pdH0[i] for i in range(3)])
-        # lagged Gamma data on the fine meshes: p_FH^n for the conduit, u_cH^n . n_c for Darcy
-        pFn_c = np.zeros(self.mch.nn)
-        pFn_c[self.gam_c_h] = pdH0h[0][self.gam_p_h]
-        ucn_p = np.zeros(self.mph.nn)
-        ucn_p[self.gam_p_h] = -uH0h[self.gam_c_h, 1]
+        d = self.step_inputs()
+        t = d["t"]
         new_ec, new_dc, new_ep = [], [], []
         for j in range(len(self.sub_c)):
-            e, dl = self.local_fluid(j, t, uH1h, uH0h, pH1h, pFn_c)
+            e, dl = self.local_fluid(j, t, d["uH1h"], d["uH0h"], d["pH1h"], d["pFn_c"])
             new_ec.append(e)
             new_dc.append(dl)
         for j in range(len(self.sub_p)):
-            new_ep.append(self.local_porous(j, t, pdH1h, pdH0h, ucn_p))
-        self.uH, self.pH, self.pdH = u1, p1, pd1
+            new_ep.append(self.local_porous(j, t, d["pdH1h"], d["pdH0h"], d["ucn_p"]))
+        self.uH, self.pH, self.pdH = d["u1"], d["p1"], d["pd1"]
         self.ec, self.dc, self.ep = new_ec, new_dc, new_ep
         self.n += 1
         return self.glue()

@@ -15,6 +15,12 @@
 
 using namespace tpns;
 
+// Phases timed with CUDA events on the context's stream when timing is enabled.
+enum Phase {
+  PH_COARSE = 0, PH_PROLONG, PH_ASM_OSEEN, PH_SCATTER, PH_ASM_DARCY, PH_BAND_FILL, PH_BAND_LU,
+  PH_SOLVE, PH_RESIDUAL, PH_STATE_GLUE, PH_COPIES, PH_COUNT
+};
+
 struct tpns_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -41,9 +47,14 @@ struct tpns_ctx {
   std::vector<int> hchol;
   int nsys = 0;
   std::vector<int> list_osl, list_cf, list_dl, list_cp, list_local;
-  int kl_max_osl = 0, n_max_local = 0, kl_max_cf = 0, n_max_cf = 0, n_max_cp = 0;
+  int kl_max_osl = 0, n_max_local = 0, kmax_local = 0, kmax_cf = 0, kmax_cp = 0, kl_max_cf = 0, n_max_cf = 0, n_max_cp = 0;
   int64_t band_local_len = 0, band_coarse_len = 0, nnz_tot = 0, vals_tot = 0, xvec_tot = 0;
   double lu_flops_step = 0;
+  std::vector<SysDev> hsys_chol;          // Cholesky layout of the Darcy systems (setup only)
+  int64_t band_chol_local_len = 0, band_chol_coarse_len = 0, dinv_local_len = 0, dinv_coarse_len = 0;
+  int flags_stride = 1;
+  int lu_epoch = 0;
+  bool host_only = false;
   // device
   ProbDev* d_probs = nullptr;
   int32_t *d_eprob = nullptr, *d_e6 = nullptr, *d_e3 = nullptr;
@@ -61,6 +72,10 @@ struct tpns_ctx {
   int *d_done = nullptr, *d_iters = nullptr, *d_status = nullptr;
   void* d_band_local = nullptr;
   double* d_band_coarse = nullptr;
+  void* d_dinv_local = nullptr;
+  double* d_dinv_coarse = nullptr;
+  int* d_flags = nullptr;
+  SysDev* d_sys_chol = nullptr;
   int *d_list_osl = nullptr, *d_list_cf = nullptr, *d_list_dl = nullptr, *d_list_cp = nullptr,
       *d_list_local = nullptr;
   double *d_Ke = nullptr, *d_Re = nullptr, *d_ReD = nullptr;
@@ -88,11 +103,22 @@ struct tpns_ctx {
   int traj_base = 0;                  // step index of traj[0]
   int64_t step = 0;
   tpns_stats stats{};
+  // phase timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  cudaEvent_t ev_open[PH_COUNT] = {};
+  double ph_ms[PH_COUNT] = {};
+  int64_t ph_n[PH_COUNT] = {};
   AsmArgs asmargs{};
   GlueArgs glue{};
 };
 
 static thread_local std::string g_err;
+
+
+static void ph_begin(tpns_ctx* ctx, int id);
+static void ph_end(tpns_ctx* ctx, int id);
 
 #define CK(call)                                                                   \
   do {                                                                             \
@@ -123,6 +149,7 @@ template <typename T>
 static tpns_status upload(tpns_ctx* ctx, T** p, const std::vector<T>& v) {
   tpns_status s = dalloc(ctx, p, v.size());
   if (s != TPNS_OK) return s;
+  ctx->stats.h2d_bytes += (int64_t)(v.size() * sizeof(T));
   if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return TPNS_OK;
 }
@@ -206,7 +233,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   ctx->nb_pl = ctx->n_off[CF] + ctx->nn_cf; ctx->nn_pl = ctx->n_off[CP] - ctx->nb_pl;
   ctx->nb_cp = ctx->n_off[CP]; ctx->nn_cp = ctx->probs[CP]->nn;
   // systems
-  ctx->hsys.clear(); ctx->hchol.clear(); ctx->sys_first.assign(ctx->nprob, 0);
+  ctx->hsys.clear(); ctx->hchol.clear(); ctx->hsys_chol.clear(); ctx->sys_first.assign(ctx->nprob, 0);
+  ctx->band_chol_local_len = ctx->band_chol_coarse_len = ctx->dinv_local_len = ctx->dinv_coarse_len = 0;
   ctx->x_off.assign(ctx->nprob, 0);
   int64_t rp = 0, nz = 0, vals = 0, xo = 0, bl = 0, bc = 0;
   std::vector<int32_t> h_rowptr, h_colidx, h_rowof;
@@ -222,15 +250,28 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     h_rowof.insert(h_rowof.end(), P.rowof.begin(), P.rowof.end());
     for (int f = 0; f < nfld; ++f) {
       SysDev S{};
-      S.n = P.n; S.kl = P.kl; S.ku = P.kind == PK_OSEEN ? P.ku : 0;
-      S.ldab = P.kind == PK_OSEEN ? P.kl + P.ku + 1 : P.kl + 1;
+      S.n = P.n; S.kl = P.kl; S.ku = P.kind == PK_OSEEN ? P.ku : P.kl;
+      S.ldab = S.kl + S.ku + 1;
       S.rp_off = rp; S.nnz_off = nz; S.nnz = (int64_t)P.colidx.size();
       S.val_off = vals; vals += S.nnz;
       S.x_off = xo; xo += P.n;
-      int64_t blen = (int64_t)S.n * S.ldab;
-      if (coarse) { S.band_off = bc; bc += blen; } else { S.band_off = bl; bl += blen; }
-      S.dinv_off = 0;
+      const int64_t blen = (int64_t)S.n * S.ldab;
+      const int nblk = (S.n + LU_NB - 1) / LU_NB;
+      const int64_t dlen = (int64_t)nblk * 2 * LU_NB * LU_NB;
+      ctx->flags_stride = std::max(ctx->flags_stride, nblk);
+      SysDev C = S;
+      C.ku = 0; C.ldab = S.kl + 1;
+      if (coarse) {
+        S.band_off = bc; bc += blen;
+        S.dinv_off = ctx->dinv_coarse_len; ctx->dinv_coarse_len += dlen;
+        C.band_off = ctx->band_chol_coarse_len; ctx->band_chol_coarse_len += (int64_t)S.n * C.ldab;
+      } else {
+        S.band_off = bl; bl += blen;
+        S.dinv_off = ctx->dinv_local_len; ctx->dinv_local_len += dlen;
+        C.band_off = ctx->band_chol_local_len; ctx->band_chol_local_len += (int64_t)S.n * C.ldab;
+      }
       ctx->hsys.push_back(S);
+      ctx->hsys_chol.push_back(C);
       ctx->hchol.push_back(P.kind == PK_DARCY ? 1 : 0);
     }
     rp += P.n + 1; nz += (int64_t)P.colidx.size();
@@ -248,7 +289,12 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   ctx->list_local = ctx->list_osl;
   ctx->list_local.insert(ctx->list_local.end(), ctx->list_dl.begin(), ctx->list_dl.end());
   for (int s : ctx->list_osl) ctx->kl_max_osl = std::max(ctx->kl_max_osl, ctx->hsys[s].kl);
-  for (int s : ctx->list_local) ctx->n_max_local = std::max(ctx->n_max_local, ctx->hsys[s].n);
+  for (int s : ctx->list_local) {
+    ctx->n_max_local = std::max(ctx->n_max_local, ctx->hsys[s].n);
+    ctx->kmax_local = std::max(ctx->kmax_local, std::max(ctx->hsys[s].kl, ctx->hsys[s].ku));
+  }
+  ctx->kmax_cf = std::max(ctx->hsys[ctx->list_cf[0]].kl, ctx->hsys[ctx->list_cf[0]].ku);
+  for (int s : ctx->list_cp) ctx->kmax_cp = std::max(ctx->kmax_cp, ctx->hsys[s].kl);
   ctx->kl_max_cf = ctx->hsys[ctx->list_cf[0]].kl;
   ctx->n_max_cf = ctx->hsys[ctx->list_cf[0]].n;
   for (int s : ctx->list_cp) ctx->n_max_cp = std::max(ctx->n_max_cp, ctx->hsys[s].n);
@@ -333,6 +379,9 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(upload(ctx, &ctx->d_colidx, h_colidx));
   TRY(upload(ctx, &ctx->d_rowof, h_rowof));
   TRY(upload(ctx, &ctx->d_sys, ctx->hsys));
+  TRY(upload(ctx, &ctx->d_sys_chol, ctx->hsys_chol));
+  TRY(dalloc(ctx, &ctx->d_flags, (size_t)ctx->nsys * ctx->flags_stride));
+  CK(cudaMemset(ctx->d_flags, 0, (size_t)ctx->nsys * ctx->flags_stride * sizeof(int)));
   TRY(upload(ctx, &ctx->d_chol, ctx->hchol));
   TRY(upload(ctx, &ctx->d_list_osl, ctx->list_osl));
   TRY(upload(ctx, &ctx->d_list_cf, ctx->list_cf));
@@ -350,15 +399,20 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(dalloc(ctx, &ctx->d_status, ctx->nsys));
   CK(cudaMemset(ctx->d_status, 0, ctx->nsys * sizeof(int)));
   if (ctx->prec == TPNS_FP64) {
-    double* b;
+    double *b, *d;
     TRY(dalloc(ctx, &b, ctx->band_local_len));
+    TRY(dalloc(ctx, &d, ctx->dinv_local_len));
     ctx->d_band_local = b;
+    ctx->d_dinv_local = d;
   } else {
-    float* b;
+    float *b, *d;
     TRY(dalloc(ctx, &b, ctx->band_local_len));
+    TRY(dalloc(ctx, &d, ctx->dinv_local_len));
     ctx->d_band_local = b;
+    ctx->d_dinv_local = d;
   }
   TRY(dalloc(ctx, &ctx->d_band_coarse, ctx->band_coarse_len));
+  TRY(dalloc(ctx, &ctx->d_dinv_coarse, ctx->dinv_coarse_len));
   TRY(dalloc(ctx, &ctx->d_Ke, (size_t)(ctx->ne_osl + ctx->ne_cf) * 225));
   TRY(dalloc(ctx, &ctx->d_Re, (size_t)(ctx->ne_osl + ctx->ne_cf) * 15));
   TRY(dalloc(ctx, &ctx->d_ReD, (size_t)(ctx->ne_dl + ctx->ne_cp) * 18));
@@ -497,6 +551,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   CK(cudaMemcpy(ctx->d_pc_new, pc.data(), pc.size() * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_pd_old, pdl.data(), pdl.size() * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_pd_new, pdl.data(), pdl.size() * 8, cudaMemcpyHostToDevice));
+  ctx->stats.h2d_bytes += (int64_t)(2 * uc.size() + pc.size() + 2 * pdl.size()) * 8;
   // fine interpolants of the coarse initial data (host, same tables as the device)
   std::vector<double> Iuh((size_t)nnc * 2, 0.0), Ipdh((size_t)nnp * 3, 0.0);
   for (int i = 0; i < nnc; ++i)
@@ -536,6 +591,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       }
     }
     CK(cudaMemcpy(state[p], e0.data(), e0.size() * 8, cudaMemcpyHostToDevice));
+    ctx->stats.h2d_bytes += (int64_t)e0.size() * 8;
   }
   int64_t zero64 = 0;
   CK(cudaMemcpy(ctx->d_step, &zero64, 8, cudaMemcpyHostToDevice));
@@ -557,6 +613,43 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   return TPNS_OK;
 }
 
+// ------------------------------------------------------------------------------ timing
+static cudaEvent_t ev_get(tpns_ctx* ctx) {
+  if (ctx->ev_pool.empty()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t e = ctx->ev_pool.back();
+  ctx->ev_pool.pop_back();
+  return e;
+}
+static void ph_begin(tpns_ctx* ctx, int id) {
+  if (!ctx->timing) return;
+  cudaEvent_t e = ev_get(ctx);
+  cudaEventRecord(e, ctx->stream);
+  ctx->ev_open[id] = e;
+}
+static void ph_end(tpns_ctx* ctx, int id) {
+  if (!ctx->timing || !ctx->ev_open[id]) return;
+  cudaEvent_t e = ev_get(ctx);
+  cudaEventRecord(e, ctx->stream);
+  ctx->ev_pending.push_back({id, {ctx->ev_open[id], e}});
+  ctx->ev_open[id] = nullptr;
+}
+static void ph_collect(tpns_ctx* ctx) {
+  for (auto& p : ctx->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+      ctx->ph_ms[p.first] += ms;
+      ctx->ph_n[p.first] += 1;
+    }
+    ctx->ev_pool.push_back(p.second.first);
+    ctx->ev_pool.push_back(p.second.second);
+  }
+  ctx->ev_pending.clear();
+}
+
 // ------------------------------------------------------------------------------ step
 static tpns_status prolong_and_glue(tpns_ctx* ctx) {
   const Layout& L = ctx->L;
@@ -576,8 +669,8 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
   double* ReCP = ctx->d_ReD + ctx->ne_dl * 18;
   CK(launch_darcy_elem(ctx->asmargs, ctx->e_off[CP], ctx->ne_cp, ReCP, nullptr, st));
   CK(launch_seg_reduce(ctx->d_rcp_t, ctx->d_rcp_s, ctx->n_rcp, ReCP, ctx->d_b, st, nullptr));
-  CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cp, ctx->d_chol, 3, ctx->n_max_cp, ctx->d_band_coarse, ctx->d_b,
-                               ctx->d_x, 0, nullptr, st, nullptr));
+  CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->n_max_cp, ctx->kmax_cp, ctx->d_band_coarse, ctx->d_dinv_coarse,
+                               ctx->d_b, ctx->d_x, 0, nullptr, st, nullptr));
   CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cp, ctx->nn_cp, ctx->d_x, st, nullptr));
   // Step 1(2): coarse conduit problem (eq. pcFully) by Newton's method
   CK(cudaMemcpyAsync(ctx->d_uc_new, ctx->d_uc_old, (size_t)L.mcH.nn * 2 * 8, cudaMemcpyDeviceToDevice, st));
@@ -590,10 +683,10 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
     CK(launch_seg_reduce(ctx->d_rcf_t, ctx->d_rcf_s, ctx->n_rcf, ctx->d_Re, ctx->d_b, st, skip));
     CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
                                 ctx->d_band_coarse, 0, 0, st, skip));
-    CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse, nullptr,
-                              ctx->d_status, st, skip));
-    CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cf, ctx->d_chol, 1, ctx->n_max_cf, ctx->d_band_coarse,
-                                 ctx->d_b, ctx->d_x, 0, nullptr, st, skip));
+    CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse, ctx->d_dinv_coarse,
+                              ctx->d_flags, ctx->flags_stride, ++ctx->lu_epoch, ctx->d_status, st, skip));
+    CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->n_max_cf, ctx->kmax_cf, ctx->d_band_coarse,
+                                 ctx->d_dinv_coarse, ctx->d_b, ctx->d_x, 0, nullptr, st, skip));
     CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cf, ctx->nn_cf, ctx->d_x, st, skip));
     CK(launch_newton_update(ctx->d_probs + CF, ctx->d_gnode, ctx->d_vloc, L.cfl.nn, L.cfl.nvl, ctx->d_uc_new,
                             ctx->d_pc_new, ctx->d_newton_done, ctx->d_newton_iters, st));
@@ -605,48 +698,75 @@ template <typename T>
 static tpns_status local_step(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   T* band = reinterpret_cast<T*>(ctx->d_band_local);
+  T* dinv = reinterpret_cast<T*>(ctx->d_dinv_local);
   const int nosl = (int)ctx->list_osl.size(), nloc = (int)ctx->list_local.size();
   // a1: coarse fields on the fine meshes
+  ph_begin(ctx, PH_PROLONG);
   TRY(prolong_and_glue(ctx));
+  ph_end(ctx, PH_PROLONG);
   // a2-a3: Oseen matrices and right-hand sides of all conduit subdomains
+  ph_begin(ctx, PH_ASM_OSEEN);
   CK(launch_oseen_elem(ctx->asmargs, 0, ctx->ne_osl, ctx->d_Ke, ctx->d_Re, st, nullptr));
+  ph_end(ctx, PH_ASM_OSEEN);
+  ph_begin(ctx, PH_SCATTER);
   CK(launch_seg_reduce(ctx->d_mo_t, ctx->d_mo_s, ctx->n_mo, ctx->d_Ke, ctx->d_vals, st, nullptr));
   CK(launch_seg_reduce(ctx->d_ro_t, ctx->d_ro_s, ctx->n_ro, ctx->d_Re, ctx->d_b, st, nullptr));
+  ph_end(ctx, PH_SCATTER);
   // a4: Darcy right-hand sides of all porous subdomains
+  ph_begin(ctx, PH_ASM_DARCY);
   CK(launch_darcy_elem(ctx->asmargs, ctx->eD0, ctx->ne_dl, ctx->d_ReD, nullptr, st));
   CK(launch_seg_reduce(ctx->d_rd_t, ctx->d_rd_s, ctx->n_rd, ctx->d_ReD, ctx->d_b, st, nullptr));
+  ph_end(ctx, PH_ASM_DARCY);
   // a6: band LU of every Oseen system
+  ph_begin(ctx, PH_BAND_FILL);
   CK(launch_band_fill<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 0, 0, st,
                          nullptr));
-  CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, nullptr, ctx->d_status, st, nullptr));
+  ph_end(ctx, PH_BAND_FILL);
+  ph_begin(ctx, PH_BAND_LU);
+  CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, dinv, ctx->d_flags, ctx->flags_stride,
+                       ++ctx->lu_epoch, ctx->d_status, st, nullptr));
+  ph_end(ctx, PH_BAND_LU);
   // a8: solves with FP64-residual iterative refinement
   const bool fp64 = ctx->prec == TPNS_FP64;
   const int maxit = fp64 ? 2 : 12;
   const double tol = fp64 ? 1e-14 : 1e-13;
+  ph_begin(ctx, PH_RESIDUAL);
   CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
                      ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, tol, 1, st, nullptr));
-  CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, ctx->d_chol, nloc, ctx->n_max_local, band, ctx->d_b, ctx->d_x,
-                          0, nullptr, st, nullptr));
+  ph_end(ctx, PH_RESIDUAL);
+  ph_begin(ctx, PH_SOLVE);
+  CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, band, dinv, ctx->d_b, ctx->d_x, 0,
+                          nullptr, st, nullptr));
+  ph_end(ctx, PH_SOLVE);
   for (int it = 0; it < maxit; ++it) {
+    ph_begin(ctx, PH_RESIDUAL);
     CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
                        ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, tol, 0, st, nullptr));
-    if (it + 1 < maxit)
-      CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, ctx->d_chol, nloc, ctx->n_max_local, band, ctx->d_r,
-                              ctx->d_x, 1, ctx->d_done, st, nullptr));
+    ph_end(ctx, PH_RESIDUAL);
+    if (it + 1 < maxit) {
+      ph_begin(ctx, PH_SOLVE);
+      CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, band, dinv, ctx->d_r, ctx->d_x, 1,
+                              ctx->d_done, st, nullptr));
+      ph_end(ctx, PH_SOLVE);
+    }
   }
   // a9: new corrections and glue
+  ph_begin(ctx, PH_STATE_GLUE);
   CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_fl, ctx->nn_fl, ctx->d_x, st, nullptr));
   CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_pl, ctx->nn_pl, ctx->d_x, st, nullptr));
   CK(launch_glue(ctx->glue, st));
+  ph_end(ctx, PH_STATE_GLUE);
   return TPNS_OK;
 }
 
 static tpns_status end_step(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   const Layout& L = ctx->L;
+  ph_begin(ctx, PH_COPIES);
   CK(cudaMemcpyAsync(ctx->d_uc_old, ctx->d_uc_new, (size_t)L.mcH.nn * 2 * 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(ctx->d_pd_old, ctx->d_pd_new, (size_t)L.mpH.nn * 3 * 8, cudaMemcpyDeviceToDevice, st));
   CK(launch_set_time(ctx->d_tnow, ctx->d_step, ctx->dt, 1, st));
+  ph_end(ctx, PH_COPIES);
   ctx->step += 1;
   return TPNS_OK;
 }
@@ -656,6 +776,7 @@ static tpns_status read_stats(tpns_ctx* ctx) {
   std::vector<double> rel(ctx->nsys);
   int nit = 0;
   CK(cudaStreamSynchronize(ctx->stream));
+  ph_collect(ctx);
   CK(cudaMemcpy(it.data(), ctx->d_iters, ctx->nsys * sizeof(int), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(rel.data(), ctx->d_rel, ctx->nsys * sizeof(double), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(stt.data(), ctx->d_status, ctx->nsys * sizeof(int), cudaMemcpyDeviceToHost));
@@ -699,7 +820,9 @@ static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
       CK(cudaMemcpyAsync(ctx->d_pc_new, ctx->traj[k + 1] + nu, npc * 8, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(ctx->d_pd_new, ctx->traj[k + 1] + nu + npc, npd * 8, cudaMemcpyDeviceToDevice, st));
     } else {
+      ph_begin(ctx, PH_COARSE);
       TRY(coarse_step(ctx));
+      ph_end(ctx, PH_COARSE);
     }
     if (ctx->prec == TPNS_FP64) TRY(local_step<double>(ctx));
     else TRY(local_step<float>(ctx));
@@ -736,20 +859,37 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
   CK(launch_darcy_elem(ctx->asmargs, ctx->eD0, neD, nullptr, KeD, st));
   CK(launch_seg_reduce(dt1, ds1, (int64_t)t1.size(), KeD, ctx->d_vals, st, nullptr));
   const int ndl = (int)ctx->list_dl.size();
+  // one-time band Cholesky of every Darcy system, rewritten as unit-L / U factors
+  {
+    double* cband;
+    TRY(dalloc(ctx, &cband, ctx->band_chol_coarse_len));
+    CK(launch_band_fill<double>(ctx->d_sys_chol, ctx->d_list_cp, 3, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, cband, 1,
+                                0, st, nullptr));
+    CK(launch_band_chol<double>(ctx->d_sys_chol, ctx->d_list_cp, 3, cband, ctx->d_status, st));
+    CK(launch_chol_to_lu<double>(ctx->d_sys_chol, ctx->d_sys, ctx->d_list_cp, 3, cband, ctx->d_band_coarse, st));
+    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->d_band_coarse, ctx->d_dinv_coarse, st));
+  }
   if (ctx->prec == TPNS_FP64) {
     double* band = reinterpret_cast<double*>(ctx->d_band_local);
-    CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_dl, ndl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 1, 0,
-                                st, nullptr));
-    CK(launch_band_chol<double>(ctx->d_sys, ctx->d_list_dl, ndl, band, ctx->d_status, st));
+    double* dinv = reinterpret_cast<double*>(ctx->d_dinv_local);
+    double* cband;
+    TRY(dalloc(ctx, &cband, ctx->band_chol_local_len));
+    CK(launch_band_fill<double>(ctx->d_sys_chol, ctx->d_list_dl, ndl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, cband, 1,
+                                0, st, nullptr));
+    CK(launch_band_chol<double>(ctx->d_sys_chol, ctx->d_list_dl, ndl, cband, ctx->d_status, st));
+    CK(launch_chol_to_lu<double>(ctx->d_sys_chol, ctx->d_sys, ctx->d_list_dl, ndl, cband, band, st));
+    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_dl, ndl, band, dinv, st));
   } else {
     float* band = reinterpret_cast<float*>(ctx->d_band_local);
-    CK(launch_band_fill<float>(ctx->d_sys, ctx->d_list_dl, ndl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 1, 0,
-                               st, nullptr));
-    CK(launch_band_chol<float>(ctx->d_sys, ctx->d_list_dl, ndl, band, ctx->d_status, st));
+    float* dinv = reinterpret_cast<float*>(ctx->d_dinv_local);
+    float* cband;
+    TRY(dalloc(ctx, &cband, ctx->band_chol_local_len));
+    CK(launch_band_fill<float>(ctx->d_sys_chol, ctx->d_list_dl, ndl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, cband, 1,
+                               0, st, nullptr));
+    CK(launch_band_chol<float>(ctx->d_sys_chol, ctx->d_list_dl, ndl, cband, ctx->d_status, st));
+    CK(launch_chol_to_lu<float>(ctx->d_sys_chol, ctx->d_sys, ctx->d_list_dl, ndl, cband, band, st));
+    CK(launch_band_dinv<float>(ctx->d_sys, ctx->d_list_dl, ndl, band, dinv, st));
   }
-  CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
-                              ctx->d_band_coarse, 1, 0, st, nullptr));
-  CK(launch_band_chol<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->d_band_coarse, ctx->d_status, st));
   // initial glued fields
   TRY(prolong_and_glue(ctx));
   CK(launch_glue(ctx->glue, st));
@@ -813,15 +953,50 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   return TPNS_OK;
 }
 
+tpns_status tpns_layout_create(const tpns_mesh_desc* mesh, const tpns_partition_desc* part, tpns_ctx** out) {
+  g_err.clear();
+  if (!out || !mesh || !part) { g_err = "NULL argument"; return TPNS_EINVAL; }
+  *out = nullptr;
+  tpns_ctx* ctx = new (std::nothrow) tpns_ctx();
+  if (!ctx) return TPNS_ENOMEM;
+  ctx->host_only = true;
+  std::string msg = build_layout(*mesh, *part, ctx->L);
+  if (!msg.empty()) {
+    g_err = msg;
+    delete ctx;
+    return TPNS_EINVAL;
+  }
+  ctx->nf = (int)ctx->L.fluid.size();
+  ctx->np = (int)ctx->L.porous.size();
+  *out = ctx;
+  return TPNS_OK;
+}
+
+tpns_status tpns_debug_values(tpns_ctx* ctx, int32_t j, int32_t field, double* vals, double* rhs) {
+  if (!ctx || ctx->host_only) return TPNS_EINVAL;
+  int p;
+  if (j >= 0 && j < ctx->nf) p = j;
+  else if (j >= ctx->nf && j < ctx->nf + ctx->np) p = j + 1;   // skip the coarse conduit problem
+  else return TPNS_EINVAL;
+  const Problem& P = *ctx->probs[p];
+  const int f = P.kind == PK_OSEEN ? 0 : field;
+  if (f < 0 || f > 2) return TPNS_EINVAL;
+  const SysDev& S = ctx->hsys[ctx->sys_first[p] + f];
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (vals) CK(cudaMemcpy(vals, ctx->d_vals + S.val_off, S.nnz * sizeof(double), cudaMemcpyDeviceToHost));
+  if (rhs) CK(cudaMemcpy(rhs, ctx->d_b + S.x_off, S.n * sizeof(double), cudaMemcpyDeviceToHost));
+  return TPNS_OK;
+}
+
 tpns_status tpns_step(tpns_ctx* ctx, int32_t nsteps) {
-  if (!ctx || nsteps < 0) return TPNS_EINVAL;
+  if (!ctx || nsteps < 0 || ctx->host_only) return TPNS_EINVAL;
   ctx->err.clear();
   ctx->traj_base = -1000000000;
   return run_steps(ctx, nsteps, false);
 }
 
 tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps) {
-  if (!ctx || nsteps < 0) return TPNS_EINVAL;
+  if (!ctx || nsteps < 0 || ctx->host_only) return TPNS_EINVAL;
   ctx->err.clear();
   const Layout& L = ctx->L;
   size_t nu = (size_t)L.mcH.nn * 2, npc = L.mcH.nv, npd = (size_t)L.mpH.nn * 3;
@@ -870,7 +1045,7 @@ tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps) {
 }
 
 tpns_status tpns_local_step(tpns_ctx* ctx, int32_t nsteps) {
-  if (!ctx || nsteps < 0) return TPNS_EINVAL;
+  if (!ctx || nsteps < 0 || ctx->host_only) return TPNS_EINVAL;
   ctx->err.clear();
   cudaStream_t st = ctx->stream;
   CK(launch_set_time(ctx->d_tnow, ctx->d_step, ctx->dt, 0, st));
@@ -889,7 +1064,7 @@ tpns_status tpns_num_dofs(const tpns_ctx* ctx, int32_t field, size_t* n) {
 }
 
 tpns_status tpns_get_field(tpns_ctx* ctx, int32_t field, double* dst, size_t n, int32_t dst_on_device) {
-  if (!ctx || !dst) return TPNS_EINVAL;
+  if (!ctx || !dst || ctx->host_only) return TPNS_EINVAL;
   size_t need = 0;
   if (tpns_num_dofs(ctx, field, &need) != TPNS_OK || n < need) {
     ctx->err = "destination too small or bad field";
@@ -923,11 +1098,30 @@ tpns_status tpns_get_stats(tpns_ctx* ctx, tpns_stats* out) {
 tpns_status tpns_batch_step(tpns_ctx** ctxs, int32_t n) {
   if (!ctxs || n < 0) return TPNS_EINVAL;
   for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return TPNS_EINVAL;
     tpns_status s = tpns_step(ctxs[i], 1);
     if (s != TPNS_OK) return s;
   }
   return TPNS_OK;
 }
+
+tpns_status tpns_set_timing(tpns_ctx* ctx, int32_t on) {
+  if (!ctx || ctx->host_only) return TPNS_EINVAL;
+  ctx->timing = on != 0;
+  for (int i = 0; i < PH_COUNT; ++i) { ctx->ph_ms[i] = 0; ctx->ph_n[i] = 0; }
+  return TPNS_OK;
+}
+
+tpns_status tpns_get_timings(const tpns_ctx* ctx, double* ms, int64_t* count, int32_t n) {
+  if (!ctx || n < 0) return TPNS_EINVAL;
+  for (int i = 0; i < n && i < PH_COUNT; ++i) {
+    if (ms) ms[i] = ctx->ph_ms[i];
+    if (count) count[i] = ctx->ph_n[i];
+  }
+  return TPNS_OK;
+}
+
+int64_t tpns_launch_count(void) { return tpns::launch_counter(); }
 
 const char* tpns_last_error(const tpns_ctx* ctx) {
   if (!ctx) return g_err.c_str();
@@ -937,6 +1131,8 @@ const char* tpns_last_error(const tpns_ctx* ctx) {
 void tpns_destroy(tpns_ctx* ctx) {
   if (!ctx) return;
   for (void* p : ctx->allocs) cudaFree(p);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto& p : ctx->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
   for (double* p : ctx->traj) {
     (void)p;
   }

@@ -7,6 +7,10 @@
 
 namespace tpns {
 
+// number of kernel launches issued by this library since it was loaded
+int64_t launch_counter();
+void count_launches(int n);
+
 constexpr int LU_NB = 32;        // panel width of the band LU and block size of the solves
 constexpr int LU_CLUSTER = 8;    // CTAs per system in the band LU
 
@@ -16,16 +20,23 @@ cudaError_t launch_band_fill(const SysDev* sys, const int* sys_list, int nsys, c
                              const int32_t* colidx, const double* vals, T* band, int chol,
                              int64_t total_nnz_hint, cudaStream_t st, const int* skip);
 template <typename T>
-cudaError_t launch_band_lu(const SysDev* sys, const int* sys_list, int nsys, int kl_max, T* band,
-                           T* dinv, int* status, cudaStream_t st, const int* skip);
+cudaError_t launch_band_lu(const SysDev* sys, const int* sys_list, int nsys, int kl_max, T* band, T* dinv,
+                           int* flags, int flags_stride, int epoch, int* status, cudaStream_t st,
+                           const int* skip);
+template <typename T>
+cudaError_t launch_band_dinv(const SysDev* sys, const int* sys_list, int nsys, const T* band, T* dinv,
+                             cudaStream_t st);
 template <typename T>
 cudaError_t launch_band_chol(const SysDev* sys, const int* sys_list, int nsys, T* band, int* status,
                              cudaStream_t st);
-// x (+)= (LU)^{-1} r  (mode per system: sys_chol[s] = 1 for Cholesky storage)
 template <typename T>
-cudaError_t launch_band_solve(const SysDev* sys, const int* sys_list, const int* sys_chol, int nsys,
-                              int n_max, const T* band, const double* r, double* x, int accumulate,
-                              const int* done, cudaStream_t st, const int* skip);
+cudaError_t launch_chol_to_lu(const SysDev* sys_chol, const SysDev* sys_lu, const int* list, int nsys,
+                              const T* cband, T* lband, cudaStream_t st);
+// x (+)= U^{-1} L^{-1} r with the stored diagonal-block inverses
+template <typename T>
+cudaError_t launch_band_solve(const SysDev* sys, const int* sys_list, int nsys, int n_max, int kmax,
+                              const T* band, const T* dinv, const double* r, double* x, int accumulate, const int* done,
+                              cudaStream_t st, const int* skip);
 // r = b - A x in FP64, convergence bookkeeping (relative residual <= tol, or stagnation)
 cudaError_t launch_residual(const SysDev* sys, const int* sys_list, int nsys, const int32_t* rowptr,
                             const int32_t* colidx, const double* vals, const double* b,

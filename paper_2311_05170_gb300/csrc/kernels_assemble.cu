@@ -5,12 +5,17 @@
 // use reference-element integrals (computed once by the degree-5 rule), so they are exact;
 // forcing and interface data are integrated with the 7-point (cells) and 3-point (edges)
 // rules at run time.
+#include <atomic>
 #include <cmath>
 
 #include "kernels.hpp"
 #include "setup.hpp"
 
 namespace tpns {
+
+static std::atomic<int64_t> g_launches{0};
+int64_t launch_counter() { return g_launches.load(); }
+void count_launches(int n) { g_launches.fetch_add(n); }
 
 namespace {
 
@@ -218,6 +223,7 @@ cudaError_t launch_oseen_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, dou
                               cudaStream_t st, const int* skip) {
   if (ne <= 0) return cudaSuccess;
   int blocks = (int)((ne + 7) / 8);
+  count_launches(1);
   oseen_elem_kernel<<<blocks, 128, 0, st>>>(a, e_begin, ne, Ke, Re, skip);
   return cudaGetLastError();
 }
@@ -336,6 +342,7 @@ cudaError_t launch_darcy_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, dou
                               cudaStream_t st) {
   if (ne <= 0) return cudaSuccess;
   int blocks = (int)((ne * 3 + 127) / 128);
+  count_launches(1);
   darcy_elem_kernel<<<blocks, 128, 0, st>>>(a, e_begin, ne, Re, Ke);
   return cudaGetLastError();
 }
@@ -381,6 +388,7 @@ cudaError_t launch_seg_reduce(const int32_t* tgt, const int32_t* src, int64_t nl
                               double* out, cudaStream_t st, const int* skip) {
   if (nlanes <= 0) return cudaSuccess;
   int blocks = (int)((nlanes + 255) / 256);
+  count_launches(1);
   seg_reduce_kernel<<<blocks, 256, 0, st>>>(tgt, src, nlanes, in, out, skip);
   return cudaGetLastError();
 }
@@ -435,6 +443,7 @@ __global__ void state_kernel(AsmArgs A, const int32_t* __restrict__ nprob, const
 cudaError_t launch_state(const AsmArgs& a, const int32_t* nprob, const int32_t* nvidx, int64_t n_begin,
                          int64_t nn, const double* x, cudaStream_t st, const int* skip) {
   if (nn <= 0) return cudaSuccess;
+  count_launches(1);
   state_kernel<<<(int)((nn + 255) / 256), 256, 0, st>>>(a, nprob, nvidx, n_begin, nn, x, skip);
   return cudaGetLastError();
 }
@@ -490,6 +499,7 @@ cudaError_t launch_prolong(int n2c, int n1c, int n2p, const int32_t* pc2i, const
                            const double* pd_new, const double* pd_old, int64_t nnpH, double* FW1, double* FW0,
                            double* FP1, double* FPD1, double* FPD0, int64_t nnp, cudaStream_t st) {
   int n = n2c > n2p ? n2c : n2p;
+  count_launches(1);
   prolong_kernel<<<(n + 255) / 256, 256, 0, st>>>(n2c, n1c, n2p, pc2i, pc2w, pc1i, pc1w, pp2i, pp2w, uc_new,
                                                    uc_old, pc_new, pd_new, pd_old, nnpH, FW1, FW0, FP1, FPD1,
                                                    FPD0, nnp);
@@ -534,6 +544,7 @@ __global__ void glue_kernel(GlueArgs G) {
 
 cudaError_t launch_glue(const GlueArgs& g, cudaStream_t st) {
   int n = g.nnc > g.nnp ? g.nnc : g.nnp;
+  count_launches(1);
   glue_kernel<<<(n + 255) / 256, 256, 0, st>>>(g);
   return cudaGetLastError();
 }
@@ -584,6 +595,7 @@ __global__ void __launch_bounds__(256) newton_update_kernel(const ProbDev* __res
 
 cudaError_t launch_newton_update(const ProbDev* prob, const int32_t* gnode, const int32_t* vloc, int nn, int nvl,
                                  double* u, double* p, int* done, int* iters, cudaStream_t st) {
+  count_launches(1);
   newton_update_kernel<<<1, 256, 0, st>>>(prob, gnode, vloc, nn, nvl, u, p, done, iters);
   return cudaGetLastError();
 }
@@ -594,6 +606,7 @@ __global__ void set_time_kernel(double* tnow, int64_t* step, double dt, int adva
 }
 
 cudaError_t launch_set_time(double* tnow, int64_t* step, double dt, int advance, cudaStream_t st) {
+  count_launches(1);
   set_time_kernel<<<1, 1, 0, st>>>(tnow, step, dt, advance);
   return cudaGetLastError();
 }

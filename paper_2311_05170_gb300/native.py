@@ -38,7 +38,7 @@ class DataDesc(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("last_ir_iters_max", C.c_int32), ("last_newton_iters", C.c_int32),
                 ("last_ir_relres_max", C.c_double), ("n_fine_dofs", C.c_int64), ("n_local_systems", C.c_int64),
-                ("device_bytes", C.c_int64), ("band_lu_flops", C.c_double)]
+                ("device_bytes", C.c_int64), ("band_lu_flops", C.c_double), ("h2d_bytes", C.c_int64)]
 
 
 class TpnsError(RuntimeError):
@@ -51,7 +51,11 @@ _lib = None
 
 EXPORTS = ["tpns_create", "tpns_step", "tpns_coarse_precompute", "tpns_local_step", "tpns_num_dofs",
            "tpns_get_field", "tpns_get_stats", "tpns_batch_step", "tpns_last_error", "tpns_destroy",
-           "tpns_debug_mesh", "tpns_debug_system"]
+           "tpns_debug_mesh", "tpns_debug_system", "tpns_set_timing", "tpns_get_timings", "tpns_launch_count",
+           "tpns_layout_create", "tpns_debug_values"]
+
+PHASES = ["coarse", "prolong", "asm_oseen", "scatter", "asm_darcy", "band_fill", "band_lu", "solve", "residual",
+          "state_glue", "copies"]
 
 
 def load(path=LIB_PATH):
@@ -86,6 +90,16 @@ def load(path=LIB_PATH):
     I32 = C.POINTER(C.c_int32)
     lib.tpns_debug_system.argtypes = [P, C.c_int32, I32, I32, I32, C.POINTER(C.c_int64), I32, I32, I32, I32]
     lib.tpns_debug_system.restype = C.c_int
+    lib.tpns_set_timing.argtypes = [P, C.c_int32]
+    lib.tpns_set_timing.restype = C.c_int
+    lib.tpns_get_timings.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]
+    lib.tpns_get_timings.restype = C.c_int
+    lib.tpns_launch_count.argtypes = []
+    lib.tpns_launch_count.restype = C.c_int64
+    lib.tpns_layout_create.argtypes = [C.POINTER(MeshDesc), C.POINTER(PartitionDesc), C.POINTER(P)]
+    lib.tpns_layout_create.restype = C.c_int
+    lib.tpns_debug_values.argtypes = [P, C.c_int32, C.c_int32, P, P]
+    lib.tpns_debug_values.restype = C.c_int
     _lib = lib
     return lib
 
@@ -114,13 +128,17 @@ FIELD_IDS = {"ux": 0, "uy": 1, "p": 2, "pF": 3, "pf": 4, "pm": 5}
 
 
 class Solver:
-    """One simulation context on the current CUDA device."""
+    """One simulation context on the current CUDA device (host_only=True: layout only)."""
 
-    def __init__(self, w, precision="fp64", hbm_budget_bytes=0, stream=None):
+    def __init__(self, w, precision="fp64", hbm_budget_bytes=0, stream=None, host_only=False):
         self.lib = load()
         self.w = w
         md, pr, pd, dd = descriptors(w)
         ctx = C.c_void_p()
+        if host_only:
+            _check(self.lib, None, self.lib.tpns_layout_create(C.byref(md), C.byref(pd), C.byref(ctx)))
+            self.ctx = ctx
+            return
         st = C.c_void_p(stream) if stream else None
         s = self.lib.tpns_create(C.byref(md), C.byref(pr), C.byref(pd), C.byref(dd), float(w.dt),
                                  PRECISIONS[precision], int(hbm_budget_bytes), st, C.byref(ctx))
@@ -186,6 +204,24 @@ class Solver:
                                                     ci.ctypes.data_as(I32), None, None))
         return {"node": node, "comp": comp, "rowptr": rp, "colidx": ci, "kl": kl.value, "ku": ku.value}
 
+    def set_timing(self, on=True):
+        _check(self.lib, self.ctx, self.lib.tpns_set_timing(self.ctx, 1 if on else 0))
+
+    def timings(self):
+        """Per-phase totals {phase: (ms, intervals)} measured with CUDA events."""
+        n = len(PHASES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        _check(self.lib, self.ctx, self.lib.tpns_get_timings(self.ctx, ms, cnt, n))
+        return {PHASES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    def debug_values(self, j, field=0):
+        info = self.debug_system(j)
+        vals = np.empty(len(info["colidx"]), np.float64)
+        rhs = np.empty(len(info["node"]), np.float64)
+        _check(self.lib, self.ctx, self.lib.tpns_debug_values(self.ctx, j, field, vals.ctypes.data, rhs.ctypes.data))
+        return vals, rhs
+
     def close(self):
         if getattr(self, "ctx", None):
             self.lib.tpns_destroy(self.ctx)
@@ -196,6 +232,10 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def launch_count():
+    return load().tpns_launch_count()
 
 
 def batch_step(solvers):

@@ -1,0 +1,158 @@
+"""GPU parity of the native library against the CPU oracle (same seeded inputs).
+
+Tolerances (per field, relative L2 over the global fine dofs): 1e-10 for the FP64 path,
+1e-8 for FP32 factors with FP64-residual refinement.  Both sides integrate the
+transcendental data with the same quadrature rules, so the only differences are rounding
+orders and the refinement's stopping point."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.scheme import TwoGridOracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-8}
+
+
+@pytest.fixture(scope="module")
+def native():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for the gpu tests")
+    from paper_2311_05170_gb300 import build
+    build.build()
+    from paper_2311_05170_gb300 import native as N
+    N.load()
+    return N
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_pair(native, w, prec, nsteps):
+    o = TwoGridOracle(w)
+    s = native.Solver(w, precision=prec)
+    f0 = s.fields()
+    for k in f0:
+        assert rel(f0[k], o.fine[k]) < 1e-13, ("initial", k)
+    o.run(nsteps)
+    s.step(nsteps)
+    f = s.fields()
+    stats = s.stats()
+    s.close()
+    return f, o, stats
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_patch_field_exact_on_gpu(native, prec):
+    w = W.config_patch(nx_coarse=2, r=2, nsub=(2, 2), nsteps=3)
+    f, o, _ = run_pair(native, w, prec, 3)
+    ex = o.exact_fine()
+    for k in f:
+        assert np.abs(f[k] - ex[k]).max() < 1e-11, k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_2d_parity(native, prec):
+    w = W.config_small(nsteps=10)
+    f, o, stats = run_pair(native, w, prec, 10)
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))
+    assert stats["last_ir_relres_max"] <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graded_full_size_parity(native, prec):
+    """The bench workload at full size (130,966 fine dofs, 16 + 48 local systems of 1.4k to
+    8.3k unknowns), three steps."""
+    w = W.config_graded(nsteps=3)
+    f, o, stats = run_pair(native, w, prec, 3)
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))
+    assert stats["n_fine_dofs"] == 130966 and stats["n_local_systems"] == 64
+
+
+@pytest.mark.parametrize("w", [W.config_uniform(4, 2, nsub=(1, 1), overlap=1, nsteps=3),
+                               W.config_uniform(8, 2, nsub=(4, 2), overlap=3, nsteps=3),
+                               W.config_uniform(4, 1, nsub=(2, 2), overlap=1, nsteps=3)],
+                         ids=["single_subdomain", "uneven_4x2", "H_equals_h"])
+def test_edge_layouts_parity(native, w):
+    f, o, _ = run_pair(native, w, "fp32", 3)
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= 1e-8, k
+
+
+def test_assembled_systems_match_oracle(native):
+    """FP64 CSR values and right-hand sides of the local systems after one step equal
+    the oracle's assembled matrices (keyed by global node and component)."""
+    w = W.config_small(nsteps=1)
+    o = TwoGridOracle(w)
+    d = o.step_inputs()
+    s = native.Solver(w, precision="fp64")
+    s.step(1)
+    for j in range(len(o.sub_c) + len(o.sub_p)):
+        info = s.debug_system(j)
+        if j < len(o.sub_c):
+            sub, O = o.sub_c[j]
+            Aff, b, free, _ = o.local_fluid_system(j, d["t"], d["uH1h"], d["uH0h"], d["pH1h"], d["pFn_c"])
+            nn = len(sub.gnode)
+            key = [(int(sub.gnode[q // 2]), q % 2) if q < 2 * nn else (int(sub.gvert[q - 2 * nn]), 2) for q in free]
+            fields = [0]
+        else:
+            sub, O = o.sub_p[j - len(o.sub_c)]
+            fields = [0, 1, 2]
+        for fld in fields:
+            if j >= len(o.sub_c):
+                Aff, b, free, _ = o.local_porous_system(j - len(o.sub_c), fld, d["t"], d["pdH1h"], d["pdH0h"], d["ucn_p"])
+                key = [(int(sub.gnode[q]), 0) for q in free]
+            pos = {k: i for i, k in enumerate(key)}
+            perm = np.array([pos[(int(g), int(c))] for g, c in zip(info["node"], info["comp"])])
+            vals, rhs = s.debug_values(j, fld)
+            A = Aff.tocsr()
+            rows = np.repeat(np.arange(len(perm)), np.diff(info["rowptr"]))
+            ref_vals = np.asarray(A[perm[rows], perm[info["colidx"]]]).ravel()
+            scale = np.abs(ref_vals).max()
+            assert np.abs(vals - ref_vals).max() <= 1e-13 * scale, (j, fld)
+            assert np.abs(rhs - b[perm]).max() <= 1e-12 * max(np.abs(b).max(), 1e-300), (j, fld)
+            # every CSR entry of the oracle is present in the library's pattern
+            assert abs(A.sum() - vals.sum()) <= 1e-12 * np.abs(A).sum()
+    s.close()
+
+
+def test_deterministic_and_precomputed_coarse_path_bitwise(native):
+    """Two runs give bit-identical fields (no atomics anywhere), and running the local hot
+    path on precomputed coarse states gives bit-identical fields to full steps."""
+    w = W.config_small(nsteps=4)
+    a = native.Solver(w, precision="fp32")
+    a.step(4)
+    fa = a.fields()
+    a.close()
+    b = native.Solver(w, precision="fp32")
+    b.step(4)
+    fb = b.fields()
+    b.close()
+    c = native.Solver(w, precision="fp32")
+    c.coarse_precompute(4)
+    c.local_step(4)
+    fc = c.fields()
+    c.close()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+        assert np.array_equal(fa[k], fc[k]), k
+
+
+def test_refinement_statistics(native):
+    w = W.config_graded(nsteps=2)
+    s = native.Solver(w, precision="fp32")
+    s.step(2)
+    st = s.stats()
+    assert 1 <= st["last_ir_iters_max"] <= 12
+    assert st["last_ir_relres_max"] <= 1e-12
+    assert st["last_newton_iters"] >= 2
+    s.set_timing(True)
+    s.step(1)
+    t = s.timings()
+    assert t["band_lu"][1] == 1 and t["band_lu"][0] > 0
+    s.close()
