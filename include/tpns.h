@@ -180,6 +180,26 @@ tpns_status tpns_debug_system(const tpns_ctx* ctx, int32_t j, int32_t* n_unknown
                               int64_t* nnz, int32_t* rowptr, int32_t* colidx,
                               int32_t* kl, int32_t* ku);
 
+/* Standalone solve of one sparse system A x = b with the library's band solver (the
+ * factorisation and solves of Algorithm 3 Step 3): the CSR matrix is copied into band
+ * storage, factored by the unpivoted band LU (FP32 or FP64 factors), and x is obtained by
+ * triangular solves with FP64-residual iterative refinement (stop at ||b - A x|| <= 1e-13
+ * ||b||, on stagnation, or after 12 corrections).
+ *   n            unknowns; kl, ku: lower / upper bandwidth of A (every entry a_ij != 0 has
+ *                i - j <= kl and j - i <= ku); kl + 32 <= 512.
+ *   rowptr, colidx, vals, b, x: DEVICE pointers (CSR int32 / FP64, b and x FP64, n each);
+ *                x is overwritten.
+ *   precision    TPNS_FP64 or TPNS_FP32_IR; stream: cudaStream_t (NULL = legacy stream).
+ *   relres_out   host pointer or NULL: final ||b - A x|| / ||b||.
+ * Scratch (band, block inverses, vectors) is allocated with cudaMalloc for the call and
+ * freed before returning (the call synchronises the stream).  The ordering of the unknowns
+ * must make every leading block invertible (no pivoting); a zero or non-finite pivot
+ * returns TPNS_EBREAKDOWN. */
+tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* rowptr,
+                            const int32_t* colidx, const double* vals, const double* b,
+                            double* x, tpns_precision precision, void* cuda_stream,
+                            double* relres_out);
+
 /* Host-only context: builds meshes, subdomains, orderings and patterns (Algorithm 3 Step 2)
  * without touching a GPU, for the introspection calls above.  Every other call on it
  * returns TPNS_EINVAL.  Release with tpns_destroy. */

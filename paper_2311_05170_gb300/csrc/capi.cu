@@ -904,6 +904,89 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
   return TPNS_OK;
 }
 
+// ------------------------------------------------------------------------------ standalone solve
+__global__ void csr_rowof_kernel(const int32_t* __restrict__ rowptr, int n, int32_t* __restrict__ rowof) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) rowof[k] = i;
+}
+
+// Run the band solver on one system whose descriptors and scratch live at caller-chosen
+// device addresses (`sysd`: SysDev, `listd`: int 0, `vecs`: r, rel, relprev, done, iters,
+// status, flags).  The band and dinv buffers must hold n * (kl + ku + 1) and
+// ceil(n / 32) * 2048 elements of T.
+template <typename T>
+static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, const int32_t* colidx,
+                                  const double* vals, const double* b, double* x, cudaStream_t st, SysDev* sysd,
+                                  int* listd, int32_t* rowof, T* band, T* dinv, double* r, double* rel,
+                                  double* relprev, int* done, int* iters, int* status, int* flags, int epoch,
+                                  double* relres_out, std::string& err) {
+#define CKS(call)                                                           \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+      return TPNS_EDEVICE;                                                  \
+    }                                                                       \
+  } while (0)
+  int nnz = 0;
+  CKS(cudaMemcpyAsync(&nnz, rowptr + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+  SysDev S{};
+  S.n = n; S.kl = kl; S.ku = ku; S.ldab = kl + ku + 1;
+  S.band_off = 0; S.rp_off = 0; S.nnz_off = 0; S.nnz = nnz; S.val_off = 0; S.x_off = 0; S.dinv_off = 0;
+  const int zero = 0;
+  CKS(cudaMemcpyAsync(sysd, &S, sizeof(SysDev), cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(listd, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+  CKS(cudaMemsetAsync(status, 0, sizeof(int), st));
+  count_launches(1);
+  csr_rowof_kernel<<<(n + 255) / 256, 256, 0, st>>>(rowptr, n, rowof);
+  CKS(cudaGetLastError());
+  CKS(launch_band_fill<T>(sysd, listd, 1, rowof, colidx, vals, band, 0, 0, st, nullptr));
+  CKS(launch_band_lu<T>(sysd, listd, 1, kl, band, dinv, flags, (n + LU_NB - 1) / LU_NB, epoch, status, st, nullptr));
+  const bool fp64 = sizeof(T) == 8;
+  const int maxit = 12;
+  const double tol = fp64 ? 1e-14 : 1e-13;
+  const int kmax = std::max(kl, ku);
+  CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, tol, 1, st, nullptr));
+  CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, band, dinv, b, x, 0, nullptr, st, nullptr));
+  for (int it = 0; it < maxit; ++it) {
+    CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, tol, 0, st, nullptr));
+    if (it + 1 < maxit) CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, band, dinv, r, x, 1, done, st, nullptr));
+  }
+  int hst = 0;
+  double hrel = 0;
+  CKS(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKS(cudaMemcpyAsync(&hrel, rel, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+  if (relres_out) *relres_out = hrel;
+  if (hst) {
+    err = "zero or non-finite pivot";
+    return TPNS_EBREAKDOWN;
+  }
+  if (!(hrel <= 1e-9)) {
+    err = "iterative refinement stopped at relative residual " + std::to_string(hrel);
+    return TPNS_ENOTCONV;
+  }
+  return TPNS_OK;
+#undef CKS
+}
+
+static int g_solve_epoch = 0;
+
+static tpns_status band_solve_check(int32_t n, int32_t kl, int32_t ku, const int32_t* rowptr, const int32_t* colidx,
+                                    const double* vals, const double* b, double* x, tpns_precision precision) {
+  if (n <= 0 || kl < 0 || ku < 1 || kl + LU_NB > 512 || !rowptr || !colidx || !vals || !b || !x) {
+    g_err = "invalid band solve arguments";
+    return TPNS_EINVAL;
+  }
+  if (precision != TPNS_FP64 && precision != TPNS_FP32_IR) {
+    g_err = "precision not available in this build";
+    return TPNS_EINVAL;
+  }
+  return TPNS_OK;
+}
+
 // ------------------------------------------------------------------------------ ABI
 extern "C" {
 
@@ -970,6 +1053,62 @@ tpns_status tpns_layout_create(const tpns_mesh_desc* mesh, const tpns_partition_
   ctx->np = (int)ctx->L.porous.size();
   *out = ctx;
   return TPNS_OK;
+}
+
+tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* rowptr, const int32_t* colidx,
+                            const double* vals, const double* b, double* x, tpns_precision precision,
+                            void* cuda_stream, double* relres_out) {
+  g_err.clear();
+  tpns_status s = band_solve_check(n, kl, ku, rowptr, colidx, vals, b, x, precision);
+  if (s != TPNS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const size_t tsz = precision == TPNS_FP64 ? 8 : 4;
+  const int nblk = (n + LU_NB - 1) / LU_NB;
+  int nnz = 0;
+  if (cudaMemcpy(&nnz, rowptr + n, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    g_err = "cannot read rowptr";
+    return TPNS_EDEVICE;
+  }
+  std::vector<void*> mem;
+  auto get = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+    mem.push_back(p);
+    return p;
+  };
+  void* band = get((size_t)n * (kl + ku + 1) * tsz);
+  void* dinv = get((size_t)nblk * 2 * LU_NB * LU_NB * tsz);
+  SysDev* sysd = (SysDev*)get(sizeof(SysDev));
+  int* ints = (int*)get(sizeof(int) * (5 + nblk));
+  int32_t* rowof = (int32_t*)get(sizeof(int32_t) * (size_t)std::max(nnz, 1));
+  double* dbl = (double*)get(sizeof(double) * ((size_t)n + 2));
+  tpns_status out;
+  if (!band || !dinv || !sysd || !ints || !rowof || !dbl) {
+    g_err = "cudaMalloc failed";
+    out = TPNS_ENOMEM;
+  } else {
+    cudaMemsetAsync(ints, 0, sizeof(int) * (5 + nblk), st);
+    int* listd = ints;
+    int* done = ints + 1;
+    int* iters = ints + 2;
+    int* status = ints + 3;
+    int* flags = ints + 5;
+    double* r = dbl;
+    double* rel = dbl + n;
+    double* relprev = dbl + n + 1;
+    const int epoch = ++g_solve_epoch;
+    if (precision == TPNS_FP64)
+      out = band_solve_run<double>(n, kl, ku, rowptr, colidx, vals, b, x, st, sysd, listd, rowof, (double*)band,
+                                   (double*)dinv, r, rel, relprev, done, iters, status, flags, epoch, relres_out,
+                                   g_err);
+    else
+      out = band_solve_run<float>(n, kl, ku, rowptr, colidx, vals, b, x, st, sysd, listd, rowof, (float*)band,
+                                  (float*)dinv, r, rel, relprev, done, iters, status, flags, epoch, relres_out,
+                                  g_err);
+  }
+  cudaStreamSynchronize(st);
+  for (void* p : mem) cudaFree(p);
+  return out;
 }
 
 tpns_status tpns_debug_values(tpns_ctx* ctx, int32_t j, int32_t field, double* vals, double* rhs) {

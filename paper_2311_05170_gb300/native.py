@@ -52,7 +52,7 @@ _lib = None
 EXPORTS = ["tpns_create", "tpns_step", "tpns_coarse_precompute", "tpns_local_step", "tpns_num_dofs",
            "tpns_get_field", "tpns_get_stats", "tpns_batch_step", "tpns_last_error", "tpns_destroy",
            "tpns_debug_mesh", "tpns_debug_system", "tpns_set_timing", "tpns_get_timings", "tpns_launch_count",
-           "tpns_layout_create", "tpns_debug_values"]
+           "tpns_layout_create", "tpns_debug_values", "tpns_band_solve"]
 
 PHASES = ["coarse", "prolong", "asm_oseen", "scatter", "asm_darcy", "band_fill", "band_lu", "solve", "residual",
           "state_glue", "copies"]
@@ -100,6 +100,9 @@ def load(path=LIB_PATH):
     lib.tpns_layout_create.restype = C.c_int
     lib.tpns_debug_values.argtypes = [P, C.c_int32, C.c_int32, P, P]
     lib.tpns_debug_values.restype = C.c_int
+    lib.tpns_band_solve.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, C.c_int, P,
+                                    C.POINTER(C.c_double)]
+    lib.tpns_band_solve.restype = C.c_int
     _lib = lib
     return lib
 
@@ -232,6 +235,18 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def band_solve(n, kl, ku, rowptr, colidx, vals, b, x, precision="fp32", stream=None):
+    """Solve A x = b with device pointers (int addresses); returns the final relative
+    residual.  See tpns_band_solve in include/tpns.h."""
+    lib = load()
+    rel = C.c_double()
+    st = lib.tpns_band_solve(int(n), int(kl), int(ku), C.c_void_p(rowptr), C.c_void_p(colidx), C.c_void_p(vals),
+                             C.c_void_p(b), C.c_void_p(x), PRECISIONS[precision],
+                             C.c_void_p(stream) if stream else None, C.byref(rel))
+    _check(lib, None, st)
+    return rel.value
 
 
 def launch_count():

@@ -156,3 +156,37 @@ def test_refinement_statistics(native):
     t = s.timings()
     assert t["band_lu"][1] == 1 and t["band_lu"][0] > 0
     s.close()
+
+
+def _local_system_on_device(native, w, j, field=0):
+    import torch
+    s = native.Solver(w, precision="fp64")
+    s.step(1)
+    info = s.debug_system(j)
+    vals, rhs = s.debug_values(j, field)
+    s.close()
+    dev = lambda a, dt: torch.tensor(a, dtype=dt, device="cuda")
+    return info, vals, rhs, (dev(info["rowptr"], torch.int32), dev(info["colidx"], torch.int32),
+                             dev(vals, torch.float64), dev(rhs, torch.float64))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("j", [0, 5], ids=["oseen", "darcy"])
+def test_standalone_band_solve_matches_sparse_lu(native, prec, j):
+    """tpns_band_solve on a local system of the graded workload equals SciPy's sparse LU
+    of the same CSR matrix."""
+    import scipy.sparse as sps
+    import scipy.sparse.linalg as spla
+    import torch
+    w = W.config_graded(nsteps=1) if j == 0 else W.config_small(nsteps=1)
+    j_sys = 0 if j == 0 else 5                 # system 5 of the small layout is a Darcy system
+    info, vals, rhs, (rp, ci, va, b) = _local_system_on_device(native, w, j_sys)
+    n = len(info["node"])
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    rel = native.band_solve(n, info["kl"], max(info["ku"], 1), rp.data_ptr(), ci.data_ptr(), va.data_ptr(),
+                            b.data_ptr(), x.data_ptr(), precision=prec)
+    assert rel <= 1e-12
+    A = sps.csr_matrix((vals, info["colidx"], info["rowptr"]), shape=(n, n))
+    ref = spla.splu(A.tocsc()).solve(rhs)
+    got = x.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
