@@ -200,6 +200,26 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
                             double* x, tpns_precision precision, void* cuda_stream,
                             double* relres_out);
 
+/* Same operation and arguments as tpns_band_solve, for callers that cannot allocate device
+ * memory: code that runs while a CUDA stream is being captured into a graph (cudaMalloc is
+ * not allowed there), hosts whose device memory is owned by another allocator that must not
+ * see foreign allocations, and loops where an allocation's latency or failure at solve time
+ * is not acceptable.  No part of the paper corresponds to it.
+ * The scratch (band, block inverses, row index, vectors, flags) lives in one device array
+ * of TPNS_NOALLOC_SCRATCH_BYTES bytes that the library declares statically; every device
+ * that loads the library holds it until the process exits.  A system fits when
+ *   n*(kl+ku+1)*s + ceil(n/32)*2048*s + 4*nnz + 8*(n+2) + 4*(5+ceil(n/32)) + 1024
+ * is at most that size (s = 4 for TPNS_FP32_IR, 8 for TPNS_FP64, plus 256-byte alignment of
+ * each piece); larger systems are refused with TPNS_EINVAL.  The first call on a device looks
+ * up the array's device address (with that device current); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (different streams or threads) race: serialise them. */
+#define TPNS_NOALLOC_SCRATCH_BYTES (32u << 20)
+tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int32_t* rowptr,
+                                    const int32_t* colidx, const double* vals, const double* b,
+                                    double* x, tpns_precision precision, void* cuda_stream,
+                                    double* relres_out);
+
 /* Host-only context: builds meshes, subdomains, orderings and patterns (Algorithm 3 Step 2)
  * without touching a GPU, for the introspection calls above.  Every other call on it
  * returns TPNS_EINVAL.  Release with tpns_destroy. */

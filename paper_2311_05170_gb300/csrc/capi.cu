@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "kernels.hpp"
@@ -987,6 +988,33 @@ static tpns_status band_solve_check(int32_t n, int32_t kl, int32_t ku, const int
   return TPNS_OK;
 }
 
+// ------------------------------------------------------------------------------ no-allocation solve
+// Scratch of tpns_band_solve_noalloc, shared by all its calls on a device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TPNS_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_ptr[256] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+static tpns_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    g_err = "no current CUDA device";
+    return TPNS_EDEVICE;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return TPNS_EDEVICE;
+    }
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return TPNS_OK;
+}
+
 // ------------------------------------------------------------------------------ ABI
 extern "C" {
 
@@ -1109,6 +1137,62 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
   cudaStreamSynchronize(st);
   for (void* p : mem) cudaFree(p);
   return out;
+}
+
+tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int32_t* rowptr, const int32_t* colidx,
+                                    const double* vals, const double* b, double* x, tpns_precision precision,
+                                    void* cuda_stream, double* relres_out) {
+  g_err.clear();
+  tpns_status s = band_solve_check(n, kl, ku, rowptr, colidx, vals, b, x, precision);
+  if (s != TPNS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  unsigned char* base = nullptr;
+  s = noalloc_scratch(&base);
+  if (s != TPNS_OK) return s;
+  int nnz = 0;
+  if (cudaMemcpyAsync(&nnz, rowptr + n, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    g_err = "cannot read rowptr";
+    return TPNS_EDEVICE;
+  }
+  // carve the scratch: every piece 256-byte aligned
+  const size_t tsz = precision == TPNS_FP64 ? 8 : 4;
+  const int nblk = (n + LU_NB - 1) / LU_NB;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> size_t {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_band = take((size_t)n * (kl + ku + 1) * tsz);
+  const size_t o_dinv = take((size_t)nblk * 2 * LU_NB * LU_NB * tsz);
+  const size_t o_sys = take(sizeof(SysDev));
+  const size_t o_ints = take(sizeof(int) * (5 + (size_t)nblk));
+  const size_t o_rowof = take(sizeof(int32_t) * (size_t)std::max(nnz, 1));
+  const size_t o_dbl = take(sizeof(double) * ((size_t)n + 2));
+  if (nnz < 0 || off > (size_t)TPNS_NOALLOC_SCRATCH_BYTES) {
+    g_err = "system needs " + std::to_string(off) + " bytes of scratch; tpns_band_solve_noalloc has " +
+            std::to_string((size_t)TPNS_NOALLOC_SCRATCH_BYTES);
+    return TPNS_EINVAL;
+  }
+  int* ints = reinterpret_cast<int*>(base + o_ints);
+  // done, iters and status must start at zero; the flags need no clearing (epochs grow)
+  if (cudaMemsetAsync(ints, 0, sizeof(int) * 5, st) != cudaSuccess) {
+    g_err = "cudaMemsetAsync failed";
+    return TPNS_EDEVICE;
+  }
+  double* dbl = reinterpret_cast<double*>(base + o_dbl);
+  const int epoch = ++g_solve_epoch;
+  if (precision == TPNS_FP64)
+    return band_solve_run<double>(n, kl, ku, rowptr, colidx, vals, b, x, st, reinterpret_cast<SysDev*>(base + o_sys),
+                                  ints, reinterpret_cast<int32_t*>(base + o_rowof),
+                                  reinterpret_cast<double*>(base + o_band), reinterpret_cast<double*>(base + o_dinv),
+                                  dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2, ints + 3, ints + 5, epoch, relres_out,
+                                  g_err);
+  return band_solve_run<float>(n, kl, ku, rowptr, colidx, vals, b, x, st, reinterpret_cast<SysDev*>(base + o_sys), ints,
+                               reinterpret_cast<int32_t*>(base + o_rowof), reinterpret_cast<float*>(base + o_band),
+                               reinterpret_cast<float*>(base + o_dinv), dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2,
+                               ints + 3, ints + 5, epoch, relres_out, g_err);
 }
 
 tpns_status tpns_debug_values(tpns_ctx* ctx, int32_t j, int32_t field, double* vals, double* rhs) {

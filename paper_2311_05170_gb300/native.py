@@ -52,7 +52,8 @@ _lib = None
 EXPORTS = ["tpns_create", "tpns_step", "tpns_coarse_precompute", "tpns_local_step", "tpns_num_dofs",
            "tpns_get_field", "tpns_get_stats", "tpns_batch_step", "tpns_last_error", "tpns_destroy",
            "tpns_debug_mesh", "tpns_debug_system", "tpns_set_timing", "tpns_get_timings", "tpns_launch_count",
-           "tpns_layout_create", "tpns_debug_values", "tpns_band_solve"]
+           "tpns_layout_create", "tpns_debug_values", "tpns_band_solve",
+           "tpns_band_solve_noalloc"]
 
 PHASES = ["coarse", "prolong", "asm_oseen", "scatter", "asm_darcy", "band_fill", "band_lu", "solve", "residual",
           "state_glue", "copies"]
@@ -103,6 +104,8 @@ def load(path=LIB_PATH):
     lib.tpns_band_solve.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, C.c_int, P,
                                     C.POINTER(C.c_double)]
     lib.tpns_band_solve.restype = C.c_int
+    lib.tpns_band_solve_noalloc.argtypes = lib.tpns_band_solve.argtypes
+    lib.tpns_band_solve_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
