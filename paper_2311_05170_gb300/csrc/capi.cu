@@ -53,6 +53,8 @@ struct tpns_ctx {
   double lu_flops_step = 0;
   std::vector<SysDev> hsys_chol;          // Cholesky layout of the Darcy systems (setup only)
   int64_t band_chol_local_len = 0, band_chol_coarse_len = 0, dinv_local_len = 0, dinv_coarse_len = 0;
+  int64_t lslab_local_len = 0, uslab_local_len = 0, lslab_coarse_len = 0, uslab_coarse_len = 0;
+  int nblk_max_osl = 1, nblk_max_dl = 1, nblk_max_cf = 1, nblk_max_cp = 1;
   int flags_stride = 1;
   int lu_epoch = 0;
   bool host_only = false;
@@ -70,11 +72,14 @@ struct tpns_ctx {
   int32_t *d_rowptr = nullptr, *d_colidx = nullptr, *d_rowof = nullptr;
   double* d_vals = nullptr;
   double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_rel = nullptr, *d_relprev = nullptr;
-  int *d_done = nullptr, *d_iters = nullptr, *d_status = nullptr;
+  int *d_done = nullptr, *d_iters = nullptr, *d_status = nullptr, *d_ticket = nullptr;
+  double* d_partial = nullptr;
   void* d_band_local = nullptr;
   double* d_band_coarse = nullptr;
   void* d_dinv_local = nullptr;
   double* d_dinv_coarse = nullptr;
+  void *d_lslab_local = nullptr, *d_uslab_local = nullptr;
+  double *d_lslab_coarse = nullptr, *d_uslab_coarse = nullptr;
   int* d_flags = nullptr;
   SysDev* d_sys_chol = nullptr;
   int *d_list_osl = nullptr, *d_list_cf = nullptr, *d_list_dl = nullptr, *d_list_cp = nullptr,
@@ -236,6 +241,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   // systems
   ctx->hsys.clear(); ctx->hchol.clear(); ctx->hsys_chol.clear(); ctx->sys_first.assign(ctx->nprob, 0);
   ctx->band_chol_local_len = ctx->band_chol_coarse_len = ctx->dinv_local_len = ctx->dinv_coarse_len = 0;
+  ctx->lslab_local_len = ctx->uslab_local_len = ctx->lslab_coarse_len = ctx->uslab_coarse_len = 0;
   ctx->x_off.assign(ctx->nprob, 0);
   int64_t rp = 0, nz = 0, vals = 0, xo = 0, bl = 0, bc = 0;
   std::vector<int32_t> h_rowptr, h_colidx, h_rowof;
@@ -262,14 +268,20 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       ctx->flags_stride = std::max(ctx->flags_stride, nblk);
       SysDev C = S;
       C.ku = 0; C.ldab = S.kl + 1;
+      auto round32 = [](int64_t v) { return (v + 31) & ~(int64_t)31; };
+      const int64_t llen = (int64_t)nblk * LU_NB * S.kl, ulen = (int64_t)nblk * LU_NB * S.ku;
       if (coarse) {
         S.band_off = bc; bc += blen;
         S.dinv_off = ctx->dinv_coarse_len; ctx->dinv_coarse_len += dlen;
         C.band_off = ctx->band_chol_coarse_len; ctx->band_chol_coarse_len += (int64_t)S.n * C.ldab;
+        S.lslab_off = ctx->lslab_coarse_len; ctx->lslab_coarse_len += round32(llen);
+        S.uslab_off = ctx->uslab_coarse_len; ctx->uslab_coarse_len += round32(ulen);
       } else {
         S.band_off = bl; bl += blen;
         S.dinv_off = ctx->dinv_local_len; ctx->dinv_local_len += dlen;
         C.band_off = ctx->band_chol_local_len; ctx->band_chol_local_len += (int64_t)S.n * C.ldab;
+        S.lslab_off = ctx->lslab_local_len; ctx->lslab_local_len += round32(llen);
+        S.uslab_off = ctx->uslab_local_len; ctx->uslab_local_len += round32(ulen);
       }
       ctx->hsys.push_back(S);
       ctx->hsys_chol.push_back(C);
@@ -295,6 +307,11 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     ctx->kmax_local = std::max(ctx->kmax_local, std::max(ctx->hsys[s].kl, ctx->hsys[s].ku));
   }
   ctx->kmax_cf = std::max(ctx->hsys[ctx->list_cf[0]].kl, ctx->hsys[ctx->list_cf[0]].ku);
+  auto nblk_of = [&](int sidx) { return (ctx->hsys[sidx].n + LU_NB - 1) / LU_NB; };
+  for (int sidx : ctx->list_osl) ctx->nblk_max_osl = std::max(ctx->nblk_max_osl, nblk_of(sidx));
+  for (int sidx : ctx->list_dl) ctx->nblk_max_dl = std::max(ctx->nblk_max_dl, nblk_of(sidx));
+  ctx->nblk_max_cf = nblk_of(ctx->list_cf[0]);
+  for (int sidx : ctx->list_cp) ctx->nblk_max_cp = std::max(ctx->nblk_max_cp, nblk_of(sidx));
   for (int s : ctx->list_cp) ctx->kmax_cp = std::max(ctx->kmax_cp, ctx->hsys[s].kl);
   ctx->kl_max_cf = ctx->hsys[ctx->list_cf[0]].kl;
   ctx->n_max_cf = ctx->hsys[ctx->list_cf[0]].n;
@@ -381,6 +398,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(upload(ctx, &ctx->d_rowof, h_rowof));
   TRY(upload(ctx, &ctx->d_sys, ctx->hsys));
   TRY(upload(ctx, &ctx->d_sys_chol, ctx->hsys_chol));
+  ctx->flags_stride *= 2;   // panel flags, then per-block progress counters
   TRY(dalloc(ctx, &ctx->d_flags, (size_t)ctx->nsys * ctx->flags_stride));
   CK(cudaMemset(ctx->d_flags, 0, (size_t)ctx->nsys * ctx->flags_stride * sizeof(int)));
   TRY(upload(ctx, &ctx->d_chol, ctx->hchol));
@@ -399,6 +417,9 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(dalloc(ctx, &ctx->d_iters, ctx->nsys));
   TRY(dalloc(ctx, &ctx->d_status, ctx->nsys));
   CK(cudaMemset(ctx->d_status, 0, ctx->nsys * sizeof(int)));
+  TRY(dalloc(ctx, &ctx->d_ticket, ctx->nsys));
+  CK(cudaMemset(ctx->d_ticket, 0, ctx->nsys * sizeof(int)));
+  TRY(dalloc(ctx, &ctx->d_partial, (size_t)ctx->nsys * RES_CHUNKS * 2));
   if (ctx->prec == TPNS_FP64) {
     double *b, *d;
     TRY(dalloc(ctx, &b, ctx->band_local_len));
@@ -414,6 +435,21 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   }
   TRY(dalloc(ctx, &ctx->d_band_coarse, ctx->band_coarse_len));
   TRY(dalloc(ctx, &ctx->d_dinv_coarse, ctx->dinv_coarse_len));
+  {
+    // factor slabs; entries outside the matrix stay zero for good
+    const size_t tsz = ctx->prec == TPNS_FP64 ? 8 : 4;
+    unsigned char *ls, *us;
+    TRY(dalloc(ctx, &ls, (size_t)ctx->lslab_local_len * tsz));
+    TRY(dalloc(ctx, &us, (size_t)ctx->uslab_local_len * tsz));
+    CK(cudaMemset(ls, 0, (size_t)ctx->lslab_local_len * tsz));
+    CK(cudaMemset(us, 0, (size_t)ctx->uslab_local_len * tsz));
+    ctx->d_lslab_local = ls;
+    ctx->d_uslab_local = us;
+    TRY(dalloc(ctx, &ctx->d_lslab_coarse, ctx->lslab_coarse_len));
+    TRY(dalloc(ctx, &ctx->d_uslab_coarse, ctx->uslab_coarse_len));
+    CK(cudaMemset(ctx->d_lslab_coarse, 0, (size_t)ctx->lslab_coarse_len * 8));
+    CK(cudaMemset(ctx->d_uslab_coarse, 0, (size_t)ctx->uslab_coarse_len * 8));
+  }
   TRY(dalloc(ctx, &ctx->d_Ke, (size_t)(ctx->ne_osl + ctx->ne_cf) * 225));
   TRY(dalloc(ctx, &ctx->d_Re, (size_t)(ctx->ne_osl + ctx->ne_cf) * 15));
   TRY(dalloc(ctx, &ctx->d_ReD, (size_t)(ctx->ne_dl + ctx->ne_cp) * 18));
@@ -670,8 +706,9 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
   double* ReCP = ctx->d_ReD + ctx->ne_dl * 18;
   CK(launch_darcy_elem(ctx->asmargs, ctx->e_off[CP], ctx->ne_cp, ReCP, nullptr, st));
   CK(launch_seg_reduce(ctx->d_rcp_t, ctx->d_rcp_s, ctx->n_rcp, ReCP, ctx->d_b, st, nullptr));
-  CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->n_max_cp, ctx->kmax_cp, ctx->d_band_coarse, ctx->d_dinv_coarse,
-                               ctx->d_b, ctx->d_x, 0, nullptr, st, nullptr));
+  CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->n_max_cp, ctx->kmax_cp, ctx->d_lslab_coarse,
+                               ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_b, ctx->d_x, 0, nullptr, ctx->d_status,
+                               st, nullptr));
   CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cp, ctx->nn_cp, ctx->d_x, st, nullptr));
   // Step 1(2): coarse conduit problem (eq. pcFully) by Newton's method
   CK(cudaMemcpyAsync(ctx->d_uc_new, ctx->d_uc_old, (size_t)L.mcH.nn * 2 * 8, cudaMemcpyDeviceToDevice, st));
@@ -684,10 +721,14 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
     CK(launch_seg_reduce(ctx->d_rcf_t, ctx->d_rcf_s, ctx->n_rcf, ctx->d_Re, ctx->d_b, st, skip));
     CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
                                 ctx->d_band_coarse, 0, 0, st, skip));
-    CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse, ctx->d_dinv_coarse,
-                              ctx->d_flags, ctx->flags_stride, ++ctx->lu_epoch, ctx->d_status, st, skip));
-    CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->n_max_cf, ctx->kmax_cf, ctx->d_band_coarse,
-                                 ctx->d_dinv_coarse, ctx->d_b, ctx->d_x, 0, nullptr, st, skip));
+    CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse, ctx->d_lslab_coarse,
+                              ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_flags, ctx->flags_stride, ++ctx->lu_epoch, ctx->d_status,
+                              st, skip));
+    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->nblk_max_cf, ctx->d_band_coarse,
+                                ctx->d_dinv_coarse, st, skip));
+    CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->n_max_cf, ctx->kmax_cf, ctx->d_lslab_coarse,
+                                 ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_b, ctx->d_x, 0, nullptr,
+                                 ctx->d_status, st, skip));
     CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cf, ctx->nn_cf, ctx->d_x, st, skip));
     CK(launch_newton_update(ctx->d_probs + CF, ctx->d_gnode, ctx->d_vloc, L.cfl.nn, L.cfl.nvl, ctx->d_uc_new,
                             ctx->d_pc_new, ctx->d_newton_done, ctx->d_newton_iters, st));
@@ -700,6 +741,8 @@ static tpns_status local_step(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   T* band = reinterpret_cast<T*>(ctx->d_band_local);
   T* dinv = reinterpret_cast<T*>(ctx->d_dinv_local);
+  T* lslab = reinterpret_cast<T*>(ctx->d_lslab_local);
+  T* uslab = reinterpret_cast<T*>(ctx->d_uslab_local);
   const int nosl = (int)ctx->list_osl.size(), nloc = (int)ctx->list_local.size();
   // a1: coarse fields on the fine meshes
   ph_begin(ctx, PH_PROLONG);
@@ -724,8 +767,9 @@ static tpns_status local_step(tpns_ctx* ctx) {
                          nullptr));
   ph_end(ctx, PH_BAND_FILL);
   ph_begin(ctx, PH_BAND_LU);
-  CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, dinv, ctx->d_flags, ctx->flags_stride,
-                       ++ctx->lu_epoch, ctx->d_status, st, nullptr));
+  CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, lslab, uslab, dinv, ctx->d_flags,
+                       ctx->flags_stride, ++ctx->lu_epoch, ctx->d_status, st, nullptr));
+  CK(launch_band_dinv<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->nblk_max_osl, band, dinv, st, nullptr));
   ph_end(ctx, PH_BAND_LU);
   // a8: solves with FP64-residual iterative refinement
   const bool fp64 = ctx->prec == TPNS_FP64;
@@ -733,21 +777,23 @@ static tpns_status local_step(tpns_ctx* ctx) {
   const double tol = fp64 ? 1e-14 : 1e-13;
   ph_begin(ctx, PH_RESIDUAL);
   CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
-                     ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, tol, 1, st, nullptr));
+                     ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial, ctx->d_ticket, tol, 1, st,
+                     nullptr));
   ph_end(ctx, PH_RESIDUAL);
   ph_begin(ctx, PH_SOLVE);
-  CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, band, dinv, ctx->d_b, ctx->d_x, 0,
-                          nullptr, st, nullptr));
+  CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, lslab, uslab, dinv,
+                          ctx->d_b, ctx->d_x, 0, nullptr, ctx->d_status, st, nullptr));
   ph_end(ctx, PH_SOLVE);
   for (int it = 0; it < maxit; ++it) {
     ph_begin(ctx, PH_RESIDUAL);
     CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
-                       ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, tol, 0, st, nullptr));
+                       ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial, ctx->d_ticket, tol, 0, st,
+                       nullptr));
     ph_end(ctx, PH_RESIDUAL);
     if (it + 1 < maxit) {
       ph_begin(ctx, PH_SOLVE);
-      CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, band, dinv, ctx->d_r, ctx->d_x, 1,
-                              ctx->d_done, st, nullptr));
+      CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, lslab, uslab,
+                              dinv, ctx->d_r, ctx->d_x, 1, ctx->d_done, ctx->d_status, st, nullptr));
       ph_end(ctx, PH_SOLVE);
     }
   }
@@ -868,7 +914,10 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
                                 0, st, nullptr));
     CK(launch_band_chol<double>(ctx->d_sys_chol, ctx->d_list_cp, 3, cband, ctx->d_status, st));
     CK(launch_chol_to_lu<double>(ctx->d_sys_chol, ctx->d_sys, ctx->d_list_cp, 3, cband, ctx->d_band_coarse, st));
-    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->d_band_coarse, ctx->d_dinv_coarse, st));
+    CK(launch_band_to_slab<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->d_band_coarse, ctx->d_lslab_coarse,
+                                   ctx->d_uslab_coarse, st));
+    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->nblk_max_cp, ctx->d_band_coarse,
+                                ctx->d_dinv_coarse, st, nullptr));
   }
   if (ctx->prec == TPNS_FP64) {
     double* band = reinterpret_cast<double*>(ctx->d_band_local);
@@ -879,7 +928,9 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
                                 0, st, nullptr));
     CK(launch_band_chol<double>(ctx->d_sys_chol, ctx->d_list_dl, ndl, cband, ctx->d_status, st));
     CK(launch_chol_to_lu<double>(ctx->d_sys_chol, ctx->d_sys, ctx->d_list_dl, ndl, cband, band, st));
-    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_dl, ndl, band, dinv, st));
+    CK(launch_band_to_slab<double>(ctx->d_sys, ctx->d_list_dl, ndl, band, (double*)ctx->d_lslab_local,
+                                   (double*)ctx->d_uslab_local, st));
+    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_dl, ndl, ctx->nblk_max_dl, band, dinv, st, nullptr));
   } else {
     float* band = reinterpret_cast<float*>(ctx->d_band_local);
     float* dinv = reinterpret_cast<float*>(ctx->d_dinv_local);
@@ -889,7 +940,9 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
                                0, st, nullptr));
     CK(launch_band_chol<float>(ctx->d_sys_chol, ctx->d_list_dl, ndl, cband, ctx->d_status, st));
     CK(launch_chol_to_lu<float>(ctx->d_sys_chol, ctx->d_sys, ctx->d_list_dl, ndl, cband, band, st));
-    CK(launch_band_dinv<float>(ctx->d_sys, ctx->d_list_dl, ndl, band, dinv, st));
+    CK(launch_band_to_slab<float>(ctx->d_sys, ctx->d_list_dl, ndl, band, (float*)ctx->d_lslab_local,
+                                  (float*)ctx->d_uslab_local, st));
+    CK(launch_band_dinv<float>(ctx->d_sys, ctx->d_list_dl, ndl, ctx->nblk_max_dl, band, dinv, st, nullptr));
   }
   // initial glued fields
   TRY(prolong_and_glue(ctx));
@@ -919,9 +972,12 @@ __global__ void csr_rowof_kernel(const int32_t* __restrict__ rowptr, int n, int3
 template <typename T>
 static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, const int32_t* colidx,
                                   const double* vals, const double* b, double* x, cudaStream_t st, SysDev* sysd,
-                                  int* listd, int32_t* rowof, T* band, T* dinv, double* r, double* rel,
-                                  double* relprev, int* done, int* iters, int* status, int* flags, int epoch,
-                                  double* relres_out, std::string& err) {
+                                  int* listd, int32_t* rowof, T* band, T* dinv, T* lslab, T* uslab, double* r,
+                                  double* rel, double* relprev, int* done, int* iters, int* status, int* flags,
+                                  int epoch, double* relres_out, std::string& err) {
+  // the residual's partial sums follow the vector r; its ticket follows the status word
+  double* partial = r + n + 2;
+  int* ticket = status + 1;
 #define CKS(call)                                                           \
   do {                                                                      \
     cudaError_t e_ = (call);                                                \
@@ -936,6 +992,11 @@ static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, 
   SysDev S{};
   S.n = n; S.kl = kl; S.ku = ku; S.ldab = kl + ku + 1;
   S.band_off = 0; S.rp_off = 0; S.nnz_off = 0; S.nnz = nnz; S.val_off = 0; S.x_off = 0; S.dinv_off = 0;
+  S.lslab_off = 0; S.uslab_off = 0;
+  const int nblk = (n + LU_NB - 1) / LU_NB;
+  CKS(cudaMemsetAsync(lslab, 0, (size_t)nblk * LU_NB * kl * sizeof(T), st));
+  CKS(cudaMemsetAsync(uslab, 0, (size_t)nblk * LU_NB * ku * sizeof(T), st));
+  CKS(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * (size_t)nblk, st));
   const int zero = 0;
   CKS(cudaMemcpyAsync(sysd, &S, sizeof(SysDev), cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(listd, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -944,16 +1005,21 @@ static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, 
   csr_rowof_kernel<<<(n + 255) / 256, 256, 0, st>>>(rowptr, n, rowof);
   CKS(cudaGetLastError());
   CKS(launch_band_fill<T>(sysd, listd, 1, rowof, colidx, vals, band, 0, 0, st, nullptr));
-  CKS(launch_band_lu<T>(sysd, listd, 1, kl, band, dinv, flags, (n + LU_NB - 1) / LU_NB, epoch, status, st, nullptr));
+  CKS(launch_band_lu<T>(sysd, listd, 1, kl, band, lslab, uslab, dinv, flags, 2 * nblk, epoch, status, st, nullptr));
+  CKS(launch_band_dinv<T>(sysd, listd, 1, nblk, band, dinv, st, nullptr));
   const bool fp64 = sizeof(T) == 8;
   const int maxit = 12;
   const double tol = fp64 ? 1e-14 : 1e-13;
   const int kmax = std::max(kl, ku);
-  CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, tol, 1, st, nullptr));
-  CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, band, dinv, b, x, 0, nullptr, st, nullptr));
+  CKS(cudaMemsetAsync(ticket, 0, sizeof(int), st));
+  CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, partial, ticket, tol, 1,
+                      st, nullptr));
+  CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, lslab, uslab, dinv, b, x, 0, nullptr, status, st, nullptr));
   for (int it = 0; it < maxit; ++it) {
-    CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, tol, 0, st, nullptr));
-    if (it + 1 < maxit) CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, band, dinv, r, x, 1, done, st, nullptr));
+    CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, partial, ticket, tol,
+                        0, st, nullptr));
+    if (it + 1 < maxit)
+      CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, lslab, uslab, dinv, r, x, 1, done, status, st, nullptr));
   }
   int hst = 0;
   double hrel = 0;
@@ -1106,16 +1172,18 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
   };
   void* band = get((size_t)n * (kl + ku + 1) * tsz);
   void* dinv = get((size_t)nblk * 2 * LU_NB * LU_NB * tsz);
+  void* lsl = get((size_t)nblk * LU_NB * kl * tsz);
+  void* usl = get((size_t)nblk * LU_NB * ku * tsz);
   SysDev* sysd = (SysDev*)get(sizeof(SysDev));
-  int* ints = (int*)get(sizeof(int) * (5 + nblk));
+  int* ints = (int*)get(sizeof(int) * (5 + 2 * (size_t)nblk));
   int32_t* rowof = (int32_t*)get(sizeof(int32_t) * (size_t)std::max(nnz, 1));
-  double* dbl = (double*)get(sizeof(double) * ((size_t)n + 2));
+  double* dbl = (double*)get(sizeof(double) * ((size_t)n + 2 + 2 * RES_CHUNKS));
   tpns_status out;
-  if (!band || !dinv || !sysd || !ints || !rowof || !dbl) {
+  if (!band || !dinv || !lsl || !usl || !sysd || !ints || !rowof || !dbl) {
     g_err = "cudaMalloc failed";
     out = TPNS_ENOMEM;
   } else {
-    cudaMemsetAsync(ints, 0, sizeof(int) * (5 + nblk), st);
+    cudaMemsetAsync(ints, 0, sizeof(int) * (5 + 2 * (size_t)nblk), st);
     int* listd = ints;
     int* done = ints + 1;
     int* iters = ints + 2;
@@ -1127,12 +1195,12 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
     const int epoch = ++g_solve_epoch;
     if (precision == TPNS_FP64)
       out = band_solve_run<double>(n, kl, ku, rowptr, colidx, vals, b, x, st, sysd, listd, rowof, (double*)band,
-                                   (double*)dinv, r, rel, relprev, done, iters, status, flags, epoch, relres_out,
-                                   g_err);
+                                   (double*)dinv, (double*)lsl, (double*)usl, r, rel, relprev, done, iters, status,
+                                   flags, epoch, relres_out, g_err);
     else
       out = band_solve_run<float>(n, kl, ku, rowptr, colidx, vals, b, x, st, sysd, listd, rowof, (float*)band,
-                                  (float*)dinv, r, rel, relprev, done, iters, status, flags, epoch, relres_out,
-                                  g_err);
+                                  (float*)dinv, (float*)lsl, (float*)usl, r, rel, relprev, done, iters, status, flags,
+                                  epoch, relres_out, g_err);
   }
   cudaStreamSynchronize(st);
   for (void* p : mem) cudaFree(p);
@@ -1166,18 +1234,20 @@ tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int
   };
   const size_t o_band = take((size_t)n * (kl + ku + 1) * tsz);
   const size_t o_dinv = take((size_t)nblk * 2 * LU_NB * LU_NB * tsz);
+  const size_t o_lsl = take((size_t)nblk * LU_NB * kl * tsz);
+  const size_t o_usl = take((size_t)nblk * LU_NB * ku * tsz);
   const size_t o_sys = take(sizeof(SysDev));
-  const size_t o_ints = take(sizeof(int) * (5 + (size_t)nblk));
+  const size_t o_ints = take(sizeof(int) * (5 + 2 * (size_t)nblk));
   const size_t o_rowof = take(sizeof(int32_t) * (size_t)std::max(nnz, 1));
-  const size_t o_dbl = take(sizeof(double) * ((size_t)n + 2));
+  const size_t o_dbl = take(sizeof(double) * ((size_t)n + 2 + 2 * RES_CHUNKS));
   if (nnz < 0 || off > (size_t)TPNS_NOALLOC_SCRATCH_BYTES) {
     g_err = "system needs " + std::to_string(off) + " bytes of scratch; tpns_band_solve_noalloc has " +
             std::to_string((size_t)TPNS_NOALLOC_SCRATCH_BYTES);
     return TPNS_EINVAL;
   }
   int* ints = reinterpret_cast<int*>(base + o_ints);
-  // done, iters and status must start at zero; the flags need no clearing (epochs grow)
-  if (cudaMemsetAsync(ints, 0, sizeof(int) * 5, st) != cudaSuccess) {
+  // done, iters, status and the panel flags / block counters must start at zero
+  if (cudaMemsetAsync(ints, 0, sizeof(int) * (5 + 2 * (size_t)nblk), st) != cudaSuccess) {
     g_err = "cudaMemsetAsync failed";
     return TPNS_EDEVICE;
   }
@@ -1187,11 +1257,13 @@ tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int
     return band_solve_run<double>(n, kl, ku, rowptr, colidx, vals, b, x, st, reinterpret_cast<SysDev*>(base + o_sys),
                                   ints, reinterpret_cast<int32_t*>(base + o_rowof),
                                   reinterpret_cast<double*>(base + o_band), reinterpret_cast<double*>(base + o_dinv),
+                                  reinterpret_cast<double*>(base + o_lsl), reinterpret_cast<double*>(base + o_usl),
                                   dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2, ints + 3, ints + 5, epoch, relres_out,
                                   g_err);
   return band_solve_run<float>(n, kl, ku, rowptr, colidx, vals, b, x, st, reinterpret_cast<SysDev*>(base + o_sys), ints,
                                reinterpret_cast<int32_t*>(base + o_rowof), reinterpret_cast<float*>(base + o_band),
-                               reinterpret_cast<float*>(base + o_dinv), dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2,
+                               reinterpret_cast<float*>(base + o_dinv), reinterpret_cast<float*>(base + o_lsl),
+                               reinterpret_cast<float*>(base + o_usl), dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2,
                                ints + 3, ints + 5, epoch, relres_out, g_err);
 }
 

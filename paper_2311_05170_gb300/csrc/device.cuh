@@ -40,6 +40,8 @@ struct SysDev {
   int64_t val_off;   // CSR values
   int64_t x_off;     // b, x, r vectors
   int64_t dinv_off;  // inverses of the diagonal blocks of L and U (2 * nblk * 32 * 32)
+  int64_t lslab_off; // L below the diagonal, per 32-column block: [c][i - j - 1], 32 * kl per block
+  int64_t uslab_off; // U above the diagonal, per 32-column block: [c][i - j + ku], 32 * ku per block
 };
 
 struct Phys {

@@ -11,7 +11,8 @@ namespace tpns {
 int64_t launch_counter();
 void count_launches(int n);
 
-constexpr int LU_NB = 32;        // panel width of the band LU and block size of the solves
+constexpr int LU_NB = 32;
+constexpr int RES_CHUNKS = 16;   // CTAs per system in the residual kernel        // panel width of the band LU and block size of the solves
 constexpr int LU_CLUSTER = 8;    // CTAs per system in the band LU
 
 // ---- band linear algebra (kernels_band.cu); `T` = float or double
@@ -20,28 +21,33 @@ cudaError_t launch_band_fill(const SysDev* sys, const int* sys_list, int nsys, c
                              const int32_t* colidx, const double* vals, T* band, int chol,
                              int64_t total_nnz_hint, cudaStream_t st, const int* skip);
 template <typename T>
-cudaError_t launch_band_lu(const SysDev* sys, const int* sys_list, int nsys, int kl_max, T* band, T* dinv,
-                           int* flags, int flags_stride, int epoch, int* status, cudaStream_t st,
+cudaError_t launch_band_lu(const SysDev* sys, const int* sys_list, int nsys, int kl_max, T* band, T* lslab,
+                           T* uslab, T* dinv, int* sync, int sync_stride, int epoch, int* status, cudaStream_t st,
                            const int* skip);
 template <typename T>
-cudaError_t launch_band_dinv(const SysDev* sys, const int* sys_list, int nsys, const T* band, T* dinv,
-                             cudaStream_t st);
+cudaError_t launch_band_dinv(const SysDev* sys, const int* sys_list, int nsys, int nblk_max, const T* band,
+                             T* dinv, cudaStream_t st, const int* skip);
+template <typename T>
+cudaError_t launch_band_to_slab(const SysDev* sys, const int* sys_list, int nsys, const T* band, T* lslab,
+                                T* uslab, cudaStream_t st);
 template <typename T>
 cudaError_t launch_band_chol(const SysDev* sys, const int* sys_list, int nsys, T* band, int* status,
                              cudaStream_t st);
 template <typename T>
 cudaError_t launch_chol_to_lu(const SysDev* sys_chol, const SysDev* sys_lu, const int* list, int nsys,
                               const T* cband, T* lband, cudaStream_t st);
-// x (+)= U^{-1} L^{-1} r with the stored diagonal-block inverses
+// x (+)= U^{-1} L^{-1} r from the factor slabs and the diagonal-block inverses
 template <typename T>
 cudaError_t launch_band_solve(const SysDev* sys, const int* sys_list, int nsys, int n_max, int kmax,
-                              const T* band, const T* dinv, const double* r, double* x, int accumulate, const int* done,
-                              cudaStream_t st, const int* skip);
+                              const T* lslab, const T* uslab, const T* dinv, const double* r, double* x,
+                              int accumulate, const int* done, int* status, cudaStream_t st, const int* skip);
 // r = b - A x in FP64, convergence bookkeeping (relative residual <= tol, or stagnation)
+// partial: nsys * RES_CHUNKS * 2 doubles; ticket: nsys ints, zero before the first call
 cudaError_t launch_residual(const SysDev* sys, const int* sys_list, int nsys, const int32_t* rowptr,
                             const int32_t* colidx, const double* vals, const double* b,
                             const double* x, double* r, double* rel, double* rel_prev, int* done,
-                            int* iters, double tol, int first, cudaStream_t st, const int* skip);
+                            int* iters, double* partial, int* ticket, double tol, int first,
+                            cudaStream_t st, const int* skip);
 
 // ---- assembly (kernels_assemble.cu)
 struct AsmArgs {

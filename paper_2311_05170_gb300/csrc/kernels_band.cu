@@ -7,6 +7,7 @@
 // L(i, j) at band[j * ldab + i - j], ldab = kl + 1.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "kernels.hpp"
@@ -63,18 +64,50 @@ cudaError_t launch_band_fill(const SysDev* sys, const int* list, int nsys, const
 }
 
 // ------------------------------------------------------------------------------ band LU
-// One thread-block cluster of LU_CLUSTER CTAs per system (the cluster guarantees that the
-// CTAs of a system are resident together).  Column blocks of LU_NB columns are owned round
-// robin by the CTAs.  At step kb every CTA waits for panel kb (L11, L21 of block kb and the
-// inverses of its diagonal block), forms U12 = L11^{-1} A12 for its column blocks inside the
-// band window and applies A22 -= L21 U12 to them.  The owner of block kb+1 updates that
-// block first and factors panel kb+1 at once (look-ahead), then publishes it with a
-// release flag; there is no barrier per step, so the CTAs run as a pipeline.
+// One thread-block cluster of LU_CLUSTER CTAs per system (the cluster keeps the CTAs of a
+// system resident together).  CTA 0 produces every panel: it keeps the current factored
+// panel (L11, L21) in shared memory, forms U12 of the next column block, applies
+// A22 -= L21 U12 to that block while loading it into registers, factors it there (no
+// pivoting) and publishes it with a release flag.  CTAs 1..7 own the other column blocks
+// round robin and apply every published panel to them, publishing per-block progress
+// counters that CTA 0 waits for.  Thus the chain of panels never waits for a barrier or a
+// global reload, and the bulk updates run beside it.
 // Unpivoted: the unknown ordering makes every leading block invertible (pressures follow
-// the velocities they couple to); a zero or non-finite pivot sets the status word.
-constexpr int LU_THREADS = 256;
-constexpr int LU_RPT = 2;                       // panel rows per thread: NB + kl <= 512
+// the velocities they couple to); a zero or non-finite pivot sets bit 0 of the status word,
+// a wait that gives up sets bit 1.
+// Besides the working band, the final factors are written to per-block slabs
+// (L: [c][i - j - 1], U: [c][i - j + ku]) that the triangular solves stream with TMA.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// threads per LU CTA: one panel row per thread (NB + kl <= threads); 768 for FP32 and 512
+// for FP64 (85 / 128 registers per thread), so that the single critical CTA has enough warps
+// to hide the latency of its dependent phases
+template <typename T>
+__host__ __device__ constexpr int lu_threads() { return sizeof(T) == 4 ? 768 : 512; }
 constexpr int SP = LU_NB + 1;                   // padded row stride of shared tiles
+constexpr int LU_BULK = LU_CLUSTER - 1;
+constexpr int WAIT_LIMIT = 1 << 22;
 
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -83,6 +116,23 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ bool wait_eq(const int* p, int v) {
+  for (int it = 0; ld_acquire(p) != v; ++it) {
+    if (it > WAIT_LIMIT) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+// progress counters hold (epoch << 12) | count
+__device__ __forceinline__ int cnt_word(int epoch, int c) { return ((epoch & 0x7FFFF) << 12) | c; }
+__device__ __forceinline__ bool wait_cnt(const int* p, int epoch, int need) {
+  for (int it = 0;; ++it) {
+    const int v = ld_acquire(p);
+    if ((v >> 12) == (epoch & 0x7FFFF) && (v & 4095) >= need) return true;
+    if (it > WAIT_LIMIT) return false;
+    __nanosleep(64);
+  }
 }
 
 // Asynchronous global -> shared copies of one element (sizeof(T) bytes).
@@ -98,9 +148,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// a pivot is unusable if it is zero, NaN or infinite (tested in its own precision)
+__device__ __forceinline__ bool bad_pivot(float v) { return !(fabsf(v) > 0.0f) || !(fabsf(v) < INFINITY); }
+__device__ __forceinline__ bool bad_pivot(double v) { return !(fabs(v) > 0.0) || !(fabs(v) < (double)INFINITY); }
+
+__device__ __forceinline__ int64_t lsl_idx(int i, int j, int kl) {
+  return (int64_t)(j >> 5) * 32 * kl + (int64_t)(j & 31) * kl + (i - j - 1);
+}
+__device__ __forceinline__ int64_t usl_idx(int i, int j, int ku) {
+  return (int64_t)(j >> 5) * 32 * ku + (int64_t)(j & 31) * ku + (i - j + ku);
+}
+
 // Inverses of the unit lower and upper triangles of a factored NB x NB diagonal block held
 // in shared memory (row stride SP); written transposed (column-major) to dinv so that a
-// warp reads one column per step with consecutive lanes.
+// warp reads one column per step with consecutive lanes.  Threads 0..63.
 template <typename T>
 __device__ void diag_inverses(const T* __restrict__ D, int kw, T* __restrict__ dinv) {
   constexpr int NB = LU_NB;
@@ -132,260 +193,402 @@ __device__ void diag_inverses(const T* __restrict__ D, int kw, T* __restrict__ d
   }
 }
 
-// Factor panel kb (columns k0..k0+kw-1, rows k0..k0+R-1) with the rows held in registers;
-// the pivot row is broadcast through shared memory.  Writes the factored panel back to the
-// band and the diagonal-block inverses to dinv.
+// Factor the panel whose rows are held in registers (row r = threadIdx.x relative to k0,
+// columns k0..k0+kw-1); the pivot row is broadcast through shared memory.  Writes the band,
+// the slabs and the factored panel into Pn (row stride SP).
 template <typename T>
-__device__ void lu_factor_panel_reg(T* __restrict__ AB, int n, int kl, int ku, int ldab, int kb,
-                                    T* __restrict__ prow, T* __restrict__ diag, T* __restrict__ dinv,
-                                    int* status) {
+__device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku, int ldab,
+                            T* __restrict__ AB, T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn,
+                            T* __restrict__ prow, int* status) {
   constexpr int NB = LU_NB;
-  const int k0 = kb * NB, kw = min(NB, n - k0);
-  const int R = min(n, k0 + kw + kl) - k0;
   const int tid = threadIdx.x;
-  T a[LU_RPT][NB];
-#pragma unroll
-  for (int q = 0; q < LU_RPT; ++q) {
-    const int r = tid + q * LU_THREADS, i = k0 + r;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      const int j = k0 + c;
-      a[q][c] = (r < R && c < kw && i - j <= kl && j - i <= ku) ? AB[(int64_t)j * ldab + (ku + i - j)] : T(0);
-    }
-  }
+  const int r = tid, i = k0 + r;
+  // one barrier per column: the owner of pivot row c+1 (thread c+1) applies column c to its
+  // row, then publishes it with the reciprocal of its pivot into the other half of prow
   bool bad = false;
+  if (tid == 0) {
+    T piv = a[0];
+    if (bad_pivot(piv)) {
+      bad = true;
+      piv = T(1);
+    }
+#pragma unroll
+    for (int c2 = 0; c2 < NB; ++c2) prow[c2] = a[c2];
+    prow[NB] = T(1) / piv;
+  }
+  __syncthreads();
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (c < kw) {
-      if (tid == c) {
+      const T* pr = prow + (c & 1) * (NB + 2);
+      T* pn = prow + ((c + 1) & 1) * (NB + 2);
+      if (r > c && r < R) {
+        const T l = a[c] * pr[NB];
+        a[c] = l;
 #pragma unroll
-        for (int c2 = 0; c2 < NB; ++c2) prow[c2] = a[0][c2];
+        for (int c2 = c + 1; c2 < NB; ++c2) a[c2] -= l * pr[c2];
       }
-      __syncthreads();
-      T piv = prow[c];
-      if (!(piv == piv) || piv == T(0) || isinf((double)piv)) {
-        bad = true;
-        piv = T(1);
-      }
-      const T inv = T(1) / piv;
-#pragma unroll
-      for (int q = 0; q < LU_RPT; ++q) {
-        const int r = tid + q * LU_THREADS;
-        if (r > c && r < R) {
-          const T l = a[q][c] * inv;
-          a[q][c] = l;
-#pragma unroll
-          for (int c2 = c + 1; c2 < NB; ++c2) a[q][c2] -= l * prow[c2];
+      if (c + 1 < kw && tid == c + 1) {
+        T piv = a[c + 1];
+        if (bad_pivot(piv)) {
+          bad = true;
+          piv = T(1);
         }
+#pragma unroll
+        for (int c2 = 0; c2 < NB; ++c2) pn[c2] = a[c2];
+        pn[NB] = T(1) / piv;
       }
       __syncthreads();
     }
   }
-  if (bad && tid == 0) atomicOr(status, 1);
-#pragma unroll
-  for (int q = 0; q < LU_RPT; ++q) {
-    const int r = tid + q * LU_THREADS, i = k0 + r;
+  if (bad) atomicOr(status, 1);
+  if (r < R) {
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       const int j = k0 + c;
-      if (r < R && c < kw && i - j <= kl && j - i <= ku) AB[(int64_t)j * ldab + (ku + i - j)] = a[q][c];
+      Pn[r * SP + c] = a[c];
+      if (c < kw && i - j <= kl && j - i <= ku) {
+        AB[(int64_t)j * ldab + (ku + i - j)] = a[c];
+        if (i > j) LS[lsl_idx(i, j, kl)] = a[c];
+        else if (i < j) US[usl_idx(i, j, ku)] = a[c];
+      }
     }
   }
-  if (tid < NB) {
+}
+
+// U12 = L11^{-1} A12 for one column block: A12 (rows k0.., columns c0..) is loaded into Ub
+// (row stride SP) and multiplied by the inverse Li (column-major NB x NB); the result goes to
+// the band, the U slab and the unpadded copy Uv used for broadcast reads.
+template <typename T>
+__device__ void form_u12(const T* __restrict__ Li, T* __restrict__ Ub, T* __restrict__ Uv, T* __restrict__ AB,
+                         T* __restrict__ US, int k0, int kw, int c0, int cw, int kl, int ku, int ldab) {
+  constexpr int NB = LU_NB;
+  constexpr int THREADS = lu_threads<T>();
+  constexpr int PER = (NB * NB + THREADS - 1) / THREADS;
+  const int tid = threadIdx.x;
+  T v[PER];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) diag[tid * SP + c] = a[0][c];
+  for (int q = 0; q < PER; ++q) {
+    const int idx = tid + q * THREADS;
+    const int jj = idx / NB, ii = idx - jj * NB;
+    const int i = k0 + ii, j = c0 + jj;
+    v[q] = (idx < NB * NB && ii < kw && jj < cw && j - i <= ku && i - j <= kl)
+               ? __ldcg(AB + (int64_t)j * ldab + (ku + i - j)) : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = tid + q * THREADS;
+    const int jj = idx / NB, ii = idx - jj * NB;
+    if (idx < NB * NB) Ub[ii * SP + jj] = v[q];
   }
   __syncthreads();
-  diag_inverses<T>(diag, kw, dinv + (int64_t)kb * 2 * NB * NB);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = tid + q * THREADS;
+    const int jj = idx / NB, ii = idx - jj * NB;
+    T acc = T(0);
+    if (idx < NB * NB) {
+#pragma unroll
+      for (int p = 0; p < NB; ++p) acc += Li[p * NB + ii] * Ub[p * SP + jj];
+    }
+    v[q] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = tid + q * THREADS;
+    const int jj = idx / NB, ii = idx - jj * NB;
+    if (idx >= NB * NB) continue;
+    Uv[ii * NB + jj] = v[q];
+    const int i = k0 + ii, j = c0 + jj;
+    if (ii < kw && jj < cw && j - i <= ku && i - j <= kl) {
+      AB[(int64_t)j * ldab + (ku + i - j)] = v[q];
+      US[usl_idx(i, j, ku)] = v[q];
+    }
+  }
+  __syncthreads();
+}
+
+// Inverse of the unit lower triangle of a factored diagonal block (rows 0..NB-1 of the panel
+// in Pn, row stride SP), column-major into Li (shared) and dli (global).  Threads 0..NB-1.
+template <typename T>
+__device__ void unit_lower_inverse(const T* __restrict__ Pn, int kw, T* __restrict__ Li, T* __restrict__ dli) {
+  constexpr int NB = LU_NB;
+  const int j = threadIdx.x;
+  if (j < NB) {
+    T x[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      T v = (i == j) ? T(1) : T(0);
+#pragma unroll
+      for (int p = 0; p < i; ++p) v -= Pn[i * SP + p] * x[p];
+      x[i] = (i < kw) ? v : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      Li[j * NB + i] = x[i];
+      dli[j * NB + i] = x[i];
+    }
+  }
+}
+
+// acc[0..W) -= sum_p l(p) Uv[p][c0 .. c0+W)  (Uv row-major NB x NB, broadcast vector reads);
+// the loop over p is fully unrolled so that l(p) may read a register array.
+template <typename T, int W, typename LF>
+__device__ __forceinline__ void row_update(T (&acc)[W], LF lf, const T* __restrict__ Uv, int c0) {
+  constexpr int NB = LU_NB;
+#pragma unroll
+  for (int p = 0; p < NB; ++p) {
+    const T l = lf(p);
+    if constexpr (sizeof(T) == 4) {
+      const float4* u = reinterpret_cast<const float4*>(Uv + p * NB + c0);
+#pragma unroll
+      for (int c4 = 0; c4 < W / 4; ++c4) {
+        const float4 v = u[c4];
+        acc[4 * c4 + 0] -= l * v.x;
+        acc[4 * c4 + 1] -= l * v.y;
+        acc[4 * c4 + 2] -= l * v.z;
+        acc[4 * c4 + 3] -= l * v.w;
+      }
+    } else {
+      const double2* u = reinterpret_cast<const double2*>(Uv + p * NB + c0);
+#pragma unroll
+      for (int c2 = 0; c2 < W / 2; ++c2) {
+        const double2 v = u[c2];
+        acc[2 * c2 + 0] -= l * v.x;
+        acc[2 * c2 + 1] -= l * v.y;
+      }
+    }
+  }
 }
 
 template <typename T>
-__global__ void __cluster_dims__(LU_CLUSTER, 1, 1) __launch_bounds__(LU_THREADS, 1)
+__global__ void __cluster_dims__(LU_CLUSTER, 1, 1) __launch_bounds__(lu_threads<T>(), 1)
 band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* __restrict__ band,
-               T* __restrict__ dinv_all, int* __restrict__ flags_all, int flags_stride, int epoch,
-               int* __restrict__ status, const int* skip) {
+               T* __restrict__ lslab, T* __restrict__ uslab, T* __restrict__ dinv_all, int* __restrict__ sync_all,
+               int sync_stride, int epoch, int* __restrict__ status, const int* skip) {
   if (skip && *skip) return;
-  constexpr int NB = LU_NB, CL = LU_CLUSTER;
+  constexpr int NB = LU_NB;
+  constexpr int THREADS = lu_threads<T>();
+  constexpr int HALF = NB / 2;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int sidx = blockIdx.x / CL;
-  const int sid = list[sidx];
+  const int sid = list[blockIdx.x / LU_CLUSTER];
   const SysDev S = sys[sid];
   const int n = S.n, kl = S.kl, ku = S.ku, ldab = S.ldab;
   T* AB = band + S.band_off;
-  T* dinv = dinv_all + S.dinv_off;
-  int* flags = flags_all + (int64_t)sid * flags_stride;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Pn = reinterpret_cast<T*>(smem_raw);            // (NB + kl) x SP panel
-  T* Ub = Pn + (size_t)(NB + kl) * SP;               // NB x SP block of A12 / U12
-  T* Li = Ub + NB * SP;                              // NB x NB L11^{-1} (column-major)
-  T* prow = Li + NB * NB;                            // NB + 1
-  T* diag = prow + SP;                               // NB x SP
+  T* LS = lslab + S.lslab_off;
+  T* US = uslab + S.uslab_off;
+  T* DI = dinv_all + S.dinv_off;
+  int* flag = sync_all + (int64_t)sid * sync_stride;
+  int* cnt = flag + sync_stride / 2;
+  int* st = status + sid;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);     // one mbarrier (bulk CTAs)
+  T* Uv = reinterpret_cast<T*>(smem_raw + 128);              // NB x NB
+  T* Li = Uv + NB * NB;                                      // NB x NB, L11^{-1} column-major
+  T* Ub = Li + NB * NB;                                      // NB x SP
+  T* prow = Ub + NB * SP;                                    // 2 x (NB + 2) pivot rows
+  T* Pn = prow + 2 * (NB + 2);                               // critical: (NB + kl) x SP panel
+  T* Ls = prow;                                              // bulk: NB x kl L slab (16-byte aligned)
   __shared__ int abort_flag;
   const int nblk = (n + NB - 1) / NB;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = LU_THREADS / 32;
-  if (tid == 0) abort_flag = 0;
-  __syncthreads();
-  if (rank == 0 && nblk > 0) {
-    lu_factor_panel_reg<T>(AB, n, kl, ku, ldab, 0, prow, diag, dinv, status + sid);
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      st_release(flags + 0, epoch);
-    }
+  const int D = (31 + ku) / 32;                              // blocks right of a panel inside its window
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = THREADS / 32;
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int kb = 0; kb < nblk; ++kb) {
-    const int k0 = kb * NB, kw = min(NB, n - k0);
-    const int R = min(n, k0 + kw + kl) - k0;
-    const int cb_last = min(nblk - 1, (k0 + kw - 1 + ku) / NB);
-    int first_mine = kb + 1;
-    while (first_mine <= cb_last && first_mine % CL != rank) ++first_mine;
-    if (first_mine > cb_last) continue;
-    // wait for panel kb (bounded; gives up with an error flag)
-    if (tid == 0) {
-      int it = 0;
-      while (ld_acquire(flags + kb) != epoch) {
-        if (++it > (1 << 22)) {
-          atomicOr(status + sid, 2);
+  __syncthreads();
+  if (rank == 0) {
+    // ------------------------------------------------ critical CTA: the chain of panels
+    T a[NB];
+    {
+      const int kw = min(NB, n), R = min(n, kw + kl), r = tid;
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        a[c] = (r < R && c < kw && r - c <= kl && c - r <= ku) ? __ldcg(AB + (int64_t)c * ldab + (ku + r - c)) : T(0);
+      factor_rows<T>(a, 0, kw, R, kl, ku, ldab, AB, LS, US, Pn, prow, st);
+      __syncthreads();
+      unit_lower_inverse<T>(Pn, kw, Li, DI);
+      __syncthreads();
+      if (tid == 0) st_release(flag + 0, epoch);   // release orders the CTA's writes (after the barrier)
+    }
+    for (int kb = 0; kb + 1 < nblk; ++kb) {
+      const int k0 = kb * NB, R = min(n, k0 + NB + kl) - k0;
+      const int cb = kb + 1, c0 = cb * NB, cw = min(NB, n - c0), R2 = min(n, c0 + cw + kl) - c0;
+      const int need = cb - 1 - max(0, cb - D);
+      if (need > 0 && tid == 0) {
+        if (!wait_cnt(cnt + cb, epoch, need)) {
+          atomicOr(st, 2);
           abort_flag = 1;
-          break;
         }
-        __nanosleep(64);
       }
+      __syncthreads();
+      if (abort_flag) return;
+      form_u12<T>(Li, Ub, Uv, AB, US, k0, NB, c0, cw, kl, ku, ldab);
+      // the row of the next panel held by this thread, updated by this panel on the way in
+      {
+        const int r2 = tid, i = c0 + r2, r = r2 + NB;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          const int j = c0 + c;
+          a[c] = (r2 < R2 && c < cw && i - j <= kl && j - i <= ku) ? __ldcg(AB + (int64_t)j * ldab + (ku + i - j)) : T(0);
+        }
+        if (r2 < R2 && r < R) row_update<T, NB>(a, [&](int p) { return Pn[r * SP + p]; }, Uv, 0);
+      }
+      __syncthreads();
+      factor_rows<T>(a, c0, cw, R2, kl, ku, ldab, AB, LS, US, Pn, prow, st);
+      __syncthreads();
+      unit_lower_inverse<T>(Pn, cw, Li, DI + (int64_t)cb * 2 * NB * NB);
+      __syncthreads();
+      if (tid == 0) st_release(flag + cb, epoch);
     }
-    __syncthreads();
-    if (abort_flag) return;
-    for (int idx = tid; idx < R * NB; idx += LU_THREADS) {
-      const int c = idx / R, r = idx - c * R;      // rows fastest: coalesced column reads
-      const int i = k0 + r, j = k0 + c;
-      if (c < kw && i - j <= kl && j - i <= ku) cp_async_elem(Pn + r * SP + c, AB + (int64_t)j * ldab + (ku + i - j));
-      else Pn[r * SP + c] = T(0);
-    }
-    for (int idx = tid; idx < NB * NB; idx += LU_THREADS) cp_async_elem(Li + idx, dinv + (int64_t)kb * 2 * NB * NB + idx);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    for (int cb = first_mine; cb <= cb_last; cb += CL) {
-      const int c0 = cb * NB, cw = min(NB, n - c0);
-      for (int idx = tid; idx < NB * NB; idx += LU_THREADS) {
-        const int jj = idx / NB, ii = idx - jj * NB;
-        const int i = k0 + ii, j = c0 + jj;
-        if (ii < kw && jj < cw && j - i <= ku && i - j <= kl) cp_async_elem(Ub + ii * SP + jj, AB + (int64_t)j * ldab + (ku + i - j));
-        else Ub[ii * SP + jj] = T(0);
-      }
-      cp_async_commit();
-      cp_async_wait<0>();
-      __syncthreads();
-      // U12 = L11^{-1} A12: four entries per thread
-      T u[NB * NB / LU_THREADS];
-#pragma unroll
-      for (int q = 0; q < NB * NB / LU_THREADS; ++q) {
-        const int idx = tid + q * LU_THREADS;
-        const int jj = idx / NB, ii = idx - jj * NB;
-        T acc = T(0);
-#pragma unroll
-        for (int p = 0; p < NB; ++p) acc += Li[p * NB + ii] * Ub[p * SP + jj];
-        u[q] = acc;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < NB * NB / LU_THREADS; ++q) {
-        const int idx = tid + q * LU_THREADS;
-        const int jj = idx / NB, ii = idx - jj * NB;
-        Ub[ii * SP + jj] = u[q];
-        const int i = k0 + ii, j = c0 + jj;
-        if (ii < kw && jj < cw && j - i <= ku && i - j <= kl) AB[(int64_t)j * ldab + (ku + i - j)] = u[q];
-      }
-      __syncthreads();
-      // A22 -= L21 U12 on rows kw..R-1 of this column block; lane = row
-      for (int rb = kw + warp * 32; rb < R; rb += nwarp * 32) {
-        const int r = rb + lane;
-        const bool ok = r < R;
-        T l[NB];
-#pragma unroll
-        for (int p = 0; p < NB; ++p) l[p] = ok ? Pn[r * SP + p] : T(0);
-        const int i = k0 + r;
+  } else {
+    // ------------------------------------------------ bulk CTAs: blocks p+2 .. of every panel p
+    int uses = 0;
+    for (int p = 0; p < nblk; ++p) {
+      const int k0 = p * NB, kw = min(NB, n - k0), R = min(n, k0 + kw + kl) - k0;
+      const int cbl = min(nblk - 1, (k0 + kw - 1 + ku) / NB);
+      int first = p + 2;
+      while (first <= cbl && 1 + first % LU_BULK != rank) ++first;
+      if (first > cbl) continue;
+      if (tid == 0) {
+        bool ok = wait_eq(flag + p, epoch);
         if (ok) {
-          // all loads of the row in flight at once, then the FMAs, then the stores
-          T acc[NB];
-          T* a0 = AB + (int64_t)c0 * ldab + (ku + i - c0);   // A(i, c0 + jj) = a0[jj * (ldab - 1)]
-#pragma unroll
-          for (int jj = 0; jj < NB; ++jj) {
-            const int j = c0 + jj;
-            const bool in = jj < cw && i - j <= kl && j - i <= ku;
-            acc[jj] = in ? a0[(int64_t)jj * (ldab - 1)] : T(0);
+          // the panel's L slab and L11^{-1}, written by CTA 0, by TMA into shared memory
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const unsigned bl = (unsigned)(NB * kl * sizeof(T)), bi = (unsigned)(NB * NB * sizeof(T));
+          mbar_expect_tx(bar, bl + bi);
+          tma_bulk_g2s(Li, DI + (int64_t)p * 2 * NB * NB, bi, bar);
+          if (bl) tma_bulk_g2s(Ls, LS + (int64_t)p * NB * kl, bl, bar);
+          int it = 0;
+          while (!mbar_try_wait(bar, (unsigned)(uses & 1))) {
+            if (++it > WAIT_LIMIT) {
+              ok = false;
+              break;
+            }
           }
-#pragma unroll
-          for (int jj = 0; jj < NB; ++jj) {
-            T t = acc[jj];
-#pragma unroll
-            for (int p = 0; p < NB; ++p) t -= l[p] * Ub[p * SP + jj];
-            acc[jj] = t;
-          }
-#pragma unroll
-          for (int jj = 0; jj < NB; ++jj) {
-            const int j = c0 + jj;
-            if (jj < cw && i - j <= kl && j - i <= ku) a0[(int64_t)jj * (ldab - 1)] = acc[jj];
-          }
+        }
+        if (!ok) {
+          atomicOr(st, 2);
+          abort_flag = 1;
         }
       }
+      ++uses;
       __syncthreads();
-      if (cb == kb + 1) {
-        // look-ahead: block kb+1 is final up to its own panel; factor and publish it
-        lu_factor_panel_reg<T>(AB, n, kl, ku, ldab, kb + 1, prow, diag, dinv, status + sid);
-        __syncthreads();
-        if (tid == 0) {
-          __threadfence();
-          st_release(flags + kb + 1, epoch);
+      if (abort_flag) return;
+      for (int cb = first; cb <= cbl; cb += LU_BULK) {
+        const int c0 = cb * NB, cw = min(NB, n - c0);
+        form_u12<T>(Li, Ub, Uv, AB, US, k0, kw, c0, cw, kl, ku, ldab);
+        // A22 -= L21 U12: warp pairs share 32 rows (lane = row), each warp one half of the columns
+        const int h = warp & 1, groups = nwarp / 2;
+        for (int rb = kw + (warp >> 1) * 32; rb < R; rb += groups * 32) {
+          const int r = rb + lane;
+          if (r < R) {
+            const int i = k0 + r;
+            const int cs = c0 + h * HALF;
+            T acc[HALF];
+            T* a0 = AB + (int64_t)cs * ldab + (ku + i - cs);    // A(i, cs + jj) = a0[jj * (ldab - 1)]
+#pragma unroll
+            for (int jj = 0; jj < HALF; ++jj) {
+              const int j = cs + jj;
+              acc[jj] = (j < c0 + cw && i - j <= kl && j - i <= ku) ? __ldcg(a0 + (int64_t)jj * (ldab - 1)) : T(0);
+            }
+            // L(i, k0 + q) = Ls[q * kl + (r - q - 1)] for 0 <= r - q - 1 < kl
+            row_update<T, HALF>(acc, [&](int q) {
+              const int o = r - q - 1;
+              return (q < kw && o < kl) ? Ls[q * kl + o] : T(0);
+            }, Uv, h * HALF);
+#pragma unroll
+            for (int jj = 0; jj < HALF; ++jj) {
+              const int j = cs + jj;
+              if (j < c0 + cw && i - j <= kl && j - i <= ku) a0[(int64_t)jj * (ldab - 1)] = acc[jj];
+            }
+          }
         }
+        __syncthreads();
+        if (tid == 0) st_release(cnt + cb, cnt_word(epoch, p - max(0, cb - D) + 1));
       }
     }
   }
 }
 
 template <typename T>
-cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_max, T* band, T* dinv,
-                           int* flags, int flags_stride, int epoch, int* status, cudaStream_t st,
+cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_max, T* band, T* lslab, T* uslab,
+                           T* dinv, int* sync, int sync_stride, int epoch, int* status, cudaStream_t st,
                            const int* skip) {
   if (nsys == 0) return cudaSuccess;
-  if (LU_NB + kl_max > LU_RPT * LU_THREADS) return cudaErrorInvalidValue;
-  size_t smem = ((size_t)(LU_NB + kl_max) * SP + LU_NB * SP + LU_NB * LU_NB + SP + LU_NB * SP) * sizeof(T);
+  if (LU_NB + kl_max > lu_threads<T>()) return cudaErrorInvalidValue;
+  // mbarrier (128 B), Uv, Li (NB x NB each), Ub (NB x SP), then the larger of
+  // [pivot rows 2 (NB + 2) + critical panel (NB + kl) x SP] and the bulk slab NB x kl
+  const size_t head = (size_t)2 * LU_NB * LU_NB + LU_NB * SP;
+  const size_t tail = std::max((size_t)2 * (LU_NB + 2) + (size_t)(LU_NB + kl_max) * SP, (size_t)LU_NB * kl_max);
+  const size_t smem = 128 + (head + tail) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(band_lu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  band_lu_kernel<T><<<nsys * LU_CLUSTER, LU_THREADS, smem, st>>>(sys, list, band, dinv, flags, flags_stride, epoch,
-                                                                 status, skip);
+  band_lu_kernel<T><<<nsys * LU_CLUSTER, lu_threads<T>(), smem, st>>>(sys, list, band, lslab, uslab, dinv, sync,
+                                                                      sync_stride, epoch, status, skip);
   return cudaGetLastError();
 }
 
-// Diagonal-block inverses of an already factored unit-L / U band (one CTA per system).
+// Diagonal-block inverses of a factored unit-L / U band: one CTA per (block, system).
 template <typename T>
-__global__ void __launch_bounds__(LU_THREADS) band_dinv_kernel(const SysDev* __restrict__ sys,
-                                                              const int* __restrict__ list, const T* __restrict__ band,
-                                                              T* __restrict__ dinv_all) {
+__global__ void __launch_bounds__(64) band_dinv_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list,
+                                                      const T* __restrict__ band, T* __restrict__ dinv_all,
+                                                      const int* skip) {
+  if (skip && *skip) return;
   constexpr int NB = LU_NB;
-  const SysDev S = sys[list[blockIdx.x]];
+  const SysDev S = sys[list[blockIdx.y]];
+  const int nblk = (S.n + NB - 1) / NB;
+  const int kb = blockIdx.x;
+  if (kb >= nblk) return;
   const T* AB = band + S.band_off;
   __shared__ T D[NB * SP];
-  const int nblk = (S.n + NB - 1) / NB;
-  for (int kb = 0; kb < nblk; ++kb) {
-    const int k0 = kb * NB, kw = min(NB, S.n - k0);
-    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-      const int c = idx / NB, r = idx - c * NB;
-      const int i = k0 + r, j = k0 + c;
-      D[r * SP + c] = (r < kw && c < kw && i - j <= S.kl && j - i <= S.ku) ? AB[(int64_t)j * S.ldab + (S.ku + i - j)] : T(0);
-    }
-    __syncthreads();
-    diag_inverses<T>(D, kw, dinv_all + S.dinv_off + (int64_t)kb * 2 * NB * NB);
-    __syncthreads();
+  const int k0 = kb * NB, kw = min(NB, S.n - k0);
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    const int c = idx / NB, r = idx - c * NB;
+    const int i = k0 + r, j = k0 + c;
+    D[r * SP + c] = (r < kw && c < kw && i - j <= S.kl && j - i <= S.ku) ? AB[(int64_t)j * S.ldab + (S.ku + i - j)] : T(0);
+  }
+  __syncthreads();
+  diag_inverses<T>(D, kw, dinv_all + S.dinv_off + (int64_t)kb * 2 * NB * NB);
+}
+
+template <typename T>
+cudaError_t launch_band_dinv(const SysDev* sys, const int* list, int nsys, int nblk_max, const T* band, T* dinv,
+                             cudaStream_t st, const int* skip) {
+  if (nsys == 0) return cudaSuccess;
+  count_launches(1);
+  band_dinv_kernel<T><<<dim3(nblk_max, nsys), 64, 0, st>>>(sys, list, band, dinv, skip);
+  return cudaGetLastError();
+}
+
+// Slabs of an already factored band (used once for the Darcy factors).
+template <typename T>
+__global__ void band_to_slab_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list,
+                                    const T* __restrict__ band, T* __restrict__ lslab, T* __restrict__ uslab) {
+  const SysDev S = sys[list[blockIdx.y]];
+  const T* AB = band + S.band_off;
+  const int64_t tot = (int64_t)S.n * S.ldab;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / S.ldab), off = (int)(idx % S.ldab);
+    const int i = off - S.ku + j;
+    if (i < 0 || i >= S.n) continue;
+    if (i > j) lslab[S.lslab_off + lsl_idx(i, j, S.kl)] = AB[idx];
+    else if (i < j) uslab[S.uslab_off + usl_idx(i, j, S.ku)] = AB[idx];
   }
 }
 
 template <typename T>
-cudaError_t launch_band_dinv(const SysDev* sys, const int* list, int nsys, const T* band, T* dinv, cudaStream_t st) {
+cudaError_t launch_band_to_slab(const SysDev* sys, const int* list, int nsys, const T* band, T* lslab, T* uslab,
+                                cudaStream_t st) {
   if (nsys == 0) return cudaSuccess;
   count_launches(1);
-  band_dinv_kernel<T><<<nsys, LU_THREADS, 0, st>>>(sys, list, band, dinv);
+  band_to_slab_kernel<T><<<dim3(64, nsys), 256, 0, st>>>(sys, list, band, lslab, uslab);
   return cudaGetLastError();
 }
 
@@ -475,143 +678,172 @@ cudaError_t launch_chol_to_lu(const SysDev* sys_chol, const SysDev* sys_lu, cons
 }
 
 // ------------------------------------------------------------------------------ solves
-// x (+)= U^{-1} L^{-1} r for unit-lower L and upper U in the LU band layout, one CTA per
-// system.  Each block of LU_NB unknowns is finished by one warp with the stored inverse of
-// its diagonal block (a GEMV), then the rows coupled to it by the band are updated by all
-// threads with coalesced column reads.  The vector lives in shared memory in precision T.
+// x (+)= U^{-1} L^{-1} r for unit-lower L and upper U, one CTA per system.  The factors are
+// read from the per-block slabs: every block's slab (32 columns x kl or ku rows, contiguous)
+// and the inverse of its diagonal triangle arrive in shared memory with two TMA bulk copies
+// completing on an mbarrier, STAGES blocks ahead of the one being solved.  Each block is
+// finished by one warp with the inverse (a GEMV), then the rows coupled to it by the band are
+// updated by all threads.  The vector lives in shared memory in precision T.
 template <typename T, int STAGES>
 __global__ void __launch_bounds__(256) band_solve_kernel(const SysDev* __restrict__ sys,
                                                          const int* __restrict__ list,
-                                                         const T* __restrict__ band, const T* __restrict__ dinv_all,
+                                                         const T* __restrict__ lslab, const T* __restrict__ uslab,
+                                                         const T* __restrict__ dinv_all,
                                                          const double* __restrict__ rhs,
                                                          double* __restrict__ x, int accumulate, int kmax,
-                                                         const int* __restrict__ done, const int* skip) {
+                                                         const int* __restrict__ done, int* __restrict__ status,
+                                                         const int* skip) {
   if (skip && *skip) return;
   const int sid = list[blockIdx.x];
   if (done && done[sid]) return;
   const SysDev S = sys[sid];
-  const int n = S.n, kl = S.kl, ku = S.ku, ld = S.ldab;
-  const T* AB = band + S.band_off;
-  const T* DI = dinv_all + S.dinv_off;
+  const int n = S.n, kl = S.kl, ku = S.ku;
   constexpr int NB = LU_NB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* dib = reinterpret_cast<T*>(smem_raw);                 // STAGES x NB*NB diagonal-block inverse
-  T* slab = dib + STAGES * NB * NB;                        // STAGES x NB*kmax band slab
-  T* v = slab + (size_t)STAGES * NB * kmax;                // n
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                  // STAGES mbarriers
+  T* stage0 = reinterpret_cast<T*>(smem_raw + 128);
+  const size_t stage_elems = (size_t)NB * NB + (size_t)NB * kmax;         // inverse, then slab
+  T* v = stage0 + STAGES * stage_elems;                                   // n
   __shared__ T yb[NB];
+  __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nblk = (n + NB - 1) / NB;
+  const int total = 2 * nblk;                                             // forward then backward
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int k = 0; k < STAGES; ++k) mbar_init(bar + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   const double* b = rhs + S.x_off;
   for (int i = tid; i < n; i += blockDim.x) v[i] = (T)b[i];
-  const int nblk = (n + NB - 1) / NB;
-  // slab of block kb: forward  = columns k0+c, rows k0+c+1 .. k0+c+kl      (L below the diagonal)
-  //                   backward = columns k0+c, rows k0+c-ku .. k0+c-1      (U above the diagonal)
-  auto issue = [&](int kb, int buf, bool fwd) {
+  __syncthreads();
+  auto issue = [&](int g) {   // thread 0 only
+    const int s = g % STAGES;
+    const bool fwd = g < nblk;
+    const int kb = fwd ? g : 2 * nblk - 1 - g;
+    const int w = fwd ? kl : ku;
+    T* dst = stage0 + s * stage_elems;
+    const T* di = dinv_all + S.dinv_off + (int64_t)kb * 2 * NB * NB + (fwd ? 0 : NB * NB);
+    const T* sl = (fwd ? lslab + S.lslab_off : uslab + S.uslab_off) + (int64_t)kb * NB * w;
+    const unsigned bi = NB * NB * sizeof(T), bs = (unsigned)(NB * w * sizeof(T));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar + s, bi + bs);
+    tma_bulk_g2s(dst, di, bi, bar + s);
+    if (bs) tma_bulk_g2s(dst + NB * NB, sl, bs, bar + s);
+  };
+  if (tid == 0)
+    for (int g = 0; g < STAGES && g < total; ++g) issue(g);
+  for (int g = 0; g < total; ++g) {
+    const int s = g % STAGES;
+    const unsigned parity = (unsigned)((g / STAGES) & 1);
+    if (tid == 0) {
+      int it = 0;
+      while (!mbar_try_wait(bar + s, parity)) {
+        if (++it > WAIT_LIMIT) {
+          atomicOr(status + sid, 2);
+          abort_flag = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (abort_flag) {
+      // let the copies already issued land before leaving (bounded)
+      if (tid == 0)
+        for (int h = g + 1; h < g + STAGES && h < total; ++h)
+          for (int it = 0; !mbar_try_wait(bar + h % STAGES, (unsigned)((h / STAGES) & 1)) && it < WAIT_LIMIT; ++it) {
+          }
+      return;
+    }
+    const bool fwd = g < nblk;
+    const int kb = fwd ? g : 2 * nblk - 1 - g;
     const int k0 = kb * NB, kw = min(NB, n - k0);
     const int w = fwd ? kl : ku;
-    T* sl = slab + (size_t)buf * NB * kmax;
-    for (int idx = tid; idx < NB * w; idx += blockDim.x) {
-      const int c = idx / w, o = idx - c * w;
-      const int j = k0 + c;
-      const int i = fwd ? j + 1 + o : j - ku + o;
-      const int boff = fwd ? ku + 1 + o : o;
-      if (c < kw && i >= 0 && i < n) cp_async_elem(sl + idx, AB + (int64_t)j * ld + boff);
-      else sl[idx] = T(0);
+    const T* Dv = stage0 + s * stage_elems;
+    const T* sl = Dv + NB * NB;
+    if (warp == 0) {
+      T acc = T(0);
+#pragma unroll 8
+      for (int p = 0; p < kw; ++p) acc += Dv[p * NB + lane] * v[k0 + p];
+      yb[lane] = lane < kw ? acc : T(0);
     }
-    const T* src = DI + (int64_t)kb * 2 * NB * NB + (fwd ? 0 : NB * NB);
-    T* dst = dib + (size_t)buf * NB * NB;
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) cp_async_elem(dst + idx, src + idx);
-    cp_async_commit();
-  };
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool fwd = pass == 0;
-    const int w = fwd ? kl : ku;
-    issue(fwd ? 0 : nblk - 1, 0, fwd);
-    for (int t = 0; t < nblk; ++t) {
-      const int kb = fwd ? t : nblk - 1 - t;
-      const int buf = STAGES == 2 ? (t & 1) : 0;
-      if (STAGES == 2) {
-        if (t + 1 < nblk) {
-          issue(fwd ? kb + 1 : kb - 1, buf ^ 1, fwd);
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
-        }
-      } else {
-        if (t > 0) issue(kb, 0, fwd);    // single buffer: fetch this block now
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-      const int k0 = kb * NB, kw = min(NB, n - k0);
-      const T* Dv = dib + (size_t)buf * NB * NB;
-      const T* sl = slab + (size_t)buf * NB * kmax;
-      if (warp == 0) {
-        T acc = T(0);
+    __syncthreads();
+    if (tid < kw) v[k0 + tid] = yb[tid];
+    if (fwd) {
+      const int rend = min(n, k0 + kw + kl);
+      for (int i = k0 + kw + tid; i < rend; i += blockDim.x) {
+        T acc = v[i];
+        // L(i, k0 + c) = sl[c * kl + (i - k0 - c - 1)], valid for 0 <= i - k0 - c - 1 < kl
 #pragma unroll 8
-        for (int p = 0; p < kw; ++p) acc += Dv[p * NB + lane] * v[k0 + p];
-        yb[lane] = lane < kw ? acc : T(0);
-      }
-      __syncthreads();
-      if (tid < kw) v[k0 + tid] = yb[tid];
-      if (fwd) {
-        const int rend = min(n, k0 + kw + kl);
-        for (int i = k0 + 1 + tid; i < rend; i += blockDim.x) {
-          if (i < k0 + kw) continue;
-          T acc = v[i];
-          // L(i, k0 + c) = sl[c * w + (i - k0 - c - 1)], valid for 0 <= i - k0 - c - 1 < kl
-#pragma unroll 8
-          for (int c = 0; c < kw; ++c) {
-            const int o = i - k0 - c - 1;
-            if (o >= 0 && o < kl) acc -= sl[c * w + o] * yb[c];
-          }
-          v[i] = acc;
+        for (int c = 0; c < kw; ++c) {
+          const int o = i - k0 - c - 1;
+          if (o < kl) acc -= sl[c * w + o] * yb[c];
         }
-      } else {
-        const int rbeg = max(0, k0 - ku);
-        for (int i = rbeg + tid; i < k0; i += blockDim.x) {
-          T acc = v[i];
-          // U(i, k0 + c) = sl[c * w + (i - k0 - c + ku)], valid for 0 <= i - k0 - c + ku < ku
-#pragma unroll 8
-          for (int c = 0; c < kw; ++c) {
-            const int o = i - k0 - c + ku;
-            if (o >= 0 && o < ku) acc -= sl[c * w + o] * yb[c];
-          }
-          v[i] = acc;
-        }
+        v[i] = acc;
       }
-      __syncthreads();
+    } else {
+      const int rbeg = max(0, k0 - ku);
+      for (int i = rbeg + tid; i < k0; i += blockDim.x) {
+        T acc = v[i];
+        // U(i, k0 + c) = sl[c * ku + (i - k0 - c + ku)], valid for 0 <= i - k0 - c + ku
+#pragma unroll 8
+        for (int c = 0; c < kw; ++c) {
+          const int o = i - k0 - c + ku;
+          if (o >= 0) acc -= sl[c * w + o] * yb[c];
+        }
+        v[i] = acc;
+      }
     }
+    __syncthreads();
+    if (tid == 0 && g + STAGES < total) issue(g + STAGES);
   }
   double* xo = x + S.x_off;
   for (int i = tid; i < n; i += blockDim.x) xo[i] = accumulate ? xo[i] + (double)v[i] : (double)v[i];
 }
 
 template <typename T>
-cudaError_t launch_band_solve(const SysDev* sys, const int* list, int nsys, int n_max, int kmax, const T* band,
-                              const T* dinv, const double* r, double* x, int accumulate, const int* done,
-                              cudaStream_t st, const int* skip) {
+cudaError_t launch_band_solve(const SysDev* sys, const int* list, int nsys, int n_max, int kmax, const T* lslab,
+                              const T* uslab, const T* dinv, const double* r, double* x, int accumulate,
+                              const int* done, int* status, cudaStream_t st, const int* skip) {
   if (nsys == 0) return cudaSuccess;
   int dev = 0, smem_max = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t need2 = ((size_t)2 * LU_NB * LU_NB + (size_t)2 * LU_NB * kmax + n_max + 4) * sizeof(T);
-  const size_t need1 = ((size_t)LU_NB * LU_NB + (size_t)LU_NB * kmax + n_max + 4) * sizeof(T);
+  const size_t stage = ((size_t)LU_NB * LU_NB + (size_t)LU_NB * kmax) * sizeof(T);
+  const size_t vec = ((size_t)n_max + 4) * sizeof(T);
+  const size_t static_smem = 1024;
   count_launches(1);
-  if (need2 + 1024 <= (size_t)smem_max) {
-    cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need2);
-    if (e != cudaSuccess) return e;
-    band_solve_kernel<T, 2><<<nsys, 256, need2, st>>>(sys, list, band, dinv, r, x, accumulate, kmax, done, skip);
-  } else {
-    if (need1 + 1024 > (size_t)smem_max) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need1);
-    if (e != cudaSuccess) return e;
-    band_solve_kernel<T, 1><<<nsys, 256, need1, st>>>(sys, list, band, dinv, r, x, accumulate, kmax, done, skip);
+  for (int stages = 3; stages >= 1; --stages) {
+    const size_t need = 128 + stages * stage + vec;
+    if (need + static_smem > (size_t)smem_max) continue;
+    cudaError_t e;
+    if (stages == 3) {
+      e = cudaFuncSetAttribute(band_solve_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      if (e != cudaSuccess) return e;
+      band_solve_kernel<T, 3><<<nsys, 256, need, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax, done,
+                                                       status, skip);
+    } else if (stages == 2) {
+      e = cudaFuncSetAttribute(band_solve_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      if (e != cudaSuccess) return e;
+      band_solve_kernel<T, 2><<<nsys, 256, need, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax, done,
+                                                       status, skip);
+    } else {
+      e = cudaFuncSetAttribute(band_solve_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      if (e != cudaSuccess) return e;
+      band_solve_kernel<T, 1><<<nsys, 256, need, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax, done,
+                                                       status, skip);
+    }
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------------------ residual
-// r = b - A x (FP64 CSR), relative residual and refinement control.  Stops a system when
-// ||r|| <= tol ||b|| or when the residual stagnates (||r_k|| > 0.5 ||r_{k-1}||).
+// r = b - A x (FP64 CSR), relative residual and refinement control.  RES_CHUNKS CTAs per
+// system each handle a slice of rows and store partial sums of ||r||^2 and ||b||^2; the last
+// CTA of a system to finish (atomic ticket) adds the partials in slice order, so the result
+// does not depend on scheduling.  A system stops when ||r|| <= tol ||b|| or when the residual
+// stagnates (||r_k|| > 0.5 ||r_{k-1}||).
 __global__ void __launch_bounds__(256) residual_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list,
                                                        const int32_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ colidx,
@@ -619,10 +851,11 @@ __global__ void __launch_bounds__(256) residual_kernel(const SysDev* __restrict_
                                                        const double* __restrict__ b, const double* __restrict__ x,
                                                        double* __restrict__ r, double* __restrict__ rel,
                                                        double* __restrict__ rel_prev, int* __restrict__ done,
-                                                       int* __restrict__ iters, double tol, int first,
+                                                       int* __restrict__ iters, double* __restrict__ partial,
+                                                       int* __restrict__ ticket, double tol, int first,
                                                        const int* skip) {
   if (skip && *skip) return;
-  const int sid = list[blockIdx.x];
+  const int sid = list[blockIdx.y];
   if (!first && done[sid]) return;
   const SysDev S = sys[sid];
   const int32_t* rp = rowptr + S.rp_off;
@@ -631,67 +864,95 @@ __global__ void __launch_bounds__(256) residual_kernel(const SysDev* __restrict_
   const double* bb = b + S.x_off;
   const double* xx = x + S.x_off;
   double* rr = r + S.x_off;
+  const int chunk = (S.n + RES_CHUNKS - 1) / RES_CHUNKS;
+  const int r0 = blockIdx.x * chunk, r1 = min(S.n, r0 + chunk);
   double sr = 0, sb = 0;
-  for (int i = threadIdx.x; i < S.n; i += blockDim.x) {
-    double acc = bb[i];
+  // one warp per row: lanes stride over the row's entries
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = r0 + warp; i < r1; i += nw) {
+    double acc = 0.0;
     if (!first)
-      for (int k = rp[i]; k < rp[i + 1]; ++k) acc -= va[k] * xx[ci[k]];
-    rr[i] = acc;
-    sr += acc * acc;
-    sb += bb[i] * bb[i];
+      for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) acc += va[k] * xx[ci[k]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const double ri = bb[i] - acc;
+      rr[i] = ri;
+      sr += ri * ri;
+      sb += bb[i] * bb[i];
+    }
   }
   __shared__ double red[2][256];
   red[0][threadIdx.x] = sr;
   red[1][threadIdx.x] = sb;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + s];
-      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if ((int)threadIdx.x < s2) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s2];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s2];
     }
     __syncthreads();
   }
+  __shared__ int last;
   if (threadIdx.x == 0) {
-    double nb = sqrt(red[1][0]);
-    double relres = nb > 0 ? sqrt(red[0][0]) / nb : 0.0;
-    if (first) {
-      done[sid] = (nb == 0.0) ? 1 : 0;
-      iters[sid] = 0;
-      rel_prev[sid] = 1.0;
-      rel[sid] = nb == 0.0 ? 0.0 : 1.0;
-    } else {
-      iters[sid] += 1;
-      double prev = rel[sid];
-      rel_prev[sid] = prev;
-      rel[sid] = relres;
-      if (relres <= tol || relres > 0.5 * prev || !(relres == relres)) done[sid] = 1;
-    }
+    double* pp = partial + ((int64_t)sid * RES_CHUNKS + blockIdx.x) * 2;
+    pp[0] = red[0][0];
+    pp[1] = red[1][0];
+    __threadfence();
+    last = atomicAdd(ticket + sid, 1) == RES_CHUNKS - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double tr = 0, tb = 0;
+  const double* pp = partial + (int64_t)sid * RES_CHUNKS * 2;
+  for (int c = 0; c < RES_CHUNKS; ++c) {
+    tr += __ldcg(pp + 2 * c);
+    tb += __ldcg(pp + 2 * c + 1);
+  }
+  ticket[sid] = 0;
+  const double nb = sqrt(tb);
+  const double relres = nb > 0 ? sqrt(tr) / nb : 0.0;
+  if (first) {
+    done[sid] = (nb == 0.0) ? 1 : 0;
+    iters[sid] = 0;
+    rel_prev[sid] = 1.0;
+    rel[sid] = nb == 0.0 ? 0.0 : 1.0;
+  } else {
+    iters[sid] += 1;
+    const double prev = rel[sid];
+    rel_prev[sid] = prev;
+    rel[sid] = relres;
+    if (relres <= tol || relres > 0.5 * prev || !(relres == relres)) done[sid] = 1;
   }
 }
 
 cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const int32_t* rowptr,
                             const int32_t* colidx, const double* vals, const double* b, const double* x,
-                            double* r, double* rel, double* rel_prev, int* done, int* iters, double tol,
-                            int first, cudaStream_t st, const int* skip) {
+                            double* r, double* rel, double* rel_prev, int* done, int* iters, double* partial,
+                            int* ticket, double tol, int first, cudaStream_t st, const int* skip) {
   if (nsys == 0) return cudaSuccess;
   count_launches(1);
-  residual_kernel<<<nsys, 256, 0, st>>>(sys, list, rowptr, colidx, vals, b, x, r, rel, rel_prev, done,
-                                        iters, tol, first, skip);
+  residual_kernel<<<dim3(RES_CHUNKS, nsys), 256, 0, st>>>(sys, list, rowptr, colidx, vals, b, x, r, rel, rel_prev,
+                                                          done, iters, partial, ticket, tol, first, skip);
   return cudaGetLastError();
 }
 
-#define TPNS_INST(T)                                                                                      \
-  template cudaError_t launch_band_fill<T>(const SysDev*, const int*, int, const int32_t*, const int32_t*, \
-                                           const double*, T*, int, int64_t, cudaStream_t, const int*);     \
-  template cudaError_t launch_band_lu<T>(const SysDev*, const int*, int, int, T*, T*, int*, int, int, int*,\
-                                         cudaStream_t, const int*);                                        \
-  template cudaError_t launch_band_dinv<T>(const SysDev*, const int*, int, const T*, T*, cudaStream_t);    \
-  template cudaError_t launch_band_chol<T>(const SysDev*, const int*, int, T*, int*, cudaStream_t);        \
-  template cudaError_t launch_chol_to_lu<T>(const SysDev*, const SysDev*, const int*, int, const T*, T*,   \
-                                            cudaStream_t);                                                 \
-  template cudaError_t launch_band_solve<T>(const SysDev*, const int*, int, int, int, const T*, const T*,  \
-                                            const double*, double*, int, const int*, cudaStream_t,         \
-                                            const int*);
+#define TPNS_INST(T)                                                                                       \
+  template cudaError_t launch_band_fill<T>(const SysDev*, const int*, int, const int32_t*, const int32_t*,  \
+                                           const double*, T*, int, int64_t, cudaStream_t, const int*);      \
+  template cudaError_t launch_band_lu<T>(const SysDev*, const int*, int, int, T*, T*, T*, T*, int*, int, int,\
+                                         int*, cudaStream_t, const int*);                                   \
+  template cudaError_t launch_band_dinv<T>(const SysDev*, const int*, int, int, const T*, T*, cudaStream_t, \
+                                           const int*);                                                     \
+  template cudaError_t launch_band_to_slab<T>(const SysDev*, const int*, int, const T*, T*, T*,             \
+                                              cudaStream_t);                                                \
+  template cudaError_t launch_band_chol<T>(const SysDev*, const int*, int, T*, int*, cudaStream_t);         \
+  template cudaError_t launch_chol_to_lu<T>(const SysDev*, const SysDev*, const int*, int, const T*, T*,    \
+                                            cudaStream_t);                                                  \
+  template cudaError_t launch_band_solve<T>(const SysDev*, const int*, int, int, int, const T*, const T*,   \
+                                            const T*, const double*, double*, int, const int*, int*,        \
+                                            cudaStream_t, const int*);
 TPNS_INST(float)
 TPNS_INST(double)
 
