@@ -19,7 +19,11 @@
  *   - Errors are returned as tpns_status; no exception crosses the ABI.  A context whose
  *     call failed keeps a message readable with tpns_last_error().
  *   - A context is bound to the device that was current at tpns_create and to the CUDA
- *     stream given there; every call enqueues on that stream.
+ *     stream given there; every call enqueues on that stream.  With a NULL stream the
+ *     context creates its own blocking stream (ordered with the legacy default stream).
+ *   - A time step is captured once into a CUDA graph and replayed (all its loops have fixed
+ *     trip counts; convergence is decided on the device); while per-phase timing is on
+ *     (tpns_set_timing) steps are launched kernel by kernel instead.
  *   - Field ids: 0 = u_x, 1 = u_y (conduit velocity, P2 nodes), 2 = p (conduit pressure,
  *     vertices), 3 = p_F (macro-fracture), 4 = p_f (micro-fracture), 5 = p_m (matrix), the
  *     last three on the P2 nodes of the porous mesh.  Global fine numbering: vertex

@@ -56,8 +56,11 @@ struct tpns_ctx {
   int64_t lslab_local_len = 0, uslab_local_len = 0, lslab_coarse_len = 0, uslab_coarse_len = 0;
   int nblk_max_osl = 1, nblk_max_dl = 1, nblk_max_cf = 1, nblk_max_cp = 1;
   int flags_stride = 1;
-  int lu_epoch = 0;
   bool host_only = false;
+  // CUDA graphs of one step: coarse solve + hot path, and hot path alone
+  bool use_graph = true;
+  bool own_stream = false;
+  cudaGraphExec_t g_full = nullptr, g_local = nullptr;
   // device
   ProbDev* d_probs = nullptr;
   int32_t *d_eprob = nullptr, *d_e6 = nullptr, *d_e3 = nullptr;
@@ -81,6 +84,7 @@ struct tpns_ctx {
   void *d_lslab_local = nullptr, *d_uslab_local = nullptr;
   double *d_lslab_coarse = nullptr, *d_uslab_coarse = nullptr;
   int* d_flags = nullptr;
+  int* d_epoch = nullptr;
   SysDev* d_sys_chol = nullptr;
   int *d_list_osl = nullptr, *d_list_cf = nullptr, *d_list_dl = nullptr, *d_list_cp = nullptr,
       *d_list_local = nullptr;
@@ -399,6 +403,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(upload(ctx, &ctx->d_sys, ctx->hsys));
   TRY(upload(ctx, &ctx->d_sys_chol, ctx->hsys_chol));
   ctx->flags_stride *= 2;   // panel flags, then per-block progress counters
+  TRY(dalloc(ctx, &ctx->d_epoch, 1));
+  CK(cudaMemset(ctx->d_epoch, 0, sizeof(int)));
   TRY(dalloc(ctx, &ctx->d_flags, (size_t)ctx->nsys * ctx->flags_stride));
   CK(cudaMemset(ctx->d_flags, 0, (size_t)ctx->nsys * ctx->flags_stride * sizeof(int)));
   TRY(upload(ctx, &ctx->d_chol, ctx->hchol));
@@ -722,7 +728,7 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
     CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
                                 ctx->d_band_coarse, 0, 0, st, skip));
     CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse, ctx->d_lslab_coarse,
-                              ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_flags, ctx->flags_stride, ++ctx->lu_epoch, ctx->d_status,
+                              ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_flags, ctx->flags_stride, ctx->d_epoch, ctx->d_status,
                               st, skip));
     CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->nblk_max_cf, ctx->d_band_coarse,
                                 ctx->d_dinv_coarse, st, skip));
@@ -768,7 +774,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   ph_end(ctx, PH_BAND_FILL);
   ph_begin(ctx, PH_BAND_LU);
   CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, lslab, uslab, dinv, ctx->d_flags,
-                       ctx->flags_stride, ++ctx->lu_epoch, ctx->d_status, st, nullptr));
+                       ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr));
   CK(launch_band_dinv<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->nblk_max_osl, band, dinv, st, nullptr));
   ph_end(ctx, PH_BAND_LU);
   // a8: solves with FP64-residual iterative refinement
@@ -806,7 +812,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   return TPNS_OK;
 }
 
-static tpns_status end_step(tpns_ctx* ctx) {
+static tpns_status end_step_device(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   const Layout& L = ctx->L;
   ph_begin(ctx, PH_COPIES);
@@ -814,8 +820,39 @@ static tpns_status end_step(tpns_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->d_pd_old, ctx->d_pd_new, (size_t)L.mpH.nn * 3 * 8, cudaMemcpyDeviceToDevice, st));
   CK(launch_set_time(ctx->d_tnow, ctx->d_step, ctx->dt, 1, st));
   ph_end(ctx, PH_COPIES);
-  ctx->step += 1;
   return TPNS_OK;
+}
+
+// Enqueue one time step: Step 1 (unless the coarse state was supplied), Steps 3-4, copies.
+static tpns_status enqueue_step(tpns_ctx* ctx, bool coarse) {
+  if (coarse) {
+    ph_begin(ctx, PH_COARSE);
+    TRY(coarse_step(ctx));
+    ph_end(ctx, PH_COARSE);
+  }
+  if (ctx->prec == TPNS_FP64) TRY(local_step<double>(ctx));
+  else TRY(local_step<float>(ctx));
+  return end_step_device(ctx);
+}
+
+// Capture one step into a graph; on failure the caller runs the step eagerly.
+static bool capture_step(tpns_ctx* ctx, bool coarse, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  tpns_status s = enqueue_step(ctx, coarse);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  bool ok = s == TPNS_OK && e == cudaSuccess && g != nullptr;
+  if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    *out = nullptr;
+  }
+  ctx->err.clear();
+  return ok;
 }
 
 static tpns_status read_stats(tpns_ctx* ctx) {
@@ -866,14 +903,18 @@ static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
       CK(cudaMemcpyAsync(ctx->d_uc_new, ctx->traj[k + 1], nu * 8, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(ctx->d_pc_new, ctx->traj[k + 1] + nu, npc * 8, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(ctx->d_pd_new, ctx->traj[k + 1] + nu + npc, npd * 8, cudaMemcpyDeviceToDevice, st));
-    } else {
-      ph_begin(ctx, PH_COARSE);
-      TRY(coarse_step(ctx));
-      ph_end(ctx, PH_COARSE);
     }
-    if (ctx->prec == TPNS_FP64) TRY(local_step<double>(ctx));
-    else TRY(local_step<float>(ctx));
-    TRY(end_step(ctx));
+    bool graph = ctx->use_graph && !ctx->timing;
+    if (graph) {
+      cudaGraphExec_t& ex = from_traj ? ctx->g_local : ctx->g_full;
+      if (!ex && !capture_step(ctx, !from_traj, &ex)) {
+        ctx->use_graph = false;
+        graph = false;
+      }
+      if (graph) CK(cudaGraphLaunch(ex, ctx->stream));
+    }
+    if (!graph) TRY(enqueue_step(ctx, !from_traj));
+    ctx->step += 1;
   }
   return read_stats(ctx);
 }
@@ -1005,7 +1046,9 @@ static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, 
   csr_rowof_kernel<<<(n + 255) / 256, 256, 0, st>>>(rowptr, n, rowof);
   CKS(cudaGetLastError());
   CKS(launch_band_fill<T>(sysd, listd, 1, rowof, colidx, vals, band, 0, 0, st, nullptr));
-  CKS(launch_band_lu<T>(sysd, listd, 1, kl, band, lslab, uslab, dinv, flags, 2 * nblk, epoch, status, st, nullptr));
+  int* epoch_dev = flags + 2 * nblk;
+  CKS(cudaMemcpyAsync(epoch_dev, &epoch, sizeof(int), cudaMemcpyHostToDevice, st));
+  CKS(launch_band_lu<T>(sysd, listd, 1, kl, band, lslab, uslab, dinv, flags, 2 * nblk, epoch_dev, status, st, nullptr));
   CKS(launch_band_dinv<T>(sysd, listd, 1, nblk, band, dinv, st, nullptr));
   const bool fp64 = sizeof(T) == 8;
   const int maxit = 12;
@@ -1107,6 +1150,11 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   if (!ctx) { g_err = "host allocation failed"; return TPNS_ENOMEM; }
   cudaGetDevice(&ctx->device);
   ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (!ctx->stream) {
+    // a blocking stream keeps the ordering with the legacy default stream and can be captured
+    if (cudaStreamCreate(&ctx->stream) == cudaSuccess) ctx->own_stream = true;
+    else ctx->stream = nullptr;
+  }
   ctx->prec = precision;
   ctx->dt = dt;
   Phys& P = ctx->phys;
@@ -1175,7 +1223,7 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
   void* lsl = get((size_t)nblk * LU_NB * kl * tsz);
   void* usl = get((size_t)nblk * LU_NB * ku * tsz);
   SysDev* sysd = (SysDev*)get(sizeof(SysDev));
-  int* ints = (int*)get(sizeof(int) * (5 + 2 * (size_t)nblk));
+  int* ints = (int*)get(sizeof(int) * (6 + 2 * (size_t)nblk));
   int32_t* rowof = (int32_t*)get(sizeof(int32_t) * (size_t)std::max(nnz, 1));
   double* dbl = (double*)get(sizeof(double) * ((size_t)n + 2 + 2 * RES_CHUNKS));
   tpns_status out;
@@ -1183,7 +1231,7 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
     g_err = "cudaMalloc failed";
     out = TPNS_ENOMEM;
   } else {
-    cudaMemsetAsync(ints, 0, sizeof(int) * (5 + 2 * (size_t)nblk), st);
+    cudaMemsetAsync(ints, 0, sizeof(int) * (6 + 2 * (size_t)nblk), st);
     int* listd = ints;
     int* done = ints + 1;
     int* iters = ints + 2;
@@ -1237,7 +1285,7 @@ tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int
   const size_t o_lsl = take((size_t)nblk * LU_NB * kl * tsz);
   const size_t o_usl = take((size_t)nblk * LU_NB * ku * tsz);
   const size_t o_sys = take(sizeof(SysDev));
-  const size_t o_ints = take(sizeof(int) * (5 + 2 * (size_t)nblk));
+  const size_t o_ints = take(sizeof(int) * (6 + 2 * (size_t)nblk));
   const size_t o_rowof = take(sizeof(int32_t) * (size_t)std::max(nnz, 1));
   const size_t o_dbl = take(sizeof(double) * ((size_t)n + 2 + 2 * RES_CHUNKS));
   if (nnz < 0 || off > (size_t)TPNS_NOALLOC_SCRATCH_BYTES) {
@@ -1247,7 +1295,7 @@ tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int
   }
   int* ints = reinterpret_cast<int*>(base + o_ints);
   // done, iters, status and the panel flags / block counters must start at zero
-  if (cudaMemsetAsync(ints, 0, sizeof(int) * (5 + 2 * (size_t)nblk), st) != cudaSuccess) {
+  if (cudaMemsetAsync(ints, 0, sizeof(int) * (6 + 2 * (size_t)nblk), st) != cudaSuccess) {
     g_err = "cudaMemsetAsync failed";
     return TPNS_EDEVICE;
   }
@@ -1319,7 +1367,8 @@ tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps) {
       CK(cudaMemcpyAsync(slot, ctx->d_uc_new, nu * 8, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(slot + nu, ctx->d_pc_new, npc * 8, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(slot + nu + npc, ctx->d_pd_new, npd * 8, cudaMemcpyDeviceToDevice, st));
-      TRY(end_step(ctx));
+      TRY(end_step_device(ctx));
+      ctx->step += 1;
     } else {
       CK(cudaMemcpyAsync(slot, ctx->d_uc_old, nu * 8, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(slot + nu, ctx->d_pc_new, npc * 8, cudaMemcpyDeviceToDevice, st));
@@ -1425,6 +1474,10 @@ const char* tpns_last_error(const tpns_ctx* ctx) {
 
 void tpns_destroy(tpns_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->g_full) cudaGraphExecDestroy(ctx->g_full);
+  if (ctx->g_local) cudaGraphExecDestroy(ctx->g_local);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   for (void* p : ctx->allocs) cudaFree(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto& p : ctx->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }

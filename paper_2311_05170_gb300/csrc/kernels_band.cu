@@ -366,8 +366,9 @@ template <typename T>
 __global__ void __cluster_dims__(LU_CLUSTER, 1, 1) __launch_bounds__(lu_threads<T>(), 1)
 band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* __restrict__ band,
                T* __restrict__ lslab, T* __restrict__ uslab, T* __restrict__ dinv_all, int* __restrict__ sync_all,
-               int sync_stride, int epoch, int* __restrict__ status, const int* skip) {
+               int sync_stride, const int* __restrict__ epoch_ptr, int* __restrict__ status, const int* skip) {
   if (skip && *skip) return;
+  const int epoch = *epoch_ptr;   // this factorisation's tag for the panel flags and counters
   constexpr int NB = LU_NB;
   constexpr int THREADS = lu_threads<T>();
   constexpr int HALF = NB / 2;
@@ -516,9 +517,13 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
   }
 }
 
+// a new tag for the next factorisation (kept on the device so that a captured graph replays
+// with fresh tags)
+__global__ void bump_kernel(int* p) { *p = (*p % 0x7FFFF) + 1; }
+
 template <typename T>
 cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_max, T* band, T* lslab, T* uslab,
-                           T* dinv, int* sync, int sync_stride, int epoch, int* status, cudaStream_t st,
+                           T* dinv, int* sync, int sync_stride, int* epoch, int* status, cudaStream_t st,
                            const int* skip) {
   if (nsys == 0) return cudaSuccess;
   if (LU_NB + kl_max > lu_threads<T>()) return cudaErrorInvalidValue;
@@ -529,7 +534,8 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   const size_t smem = 128 + (head + tail) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(band_lu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  count_launches(1);
+  count_launches(2);
+  bump_kernel<<<1, 1, 0, st>>>(epoch);
   band_lu_kernel<T><<<nsys * LU_CLUSTER, lu_threads<T>(), smem, st>>>(sys, list, band, lslab, uslab, dinv, sync,
                                                                       sync_stride, epoch, status, skip);
   return cudaGetLastError();
@@ -941,7 +947,7 @@ cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const 
 #define TPNS_INST(T)                                                                                       \
   template cudaError_t launch_band_fill<T>(const SysDev*, const int*, int, const int32_t*, const int32_t*,  \
                                            const double*, T*, int, int64_t, cudaStream_t, const int*);      \
-  template cudaError_t launch_band_lu<T>(const SysDev*, const int*, int, int, T*, T*, T*, T*, int*, int, int,\
+  template cudaError_t launch_band_lu<T>(const SysDev*, const int*, int, int, T*, T*, T*, T*, int*, int, int*,\
                                          int*, cudaStream_t, const int*);                                   \
   template cudaError_t launch_band_dinv<T>(const SysDev*, const int*, int, int, const T*, T*, cudaStream_t, \
                                            const int*);                                                     \

@@ -143,6 +143,24 @@ def test_deterministic_and_precomputed_coarse_path_bitwise(native):
         assert np.array_equal(fa[k], fc[k]), k
 
 
+def test_graph_replay_equals_eager_launches_bitwise(native):
+    """Steps replayed from the captured CUDA graph and steps launched kernel by kernel (per-
+    phase timing on) give bit-identical fields."""
+    w = W.config_small(nsteps=3)
+    a = native.Solver(w, precision="fp32")
+    a.step(3)
+    fa = a.fields()
+    a.close()
+    b = native.Solver(w, precision="fp32")
+    b.set_timing(True)
+    b.step(3)
+    fb = b.fields()
+    assert b.timings()["band_lu"][1] == 3
+    b.close()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
 def test_refinement_statistics(native):
     w = W.config_graded(nsteps=2)
     s = native.Solver(w, precision="fp32")
