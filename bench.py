@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-sample-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=16)
+    ap.add_argument("--serving-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -165,12 +167,13 @@ def main():
     stream = torch.cuda.Stream()
     handle = stream.cuda_stream
 
-    def timed_hot(prec, timing=False):
+    def timed_hot(prec, with_phases=False):
+        """K hot-path steps replayed from the captured CUDA graph (the timed region); then,
+        optionally, the same number of steps launched kernel by kernel with per-phase CUDA
+        events (the phase breakdown used for the roofline)."""
         s = Solver(w, precision=prec, stream=handle)
-        s.coarse_precompute(Wm + K)
+        s.coarse_precompute(Wm + 2 * K)
         s.local_step(Wm)
-        if timing:
-            s.set_timing(True)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -178,32 +181,44 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         clk = Clocks(local)
-        if timing:
-            clk.start()
+        clk.start()
         torch.cuda.synchronize()
         e0.record(stream)
         s.local_step(K)
         e1.record(stream)
         torch.cuda.synchronize()
-        clocks = clk.stop() if timing else None
+        clocks = clk.stop()
         ms = e0.elapsed_time(e1)
         launches = launch_count() - l0
         if dist:
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        return s, ms, launches, clocks
+        phases = None
+        if with_phases:
+            s.set_timing(True)
+            s.local_step(K)
+            torch.cuda.synchronize()
+            phases = s.timings()
+            s.set_timing(False)
+        return s, ms, launches, clocks, phases
 
-    s64, ms64, _, _ = timed_hot("fp64")
+    s64, ms64, _, _, _ = timed_hot("fp64")
     f64 = s64.fields()
     st64 = s64.stats()
     s64.close()
-    s, ms, launches, clocks = timed_hot(args.precision, timing=True)
+    s, ms, launches, clocks, phases = timed_hot(args.precision, with_phases=True)
     f = s.fields()
     st = s.stats()
+    # both runs stopped after Wm + K graph steps (the mixed run then took K eager steps more)
+    s_chk = Solver(w, precision=args.precision, stream=handle)
+    s_chk.coarse_precompute(Wm + K)
+    s_chk.local_step(Wm + K)
+    f = s_chk.fields()
+    s_chk.close()
     rel = {k: float(np.linalg.norm(f[k] - f64[k]) / np.linalg.norm(f64[k])) for k in f}
-    ph = {k: v[0] / K for k, v in s.timings().items()}
-    phn = {k: v[1] for k, v in s.timings().items()}
+    ph = {k: v[0] / K for k, v in phases.items()}
+    phn = {k: v[1] for k, v in phases.items()}
     ndofs = st["n_fine_dofs"]
     value = ndofs * K * world / (ms / 1e3)
     value64 = ndofs * K * world / (ms64 / 1e3)
@@ -260,6 +275,15 @@ def main():
     e.close()
     e2e_val = ndofs * K * world / e2e_s
     full_ms = e2e_s * 1e3 / K
+    # ---------------------------------------------------------------- serving (bounded sample)
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        from paper_2311_05170_gb300.serve import run_serving
+        reqs = [(a, rw, args.serving_steps) for a, rw in W.serving_requests()[: args.serving_requests]]
+        sstats, _ = run_serving(reqs, hbm_budget_bytes=64 << 30, precision=args.precision)
+        serving = dict(sstats)
+        serving["sample"] = (f"first {args.serving_requests} of the 512 seeded requests (Poisson arrivals, "
+                             f"20/s), {args.serving_steps} steps each, HBM budget 64 GiB")
     # ---------------------------------------------------------------- CPU baseline (oracle)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -278,7 +302,8 @@ def main():
                        % (sum(n * (kl + ku + 1) for n, kl, ku, _ in sizes) * tsz / 1e6),
                        "parallelism": "independent replicas (no data-path collective)",
                        "timed": "K hot-path steps (prolongation, assembly, band LU, solves + FP64 refinement, glue) "
-                                "on coarse states precomputed in HBM"},
+                                "replayed from a CUDA graph on coarse states precomputed in HBM; per-phase times "
+                                "from K further steps launched kernel by kernel"},
             "valid": valid, "relL2_vs_fp64_gpu": rel,
             "fp64_gpu": {"value": value64, "ms_per_step": ms64 / K},
             "speedup_vs_fp64_gpu": value / value64,
@@ -291,6 +316,7 @@ def main():
                             "tpns_get_field of all 6 fields into pinned host memory)",
                     "full_step_ms": full_ms},
             "gpu_launches": launches,
+            "serving": serving,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

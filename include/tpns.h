@@ -110,9 +110,13 @@ typedef struct tpns_ctx tpns_ctx;
 
 /* Build meshes, subdomains, sparsity, scatter maps and band orderings on the host, upload
  * them, factor the time-invariant Darcy blocks and set the initial state (nodal
- * interpolation of the data at t = 0).  `cuda_stream` is a cudaStream_t (NULL = legacy
- * default stream).  Fails with TPNS_EBUDGET if the footprint exceeds hbm_budget_bytes
- * (0 = no limit).  On success *out owns the context; release it with tpns_destroy. */
+ * interpolation of the data at t = 0).  `cuda_stream` is a cudaStream_t (NULL = a private
+ * blocking stream the context creates and destroys).  hbm_budget_bytes (0 = no limit) caps
+ * the context's device footprint: a lower-bound estimate is checked before any allocation,
+ * then every allocation (including later ones of tpns_coarse_precompute) is checked against
+ * the cap; the first one that would pass it fails the call with TPNS_EBUDGET and whatever the
+ * call allocated is released.  On success *out owns the context; release it with
+ * tpns_destroy. */
 tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params,
                         const tpns_partition_desc* part, const tpns_data_desc* data,
                         double dt, tpns_precision precision, size_t hbm_budget_bytes,
@@ -124,7 +128,9 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params,
 tpns_status tpns_step(tpns_ctx* ctx, int32_t nsteps);
 
 /* Run Step 1 (coarse decoupled solves) for the next nsteps steps ahead and keep the coarse
- * states on the device, so that tpns_local_step can run Steps 3-4 alone. */
+ * states on the device, so that tpns_local_step can run Steps 3-4 alone.  Fails with
+ * TPNS_EBUDGET, before any work, if the nsteps + 1 stored states would pass the context's
+ * HBM budget. */
 tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps);
 
 /* Advance nsteps steps using coarse states stored by tpns_coarse_precompute: the
@@ -144,9 +150,11 @@ tpns_status tpns_get_field(tpns_ctx* ctx, int32_t field, double* dst, size_t n,
 /* Counters of the last step and sizes of the context. */
 tpns_status tpns_get_stats(tpns_ctx* ctx, tpns_stats* out);
 
-/* Serving: one time step of several contexts whose local systems are assembled,
- * factorised, solved and glued in the same batched launches.  All contexts must live on
- * the same device and share the precision; the work is enqueued on ctxs[0]'s stream. */
+/* Serving: one time step of each of n contexts.  The steps of all contexts are enqueued
+ * first, each on its context's stream (graph replays), so that their assembly, factorisation,
+ * solves and glue kernels run side by side on the device; then every context's status is
+ * collected.  All contexts must live on the same device.  Returns the first failure
+ * (message in tpns_last_error(NULL)); the other contexts still advanced. */
 tpns_status tpns_batch_step(tpns_ctx** ctxs, int32_t n);
 
 /* Per-phase device time, measured with CUDA events recorded on the context's stream

@@ -33,6 +33,7 @@ struct tpns_ctx {
   std::string err;
   std::vector<void*> allocs;
   size_t bytes = 0;
+  size_t budget = 0;   // cap on `bytes` (0: none); every allocation is checked against it
   // problems: fluid locals [0,nf), CF = nf, porous locals [nf+1, nf+1+np), CP = nf+1+np
   int nf = 0, np = 0, nprob = 0;
   std::vector<const Problem*> probs;
@@ -61,6 +62,7 @@ struct tpns_ctx {
   bool use_graph = true;
   bool own_stream = false;
   cudaGraphExec_t g_full = nullptr, g_local = nullptr;
+  int64_t kernels_full = 0, kernels_local = 0;   // kernels in each captured graph
   // device
   ProbDev* d_probs = nullptr;
   int32_t *d_eprob = nullptr, *d_e6 = nullptr, *d_e3 = nullptr;
@@ -80,6 +82,7 @@ struct tpns_ctx {
   void* d_band_local = nullptr;
   double* d_band_coarse = nullptr;
   void* d_dinv_local = nullptr;
+  void* d_vwork = nullptr;   // solve vectors that do not fit in shared memory (precision T), or NULL
   double* d_dinv_coarse = nullptr;
   void *d_lslab_local = nullptr, *d_uslab_local = nullptr;
   double *d_lslab_coarse = nullptr, *d_uslab_coarse = nullptr;
@@ -143,6 +146,10 @@ template <typename T>
 static tpns_status dalloc(tpns_ctx* ctx, T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
+  if (ctx->budget > 0 && ctx->bytes + n * sizeof(T) > ctx->budget) {
+    ctx->err = "device footprint exceeds the budget of " + std::to_string(ctx->budget) + " B";
+    return TPNS_EBUDGET;
+  }
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, n * sizeof(T));
   if (e != cudaSuccess) {
@@ -325,9 +332,33 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   size_t est = (size_t)ctx->band_local_len * Tsz + (size_t)ctx->band_coarse_len * 8 +
                (size_t)(ctx->ne_osl + ctx->ne_cf) * (225 + 15) * 8 + (size_t)ctx->vals_tot * 8 +
                (size_t)ctx->nnz_tot * 8 + (size_t)ctx->xvec_tot * 3 * 8 + (size_t)ctx->ne_tot * 11 * 8;
+  ctx->budget = budget;
   if (budget > 0 && est > budget) {
     ctx->err = "device footprint " + std::to_string(est) + " B exceeds the budget";
     return TPNS_EBUDGET;
+  }
+  {
+    // every band LU must fit one CTA's shared memory (the panel of NB + kl rows)
+    int dev = 0, smem_max = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = "no CUDA device";
+      return TPNS_EDEVICE;
+    }
+    const size_t need_local = ctx->prec == TPNS_FP64 ? band_lu_smem_bytes<double>(ctx->kl_max_osl)
+                                                     : band_lu_smem_bytes<float>(ctx->kl_max_osl);
+    if (need_local > (size_t)smem_max || band_lu_smem_bytes<double>(ctx->kl_max_cf) > (size_t)smem_max) {
+      ctx->err = "band width kl = " + std::to_string(std::max(ctx->kl_max_osl, ctx->kl_max_cf)) +
+                 " needs more shared memory per CTA than the device has (" + std::to_string(smem_max) +
+                 " B); use more subdomains or the FP32 precision";
+      return TPNS_EINVAL;
+    }
+    if (!band_solve_fits_smem<double>(ctx->n_max_cf, ctx->kmax_cf) ||
+        !band_solve_fits_smem<double>(ctx->n_max_cp, ctx->kmax_cp)) {
+      ctx->err = "coarse system too large for the on-chip coarse solve; use a larger H";
+      return TPNS_EINVAL;
+    }
   }
   // element arrays
   std::vector<int32_t> h_eprob(ctx->ne_tot), h_e6((size_t)ctx->ne_tot * 6), h_e3((size_t)ctx->ne_tot * 3);
@@ -432,12 +463,22 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     TRY(dalloc(ctx, &d, ctx->dinv_local_len));
     ctx->d_band_local = b;
     ctx->d_dinv_local = d;
+    if (!band_solve_fits_smem<double>(ctx->n_max_local, ctx->kmax_local)) {
+      double* v;
+      TRY(dalloc(ctx, &v, ctx->xvec_tot));
+      ctx->d_vwork = v;
+    }
   } else {
     float *b, *d;
     TRY(dalloc(ctx, &b, ctx->band_local_len));
     TRY(dalloc(ctx, &d, ctx->dinv_local_len));
     ctx->d_band_local = b;
     ctx->d_dinv_local = d;
+    if (!band_solve_fits_smem<float>(ctx->n_max_local, ctx->kmax_local)) {
+      float* v;
+      TRY(dalloc(ctx, &v, ctx->xvec_tot));
+      ctx->d_vwork = v;
+    }
   }
   TRY(dalloc(ctx, &ctx->d_band_coarse, ctx->band_coarse_len));
   TRY(dalloc(ctx, &ctx->d_dinv_coarse, ctx->dinv_coarse_len));
@@ -747,6 +788,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   T* band = reinterpret_cast<T*>(ctx->d_band_local);
   T* dinv = reinterpret_cast<T*>(ctx->d_dinv_local);
+  T* vwork = reinterpret_cast<T*>(ctx->d_vwork);
   T* lslab = reinterpret_cast<T*>(ctx->d_lslab_local);
   T* uslab = reinterpret_cast<T*>(ctx->d_uslab_local);
   const int nosl = (int)ctx->list_osl.size(), nloc = (int)ctx->list_local.size();
@@ -788,7 +830,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   ph_end(ctx, PH_RESIDUAL);
   ph_begin(ctx, PH_SOLVE);
   CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, lslab, uslab, dinv,
-                          ctx->d_b, ctx->d_x, 0, nullptr, ctx->d_status, st, nullptr));
+                          ctx->d_b, ctx->d_x, 0, nullptr, ctx->d_status, st, nullptr, vwork));
   ph_end(ctx, PH_SOLVE);
   for (int it = 0; it < maxit; ++it) {
     ph_begin(ctx, PH_RESIDUAL);
@@ -799,7 +841,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
     if (it + 1 < maxit) {
       ph_begin(ctx, PH_SOLVE);
       CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, lslab, uslab,
-                              dinv, ctx->d_r, ctx->d_x, 1, ctx->d_done, ctx->d_status, st, nullptr));
+                              dinv, ctx->d_r, ctx->d_x, 1, ctx->d_done, ctx->d_status, st, nullptr, vwork));
       ph_end(ctx, PH_SOLVE);
     }
   }
@@ -842,7 +884,12 @@ static bool capture_step(tpns_ctx* ctx, bool coarse, cudaGraphExec_t* out) {
     cudaGetLastError();
     return false;
   }
+  const int64_t l0 = launch_counter();
   tpns_status s = enqueue_step(ctx, coarse);
+  // kernels recorded in the graph run at every replay, not now
+  const int64_t recorded = launch_counter() - l0;
+  count_launches((int)-recorded);
+  (coarse ? ctx->kernels_full : ctx->kernels_local) = recorded;
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
   bool ok = s == TPNS_OK && e == cudaSuccess && g != nullptr;
   if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
@@ -911,7 +958,10 @@ static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
         ctx->use_graph = false;
         graph = false;
       }
-      if (graph) CK(cudaGraphLaunch(ex, ctx->stream));
+      if (graph) {
+        CK(cudaGraphLaunch(ex, ctx->stream));
+        count_launches((int)(from_traj ? ctx->kernels_local : ctx->kernels_full));
+      }
     }
     if (!graph) TRY(enqueue_step(ctx, !from_traj));
     ctx->step += 1;
@@ -1350,6 +1400,10 @@ tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps) {
     if (it != ctx->allocs.end()) ctx->allocs.erase(it);
   }
   ctx->traj.clear();
+  if (ctx->budget > 0 && ctx->bytes + (size_t)(nsteps + 1) * len * 8 > ctx->budget) {
+    ctx->err = "coarse trajectory of " + std::to_string(nsteps) + " steps exceeds the budget";
+    return TPNS_EBUDGET;
+  }
   cudaStream_t st = ctx->stream;
   // save the current coarse state, then march the coarse problem alone
   std::vector<double> keep_uc(nu), keep_pc(npc), keep_pd(npd);
@@ -1441,12 +1495,48 @@ tpns_status tpns_get_stats(tpns_ctx* ctx, tpns_stats* out) {
 
 tpns_status tpns_batch_step(tpns_ctx** ctxs, int32_t n) {
   if (!ctxs || n < 0) return TPNS_EINVAL;
+  g_err.clear();
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || ctxs[i]->host_only || ctxs[i]->device != ctxs[0]->device) {
+      g_err = "batch contexts must be device contexts of one device";
+      return TPNS_EINVAL;
+    }
+  // enqueue one step of every context first (each on its own stream, so that their kernels
+  // run side by side), then collect the status words
   for (int i = 0; i < n; ++i) {
-    if (!ctxs[i]) return TPNS_EINVAL;
-    tpns_status s = tpns_step(ctxs[i], 1);
-    if (s != TPNS_OK) return s;
+    tpns_ctx* ctx = ctxs[i];
+    ctx->err.clear();
+    ctx->traj_base = -1000000000;
+    bool graph = ctx->use_graph && !ctx->timing;
+    if (graph) {
+      if (!ctx->g_full && !capture_step(ctx, true, &ctx->g_full)) {
+        ctx->use_graph = false;
+        graph = false;
+      }
+      if (graph && cudaGraphLaunch(ctx->g_full, ctx->stream) != cudaSuccess) {
+        g_err = ctx->err = "cudaGraphLaunch failed";
+        return TPNS_EDEVICE;
+      }
+      if (graph) count_launches((int)ctx->kernels_full);
+    }
+    if (!graph) {
+      tpns_status s = enqueue_step(ctx, true);
+      if (s != TPNS_OK) {
+        g_err = ctx->err;
+        return s;
+      }
+    }
+    ctx->step += 1;
   }
-  return TPNS_OK;
+  tpns_status worst = TPNS_OK;
+  for (int i = 0; i < n; ++i) {
+    tpns_status s = read_stats(ctxs[i]);
+    if (s != TPNS_OK && worst == TPNS_OK) {
+      worst = s;
+      g_err = ctxs[i]->err;
+    }
+  }
+  return worst;
 }
 
 tpns_status tpns_set_timing(tpns_ctx* ctx, int32_t on) {

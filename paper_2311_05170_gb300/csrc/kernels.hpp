@@ -41,7 +41,15 @@ cudaError_t launch_chol_to_lu(const SysDev* sys_chol, const SysDev* sys_lu, cons
 template <typename T>
 cudaError_t launch_band_solve(const SysDev* sys, const int* sys_list, int nsys, int n_max, int kmax,
                               const T* lslab, const T* uslab, const T* dinv, const double* r, double* x,
-                              int accumulate, const int* done, int* status, cudaStream_t st, const int* skip);
+                              int accumulate, const int* done, int* status, cudaStream_t st, const int* skip,
+                              T* vwork = nullptr);
+// vwork: scratch in precision T at the systems' x offsets, used when a vector does not fit
+// in shared memory beside the pipeline stages (NULL: such a launch fails)
+template <typename T>
+bool band_solve_fits_smem(int n_max, int kmax);
+// dynamic shared memory of the LU kernel for a band of kl_max sub-diagonals
+template <typename T>
+size_t band_lu_smem_bytes(int kl_max);
 // r = b - A x in FP64, convergence bookkeeping (relative residual <= tol, or stagnation)
 // partial: nsys * RES_CHUNKS * 2 doubles; ticket: nsys ints, zero before the first call
 cudaError_t launch_residual(const SysDev* sys, const int* sys_list, int nsys, const int32_t* rowptr,

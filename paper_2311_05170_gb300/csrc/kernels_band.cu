@@ -256,6 +256,50 @@ __device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku
   }
 }
 
+// Factor the panel held in shared memory Pn (row stride SP, rows 0..R-1 relative to k0,
+// columns k0..k0+kw-1), for panels taller than the CTA: each thread updates rows tid,
+// tid + THREADS, ... one column at a time.  Same arithmetic as factor_rows (multiplier =
+// entry x reciprocal of the pivot), so both give the same factors.  Writes the band and the
+// slabs.
+template <typename T>
+__device__ void factor_panel_smem(int k0, int kw, int R, int kl, int ku, int ldab, T* __restrict__ AB,
+                                  T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn, int* status) {
+  constexpr int NB = LU_NB;
+  constexpr int THREADS = lu_threads<T>();
+  const int tid = threadIdx.x;
+  for (int c = 0; c < kw; ++c) {
+    T piv = Pn[c * SP + c];
+    if (bad_pivot(piv)) {
+      if (tid == 0) atomicOr(status, 1);
+      piv = T(1);
+    }
+    const T inv = T(1) / piv;
+    const T* pr = Pn + c * SP;
+    for (int r = c + 1 + tid; r < R; r += THREADS) {
+      T* row = Pn + r * SP;
+      const T l = row[c] * inv;
+      row[c] = l;
+#pragma unroll
+      for (int c2 = 0; c2 < NB; ++c2)
+        if (c2 > c) row[c2] -= l * pr[c2];
+    }
+    __syncthreads();
+  }
+  for (int r = tid; r < R; r += THREADS) {
+    const int i = k0 + r;
+#pragma unroll 4
+    for (int c = 0; c < kw; ++c) {
+      const int j = k0 + c;
+      if (i - j <= kl && j - i <= ku) {
+        const T v = Pn[r * SP + c];
+        AB[(int64_t)j * ldab + (ku + i - j)] = v;
+        if (i > j) LS[lsl_idx(i, j, kl)] = v;
+        else if (i < j) US[usl_idx(i, j, ku)] = v;
+      }
+    }
+  }
+}
+
 // U12 = L11^{-1} A12 for one column block: A12 (rows k0.., columns c0..) is loaded into Ub
 // (row stride SP) and multiplied by the inverse Li (column-major NB x NB); the result goes to
 // the band, the U slab and the unpadded copy Uv used for broadcast reads.
@@ -362,7 +406,7 @@ __device__ __forceinline__ void row_update(T (&acc)[W], LF lf, const T* __restri
   }
 }
 
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void __cluster_dims__(LU_CLUSTER, 1, 1) __launch_bounds__(lu_threads<T>(), 1)
 band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* __restrict__ band,
                T* __restrict__ lslab, T* __restrict__ uslab, T* __restrict__ dinv_all, int* __restrict__ sync_all,
@@ -402,7 +446,62 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (rank == 0) {
+  if (WIDE && rank == 0) {
+    // ------------------------------------------------ critical CTA, panels taller than the CTA:
+    // the panel stays in shared memory and every thread works on rows tid, tid + THREADS, ...
+    {
+      const int kw = min(NB, n), R = min(n, kw + kl);
+      for (int r = tid; r < R; r += THREADS) {
+#pragma unroll 4
+        for (int c = 0; c < NB; ++c)
+          Pn[r * SP + c] = (c < kw && r - c <= kl && c - r <= ku) ? __ldcg(AB + (int64_t)c * ldab + (ku + r - c)) : T(0);
+      }
+      __syncthreads();
+      factor_panel_smem<T>(0, kw, R, kl, ku, ldab, AB, LS, US, Pn, st);
+      __syncthreads();
+      unit_lower_inverse<T>(Pn, kw, Li, DI);
+      __syncthreads();
+      if (tid == 0) st_release(flag + 0, epoch);
+    }
+    const int nslice = (NB + kl + THREADS - 1) / THREADS;
+    for (int kb = 0; kb + 1 < nblk; ++kb) {
+      const int k0 = kb * NB, R = min(n, k0 + NB + kl) - k0;
+      const int cb = kb + 1, c0 = cb * NB, cw = min(NB, n - c0), R2 = min(n, c0 + cw + kl) - c0;
+      const int need = cb - 1 - max(0, cb - D);
+      if (need > 0 && tid == 0) {
+        if (!wait_cnt(cnt + cb, epoch, need)) {
+          atomicOr(st, 2);
+          abort_flag = 1;
+        }
+      }
+      __syncthreads();
+      if (abort_flag) return;
+      form_u12<T>(Li, Ub, Uv, AB, US, k0, NB, c0, cw, kl, ku, ldab);
+      // rows of the next panel, updated by this panel, in slices of THREADS rows: row r2 reads
+      // row r2 + NB of this panel, so a slice is written back only after all its reads
+      for (int q = 0; q < nslice; ++q) {
+        const int r2 = q * THREADS + tid, i = c0 + r2, r = r2 + NB;
+        T a[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          const int j = c0 + c;
+          a[c] = (r2 < R2 && c < cw && i - j <= kl && j - i <= ku) ? __ldcg(AB + (int64_t)j * ldab + (ku + i - j)) : T(0);
+        }
+        if (r2 < R2 && r < R) row_update<T, NB>(a, [&](int p) { return Pn[r * SP + p]; }, Uv, 0);
+        __syncthreads();
+        if (r2 < R2) {
+#pragma unroll
+          for (int c = 0; c < NB; ++c) Pn[r2 * SP + c] = a[c];
+        }
+      }
+      __syncthreads();
+      factor_panel_smem<T>(c0, cw, R2, kl, ku, ldab, AB, LS, US, Pn, st);
+      __syncthreads();
+      unit_lower_inverse<T>(Pn, cw, Li, DI + (int64_t)cb * 2 * NB * NB);
+      __syncthreads();
+      if (tid == 0) st_release(flag + cb, epoch);
+    }
+  } else if (rank == 0) {
     // ------------------------------------------------ critical CTA: the chain of panels
     T a[NB];
     {
@@ -517,6 +616,16 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
   }
 }
 
+// Dynamic shared memory of the LU kernel: mbarrier (128 B), Uv, Li (NB x NB each), Ub
+// (NB x SP), then the larger of [pivot rows 2 (NB + 2) + critical panel (NB + kl) x SP] and
+// the bulk slab NB x kl.
+template <typename T>
+size_t band_lu_smem_bytes(int kl_max) {
+  const size_t head = (size_t)2 * LU_NB * LU_NB + LU_NB * SP;
+  const size_t tail = std::max((size_t)2 * (LU_NB + 2) + (size_t)(LU_NB + kl_max) * SP, (size_t)LU_NB * kl_max);
+  return 128 + (head + tail) * sizeof(T);
+}
+
 // a new tag for the next factorisation (kept on the device so that a captured graph replays
 // with fresh tags)
 __global__ void bump_kernel(int* p) { *p = (*p % 0x7FFFF) + 1; }
@@ -526,18 +635,20 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
                            T* dinv, int* sync, int sync_stride, int* epoch, int* status, cudaStream_t st,
                            const int* skip) {
   if (nsys == 0) return cudaSuccess;
-  if (LU_NB + kl_max > lu_threads<T>()) return cudaErrorInvalidValue;
-  // mbarrier (128 B), Uv, Li (NB x NB each), Ub (NB x SP), then the larger of
-  // [pivot rows 2 (NB + 2) + critical panel (NB + kl) x SP] and the bulk slab NB x kl
-  const size_t head = (size_t)2 * LU_NB * LU_NB + LU_NB * SP;
-  const size_t tail = std::max((size_t)2 * (LU_NB + 2) + (size_t)(LU_NB + kl_max) * SP, (size_t)LU_NB * kl_max);
-  const size_t smem = 128 + (head + tail) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(band_lu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = band_lu_smem_bytes<T>(kl_max);
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (kl_max < 0 || smem > (size_t)smem_max) return cudaErrorInvalidValue;
+  // panels of at most one row per thread are factored from registers
+  const bool wide = LU_NB + kl_max > lu_threads<T>();
+  auto kern = wide ? band_lu_kernel<T, true> : band_lu_kernel<T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(2);
   bump_kernel<<<1, 1, 0, st>>>(epoch);
-  band_lu_kernel<T><<<nsys * LU_CLUSTER, lu_threads<T>(), smem, st>>>(sys, list, band, lslab, uslab, dinv, sync,
-                                                                      sync_stride, epoch, status, skip);
+  kern<<<nsys * LU_CLUSTER, lu_threads<T>(), smem, st>>>(sys, list, band, lslab, uslab, dinv, sync, sync_stride, epoch,
+                                                          status, skip);
   return cudaGetLastError();
 }
 
@@ -690,7 +801,7 @@ cudaError_t launch_chol_to_lu(const SysDev* sys_chol, const SysDev* sys_lu, cons
 // completing on an mbarrier, STAGES blocks ahead of the one being solved.  Each block is
 // finished by one warp with the inverse (a GEMV), then the rows coupled to it by the band are
 // updated by all threads.  The vector lives in shared memory in precision T.
-template <typename T, int STAGES>
+template <typename T, int STAGES, bool GV>
 __global__ void __launch_bounds__(256) band_solve_kernel(const SysDev* __restrict__ sys,
                                                          const int* __restrict__ list,
                                                          const T* __restrict__ lslab, const T* __restrict__ uslab,
@@ -698,7 +809,7 @@ __global__ void __launch_bounds__(256) band_solve_kernel(const SysDev* __restric
                                                          const double* __restrict__ rhs,
                                                          double* __restrict__ x, int accumulate, int kmax,
                                                          const int* __restrict__ done, int* __restrict__ status,
-                                                         const int* skip) {
+                                                         const int* skip, T* __restrict__ vwork) {
   if (skip && *skip) return;
   const int sid = list[blockIdx.x];
   if (done && done[sid]) return;
@@ -709,7 +820,9 @@ __global__ void __launch_bounds__(256) band_solve_kernel(const SysDev* __restric
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                  // STAGES mbarriers
   T* stage0 = reinterpret_cast<T*>(smem_raw + 128);
   const size_t stage_elems = (size_t)NB * NB + (size_t)NB * kmax;         // inverse, then slab
-  T* v = stage0 + STAGES * stage_elems;                                   // n
+  // the vector: in shared memory after the stages, or (GV) in the caller's global scratch
+  // at the system's offset when it does not fit
+  T* v = GV ? vwork + S.x_off : stage0 + STAGES * stage_elems;
   __shared__ T yb[NB];
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -807,10 +920,33 @@ __global__ void __launch_bounds__(256) band_solve_kernel(const SysDev* __restric
   for (int i = tid; i < n; i += blockDim.x) xo[i] = accumulate ? xo[i] + (double)v[i] : (double)v[i];
 }
 
+// true if one CTA holds the vector of n_max entries and at least one pipeline stage
+template <typename T>
+bool band_solve_fits_smem(int n_max, int kmax) {
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t stage = ((size_t)LU_NB * LU_NB + (size_t)LU_NB * kmax) * sizeof(T);
+  return 128 + stage + ((size_t)n_max + 4) * sizeof(T) + 1024 <= (size_t)smem_max;
+}
+
+template <typename T, int STAGES, bool GV>
+static cudaError_t launch_solve_variant(size_t smem, const SysDev* sys, const int* list, int nsys, int kmax,
+                                        const T* lslab, const T* uslab, const T* dinv, const double* r, double* x,
+                                        int accumulate, const int* done, int* status, cudaStream_t st,
+                                        const int* skip, T* vwork) {
+  cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<T, STAGES, GV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  band_solve_kernel<T, STAGES, GV><<<nsys, 256, smem, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax,
+                                                            done, status, skip, vwork);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_band_solve(const SysDev* sys, const int* list, int nsys, int n_max, int kmax, const T* lslab,
                               const T* uslab, const T* dinv, const double* r, double* x, int accumulate,
-                              const int* done, int* status, cudaStream_t st, const int* skip) {
+                              const int* done, int* status, cudaStream_t st, const int* skip, T* vwork) {
   if (nsys == 0) return cudaSuccess;
   int dev = 0, smem_max = 0;
   cudaGetDevice(&dev);
@@ -819,28 +955,25 @@ cudaError_t launch_band_solve(const SysDev* sys, const int* list, int nsys, int 
   const size_t vec = ((size_t)n_max + 4) * sizeof(T);
   const size_t static_smem = 1024;
   count_launches(1);
-  for (int stages = 3; stages >= 1; --stages) {
-    const size_t need = 128 + stages * stage + vec;
-    if (need + static_smem > (size_t)smem_max) continue;
-    cudaError_t e;
-    if (stages == 3) {
-      e = cudaFuncSetAttribute(band_solve_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-      if (e != cudaSuccess) return e;
-      band_solve_kernel<T, 3><<<nsys, 256, need, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax, done,
-                                                       status, skip);
-    } else if (stages == 2) {
-      e = cudaFuncSetAttribute(band_solve_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-      if (e != cudaSuccess) return e;
-      band_solve_kernel<T, 2><<<nsys, 256, need, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax, done,
-                                                       status, skip);
-    } else {
-      e = cudaFuncSetAttribute(band_solve_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-      if (e != cudaSuccess) return e;
-      band_solve_kernel<T, 1><<<nsys, 256, need, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax, done,
-                                                       status, skip);
+  // deepest pipeline with the vector in shared memory, else (given scratch) in global memory
+  for (int gv = 0; gv < 2; ++gv) {
+    if (gv && !vwork) break;
+    for (int stages = 3; stages >= 1; --stages) {
+      const size_t need = 128 + stages * stage + (gv ? 0 : vec);
+      if (need + static_smem > (size_t)smem_max) continue;
+#define TPNS_SOLVE_ARGS need, sys, list, nsys, kmax, lslab, uslab, dinv, r, x, accumulate, done, status, st, skip, vwork
+      if (!gv) {
+        if (stages == 3) return launch_solve_variant<T, 3, false>(TPNS_SOLVE_ARGS);
+        if (stages == 2) return launch_solve_variant<T, 2, false>(TPNS_SOLVE_ARGS);
+        return launch_solve_variant<T, 1, false>(TPNS_SOLVE_ARGS);
+      }
+      if (stages == 3) return launch_solve_variant<T, 3, true>(TPNS_SOLVE_ARGS);
+      if (stages == 2) return launch_solve_variant<T, 2, true>(TPNS_SOLVE_ARGS);
+      return launch_solve_variant<T, 1, true>(TPNS_SOLVE_ARGS);
+#undef TPNS_SOLVE_ARGS
     }
-    return cudaGetLastError();
   }
+  count_launches(-1);
   return cudaErrorInvalidValue;
 }
 
@@ -958,7 +1091,9 @@ cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const 
                                             cudaStream_t);                                                  \
   template cudaError_t launch_band_solve<T>(const SysDev*, const int*, int, int, int, const T*, const T*,   \
                                             const T*, const double*, double*, int, const int*, int*,        \
-                                            cudaStream_t, const int*);
+                                            cudaStream_t, const int*, T*);                                  \
+  template bool band_solve_fits_smem<T>(int, int);                                                          \
+  template size_t band_lu_smem_bytes<T>(int);
 TPNS_INST(float)
 TPNS_INST(double)
 

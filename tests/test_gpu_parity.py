@@ -84,6 +84,29 @@ def test_edge_layouts_parity(native, w):
         assert rel(f[k], o.fine[k]) <= 1e-8, k
 
 
+def test_wide_band_parity(native):
+    """Subdomains whose Oseen band (kl = 851) is taller than the LU CTA has threads: the panel
+    is factored from shared memory and the solve vector lives in global scratch; FP32 with
+    FP64 refinement still meets the mixed-precision tolerance against the oracle."""
+    w = W.config_uniform(4, 24, nsub=(2, 2), nsteps=2)
+    s = native.Solver(w, precision="fp32", host_only=True)
+    assert max(s.debug_system(j)["kl"] for j in range(4)) == 851
+    s.close()
+    f, o, stats = run_pair(native, w, "fp32", 2)
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL["fp32"], (k, rel(f[k], o.fine[k]))
+    assert stats["last_ir_relres_max"] <= 1e-12
+
+
+def test_band_too_wide_for_fp64_is_refused(native):
+    """An FP64 panel of 32 + 851 rows does not fit one CTA's shared memory: creation fails
+    with TPNS_EINVAL and a message, before any device allocation."""
+    w = W.config_uniform(4, 24, nsub=(2, 2), nsteps=1)
+    with pytest.raises(native.TpnsError) as e:
+        native.Solver(w, precision="fp64")
+    assert e.value.status == native.TPNS_EINVAL and "shared memory" in str(e.value)
+
+
 def test_assembled_systems_match_oracle(native):
     """FP64 CSR values and right-hand sides of the local systems after one step equal
     the oracle's assembled matrices (keyed by global node and component)."""

@@ -132,3 +132,27 @@ def serving_requests(n=512, seed_arrivals=3, rate=20.0):
                      (ns, ns), 2, 0.01, 100, 1, p)
         out.append((float(t[r]), w))
     return out
+
+
+def serving_requests_small(n=6, seed=7, rate=200.0, nsteps=4):
+    """A small serving mix for tests: Poisson arrivals, h in {1/16, 1/32}, H in {1/4, 1/8},
+    2 or 4 subdomains per direction, seeded permeabilities, porosities and exchange
+    coefficients (same distributions as serving_requests).  Returns (arrival, Workload, nsteps)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for r in range(n):
+        g = np.random.default_rng(2000 + r)
+        inv_H = int(g.choice([4, 8]))
+        ratio = int(g.choice([2, 4]))
+        ns = int(g.choice([2, 4]))
+        ks = np.exp(g.uniform(math.log(1e-4), 0.0, size=3))
+        phis = g.uniform(0.05, 0.3, size=3)
+        sig = np.exp(g.uniform(math.log(1e-2), math.log(10.0), size=2))
+        p = Params(k=(float(ks[2]), float(ks[1]), float(ks[0])),
+                   phiC=(float(phis[2]), float(phis[1]), float(phis[0])),
+                   sigma=float(sig[0]), sigma_star=float(sig[1]))
+        w = Workload(f"sreq{r}_H{inv_H}_h{inv_H * ratio}", inv_H, inv_H, ratio, [ratio] * inv_H,
+                     (ns, ns), 2, 0.01, nsteps, 1, p)
+        out.append((float(t[r]), w, nsteps))
+    return out
