@@ -162,6 +162,7 @@ def main():
         dist.barrier()
     import workloads as W
     from paper_2311_05170_gb300.native import Solver, launch_count
+    from paper_2311_05170_gb300.shard import gather_lists, max_over_ranks, shard_requests, sum_over_ranks
     K, Wm = args.steps, args.warmup
     w = W.config_graded(nsteps=Wm + K)
     stream = torch.cuda.Stream()
@@ -190,16 +191,19 @@ def main():
         clocks = clk.stop()
         ms = e0.elapsed_time(e1)
         launches = launch_count() - l0
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist is not None, device="cuda")
         phases = None
         if with_phases:
+            # one step per call so that each step's solve passes (systems converge after
+            # different numbers of refinement passes) are counted into the solve bytes
             s.set_timing(True)
-            s.local_step(K)
+            solve_bytes = 0.0
+            for _ in range(K):
+                s.local_step(1)
+                solve_bytes += s.stats()["last_solve_bytes"]
             torch.cuda.synchronize()
             phases = s.timings()
+            phases["_solve_bytes"] = solve_bytes
             s.set_timing(False)
         return s, ms, launches, clocks, phases
 
@@ -208,6 +212,7 @@ def main():
     st64 = s64.stats()
     s64.close()
     s, ms, launches, clocks, phases = timed_hot(args.precision, with_phases=True)
+    launches = int(sum_over_ranks(launches, dist is not None, device="cuda"))   # the whole job's
     f = s.fields()
     st = s.stats()
     # both runs stopped after Wm + K graph steps (the mixed run then took K eager steps more)
@@ -217,6 +222,7 @@ def main():
     f = s_chk.fields()
     s_chk.close()
     rel = {k: float(np.linalg.norm(f[k] - f64[k]) / np.linalg.norm(f64[k])) for k in f}
+    solve_bytes_step = phases.pop("_solve_bytes") / K
     ph = {k: v[0] / K for k, v in phases.items()}
     phn = {k: v[1] for k, v in phases.items()}
     ndofs = st["n_fine_dofs"]
@@ -229,16 +235,17 @@ def main():
     n_fluid = 16                      # 4 x 4 conduit subdomains
     sizes = band_sizes(s, n_fluid, 16)
     tsz = 4 if args.precision == "fp32" else 8
-    solve_bytes = sum(n * (kl + ku) * tsz + ((n + 31) // 32) * 2 * 1024 * tsz + n * 8 * 2 for n, kl, ku, _ in sizes)
     lu_ms = ph["band_lu"]
     lu_tflops = st["band_lu_flops"] / (lu_ms / 1e3) / 1e12
-    solve_launch_ms = ph["solve"] * K / max(phn["solve"], 1)
+    # all solve launches of a step (the active passes and the ones that find every system
+    # converged) against the bytes of the active passes
+    solve_gbs = solve_bytes_step / (ph["solve"] / 1e3) / 1e9
     kernels = {
         "band_lu": {"bound": "alu", "achieved": lu_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": lu_tflops / FP32_PEAK_TFLOPS, "ms_per_step": lu_ms},
-        "band_solve": {"bound": "hbm", "achieved": solve_bytes / (solve_launch_ms / 1e3) / 1e9, "peak": hbm_peak,
-                       "unit": "GB/s", "frac": solve_bytes / (solve_launch_ms / 1e3) / 1e9 / hbm_peak,
-                       "ms_per_step": ph["solve"]},
+        "band_solve": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": solve_gbs / hbm_peak, "ms_per_step": ph["solve"],
+                       "bytes_per_step": solve_bytes_step, "launches_per_step": phn["solve"] / K},
     }
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     traffic = None
@@ -270,20 +277,36 @@ def main():
             e.field(k, out=buf)
             d2h += buf.nbytes
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist is not None, device="cuda")
     st_e = e.stats()
     e.close()
     e2e_val = ndofs * K * world / e2e_s
     full_ms = e2e_s * 1e3 / K
     # ---------------------------------------------------------------- serving (bounded sample)
     serving = None
-    if rank == 0 and args.serving_requests > 0:
+    if args.serving_requests > 0:
+        # each rank serves its own share of the requests (no collective while serving)
         from paper_2311_05170_gb300.serve import run_serving
         reqs = [(a, rw, args.serving_steps) for a, rw in W.serving_requests()[: args.serving_requests]]
-        sstats, _ = run_serving(reqs, hbm_budget_bytes=64 << 30, precision=args.precision)
-        serving = dict(sstats)
-        serving["sample"] = (f"first {args.serving_requests} of the 512 seeded requests (Poisson arrivals, "
-                             f"20/s), {args.serving_steps} steps each, HBM budget 64 GiB")
+        mine = shard_requests(reqs, rank, world)
+        sstats, done = run_serving(mine, hbm_budget_bytes=64 << 30, precision=args.precision)
+        on = dist is not None
+        lat = np.array(gather_lists([x for r in done for x in r.latencies_ms], on))
+        wall = max_over_ranks(sstats["wall_s"], on, device="cuda")
+        serving = {
+            "requests": int(sum_over_ranks(sstats["requests"], on, device="cuda")),
+            "ticks_max": int(max_over_ranks(sstats["ticks"], on, device="cuda")),
+            "wall_s": wall,
+            "max_concurrency_per_gpu": int(max_over_ranks(sstats["max_concurrency"], on, device="cuda")),
+            "refused_for_budget": int(sum_over_ranks(sstats["refused_for_budget"], on, device="cuda")),
+            "step_latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,
+            "step_latency_ms_p99": float(np.percentile(lat, 99)) if lat.size else None,
+            "dof_steps_per_s": sum_over_ranks(sum(r.dofs * r.done_steps for r in done), on, device="cuda") / wall,
+            "sample": (f"first {args.serving_requests} of the 512 seeded requests (Poisson arrivals, 20/s), "
+                       f"{args.serving_steps} steps each, sharded over {world} GPU(s) by estimated work, "
+                       f"HBM budget 64 GiB per GPU; latency = duration of the batched tick that advanced "
+                       f"the request; wall includes context creation"),
+        }
     # ---------------------------------------------------------------- CPU baseline (oracle)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

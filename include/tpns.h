@@ -104,6 +104,11 @@ typedef struct {
   int64_t device_bytes;           /* device footprint of the context */
   double band_lu_flops;           /* algorithmic flops of one step's Oseen band LUs */
   int64_t h2d_bytes;              /* bytes copied host -> device by tpns_create */
+  int64_t last_ir_solves;         /* band solve passes over all local systems, last step */
+  double last_solve_bytes;        /* algorithmic bytes of those passes: per pass and system
+                                     n (kl + ku) s + ceil(n / 32) 2048 s + 24 n, s = factor
+                                     element size (factor slabs, diagonal-block inverses, FP64
+                                     right-hand side read and solution read + write) */
 } tpns_stats;
 
 typedef struct tpns_ctx tpns_ctx;

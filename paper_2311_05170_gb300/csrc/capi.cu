@@ -914,10 +914,20 @@ static tpns_status read_stats(tpns_ctx* ctx) {
   CK(cudaMemcpy(&nit, ctx->d_newton_iters, sizeof(int), cudaMemcpyDeviceToHost));
   int mx = 0;
   double mr = 0;
+  int64_t passes = 0;
+  double bytes = 0;
+  const double tsz = ctx->prec == TPNS_FP64 ? 8.0 : 4.0;
   for (int s : ctx->list_local) {
     mx = std::max(mx, it[s]);
     mr = std::max(mr, rel[s]);
+    // each residual after a solve counts one iteration, so iters = solve passes this step
+    const SysDev& S = ctx->hsys[s];
+    passes += it[s];
+    bytes += (double)it[s] * ((double)S.n * (S.kl + S.ku) * tsz + (double)((S.n + 31) / 32) * 2048.0 * tsz +
+                              24.0 * S.n);
   }
+  ctx->stats.last_ir_solves = passes;
+  ctx->stats.last_solve_bytes = bytes;
   ctx->stats.step = ctx->step;
   ctx->stats.last_ir_iters_max = mx;
   ctx->stats.last_ir_relres_max = mr;

@@ -21,6 +21,9 @@ cudaError_t launch_band_fill(const SysDev* sys, const int* sys_list, int nsys, c
                              const int32_t* colidx, const double* vals, T* band, int chol,
                              int64_t total_nnz_hint, cudaStream_t st, const int* skip);
 template <typename T>
+// Unpivoted band LU A = L U into the factor slabs (lslab, uslab), the inverses of the
+// diagonal blocks' unit-lower triangles (first half of each block's dinv) and the factored
+// diagonal blocks (in the band; launch_band_dinv then forms both inverses from them).
 // epoch: device counter, bumped before the factorisation starts
 cudaError_t launch_band_lu(const SysDev* sys, const int* sys_list, int nsys, int kl_max, T* band, T* lslab,
                            T* uslab, T* dinv, int* sync, int sync_stride, int* epoch, int* status, cudaStream_t st,

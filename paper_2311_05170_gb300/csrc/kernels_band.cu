@@ -159,6 +159,23 @@ __device__ __forceinline__ int64_t usl_idx(int i, int j, int ku) {
   return (int64_t)(j >> 5) * 32 * ku + (int64_t)(j & 31) * ku + (i - j + ku);
 }
 
+// Column j of the inverse of the upper triangle of a factored NB x NB diagonal block D (row
+// stride SP), written to dinvU[j * NB + i].
+template <typename T>
+__device__ __forceinline__ void diag_upper_column(const T* __restrict__ D, int kw, int j, T* __restrict__ dinvU) {
+  constexpr int NB = LU_NB;
+  T x[NB];
+#pragma unroll
+  for (int ii = NB - 1; ii >= 0; --ii) {
+    T v = (ii == j) ? T(1) : T(0);
+#pragma unroll
+    for (int p = ii + 1; p < NB; ++p) v -= D[ii * SP + p] * x[p];
+    x[ii] = (ii < kw && j < kw) ? v / D[ii * SP + ii] : T(0);
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) dinvU[j * NB + i] = x[i];
+}
+
 // Inverses of the unit lower and upper triangles of a factored NB x NB diagonal block held
 // in shared memory (row stride SP); written transposed (column-major) to dinv so that a
 // warp reads one column per step with consecutive lanes.  Threads 0..63.
@@ -179,32 +196,99 @@ __device__ void diag_inverses(const T* __restrict__ D, int kw, T* __restrict__ d
 #pragma unroll
     for (int i = 0; i < NB; ++i) dinv[j * NB + i] = x[i];   // dinv[p * NB + i] = Linv[i][p]
   } else if (tid < 2 * NB) {
-    const int j = tid - NB;          // column j of U11^{-1}
-    T x[NB];
+    diag_upper_column<T>(D, kw, tid - NB, dinv + NB * NB);   // column j of U11^{-1}
+  }
+}
+
+// Pivot rows are broadcast through shared memory in rows of PR elements (16-byte aligned);
+// element NB holds the reciprocal of the pivot.
+constexpr int PR = LU_NB + 4;
+
+// a[c2] -= l * pr[c2] for C < c2 < NB, reading pr with 16-byte vector loads
+template <int C, typename T>
+__device__ __forceinline__ void axpy_tail(T (&a)[LU_NB], T l, const T* __restrict__ pr) {
+  constexpr int NB = LU_NB;
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int ii = NB - 1; ii >= 0; --ii) {
-      T v = (ii == j) ? T(1) : T(0);
-#pragma unroll
-      for (int p = ii + 1; p < NB; ++p) v -= D[ii * SP + p] * x[p];
-      x[ii] = (ii < kw && j < kw) ? v / D[ii * SP + ii] : T(0);
+    for (int g = (C + 1) / 4; g < NB / 4; ++g) {
+      const float4 v = reinterpret_cast<const float4*>(pr)[g];
+      if (4 * g + 0 > C) a[4 * g + 0] -= l * v.x;
+      if (4 * g + 1 > C) a[4 * g + 1] -= l * v.y;
+      if (4 * g + 2 > C) a[4 * g + 2] -= l * v.z;
+      if (4 * g + 3 > C) a[4 * g + 3] -= l * v.w;
     }
+  } else {
 #pragma unroll
-    for (int i = 0; i < NB; ++i) dinv[NB * NB + j * NB + i] = x[i];
+    for (int g = (C + 1) / 2; g < NB / 2; ++g) {
+      const double2 v = reinterpret_cast<const double2*>(pr)[g];
+      if (2 * g + 0 > C) a[2 * g + 0] -= l * v.x;
+      if (2 * g + 1 > C) a[2 * g + 1] -= l * v.y;
+    }
+  }
+}
+
+// store a row of NB values and the reciprocal of its pivot as a broadcast pivot row
+template <typename T>
+__device__ __forceinline__ void put_pivot_row(T* __restrict__ pn, const T (&a)[LU_NB], T rcp) {
+  constexpr int NB = LU_NB;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int g = 0; g < NB / 4; ++g)
+      reinterpret_cast<float4*>(pn)[g] = make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
+  } else {
+#pragma unroll
+    for (int g = 0; g < NB / 2; ++g) reinterpret_cast<double2*>(pn)[g] = make_double2(a[2 * g], a[2 * g + 1]);
+  }
+  pn[NB] = rcp;
+}
+
+// Column C of the panel factorisation: rows below the pivot take their multiplier and update
+// their tails; the owner of row C + 1 then publishes it as the next pivot row.
+template <int C, typename T>
+__device__ __forceinline__ void factor_column(T (&a)[LU_NB], int r, int kw, int R, int tid, T* __restrict__ prow,
+                                              bool& bad) {
+  constexpr int NB = LU_NB;
+  if (C < kw) {
+    const T* pr = prow + (C & 1) * PR;
+    T* pn = prow + ((C + 1) & 1) * PR;
+    if (r > C && r < R) {
+      const T l = a[C] * pr[NB];
+      a[C] = l;
+      axpy_tail<C>(a, l, pr);
+    }
+    if (C + 1 < kw && tid == C + 1) {
+      T piv = a[C + 1];
+      if (bad_pivot(piv)) {
+        bad = true;
+        piv = T(1);
+      }
+      put_pivot_row(pn, a, T(1) / piv);
+    }
+    __syncthreads();
+  }
+}
+
+template <int C, typename T>
+__device__ __forceinline__ void factor_columns(T (&a)[LU_NB], int r, int kw, int R, int tid, T* __restrict__ prow,
+                                               bool& bad) {
+  if constexpr (C < LU_NB) {
+    factor_column<C>(a, r, kw, R, tid, prow, bad);
+    factor_columns<C + 1>(a, r, kw, R, tid, prow, bad);
   }
 }
 
 // Factor the panel whose rows are held in registers (row r = threadIdx.x relative to k0,
-// columns k0..k0+kw-1); the pivot row is broadcast through shared memory.  Writes the band,
-// the slabs and the factored panel into Pn (row stride SP).
+// columns k0..k0+kw-1); the pivot row is broadcast through shared memory, one barrier per
+// column.  Writes the factor slabs, the factored diagonal block into the band (for the
+// inverses of its triangles) and the factored panel into Pn (row stride SP).  The rest of
+// the band keeps the entries before factorisation: nothing reads factored entries from it.
 template <typename T>
-__device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku, int ldab,
-                            T* __restrict__ AB, T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn,
-                            T* __restrict__ prow, int* status) {
+__device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku, int ldab, T* __restrict__ AB,
+                            T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn, T* __restrict__ prow,
+                            int* status) {
   constexpr int NB = LU_NB;
   const int tid = threadIdx.x;
   const int r = tid, i = k0 + r;
-  // one barrier per column: the owner of pivot row c+1 (thread c+1) applies column c to its
-  // row, then publishes it with the reciprocal of its pivot into the other half of prow
   bool bad = false;
   if (tid == 0) {
     T piv = a[0];
@@ -212,35 +296,10 @@ __device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku
       bad = true;
       piv = T(1);
     }
-#pragma unroll
-    for (int c2 = 0; c2 < NB; ++c2) prow[c2] = a[c2];
-    prow[NB] = T(1) / piv;
+    put_pivot_row(prow, a, T(1) / piv);
   }
   __syncthreads();
-#pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    if (c < kw) {
-      const T* pr = prow + (c & 1) * (NB + 2);
-      T* pn = prow + ((c + 1) & 1) * (NB + 2);
-      if (r > c && r < R) {
-        const T l = a[c] * pr[NB];
-        a[c] = l;
-#pragma unroll
-        for (int c2 = c + 1; c2 < NB; ++c2) a[c2] -= l * pr[c2];
-      }
-      if (c + 1 < kw && tid == c + 1) {
-        T piv = a[c + 1];
-        if (bad_pivot(piv)) {
-          bad = true;
-          piv = T(1);
-        }
-#pragma unroll
-        for (int c2 = 0; c2 < NB; ++c2) pn[c2] = a[c2];
-        pn[NB] = T(1) / piv;
-      }
-      __syncthreads();
-    }
-  }
+  factor_columns<0>(a, r, kw, R, tid, prow, bad);
   if (bad) atomicOr(status, 1);
   if (r < R) {
 #pragma unroll
@@ -248,7 +307,7 @@ __device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku
       const int j = k0 + c;
       Pn[r * SP + c] = a[c];
       if (c < kw && i - j <= kl && j - i <= ku) {
-        AB[(int64_t)j * ldab + (ku + i - j)] = a[c];
+        if (r < NB) AB[(int64_t)j * ldab + (ku + i - j)] = a[c];
         if (i > j) LS[lsl_idx(i, j, kl)] = a[c];
         else if (i < j) US[usl_idx(i, j, ku)] = a[c];
       }
@@ -259,8 +318,8 @@ __device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku
 // Factor the panel held in shared memory Pn (row stride SP, rows 0..R-1 relative to k0,
 // columns k0..k0+kw-1), for panels taller than the CTA: each thread updates rows tid,
 // tid + THREADS, ... one column at a time.  Same arithmetic as factor_rows (multiplier =
-// entry x reciprocal of the pivot), so both give the same factors.  Writes the band and the
-// slabs.
+// entry x reciprocal of the pivot), so both give the same factors.  Writes the slabs and the
+// factored diagonal block into the band.
 template <typename T>
 __device__ void factor_panel_smem(int k0, int kw, int R, int kl, int ku, int ldab, T* __restrict__ AB,
                                   T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn, int* status) {
@@ -292,7 +351,7 @@ __device__ void factor_panel_smem(int k0, int kw, int R, int kl, int ku, int lda
       const int j = k0 + c;
       if (i - j <= kl && j - i <= ku) {
         const T v = Pn[r * SP + c];
-        AB[(int64_t)j * ldab + (ku + i - j)] = v;
+        if (r < NB) AB[(int64_t)j * ldab + (ku + i - j)] = v;
         if (i > j) LS[lsl_idx(i, j, kl)] = v;
         else if (i < j) US[usl_idx(i, j, ku)] = v;
       }
@@ -301,11 +360,15 @@ __device__ void factor_panel_smem(int k0, int kw, int R, int kl, int ku, int lda
 }
 
 // U12 = L11^{-1} A12 for one column block: A12 (rows k0.., columns c0..) is loaded into Ub
-// (row stride SP) and multiplied by the inverse Li (column-major NB x NB); the result goes to
-// the band, the U slab and the unpadded copy Uv used for broadcast reads.
+// (row stride SP) with lanes along rows (coalesced band reads) and multiplied by the inverse
+// Li (column-major, column stride ls) with lanes along columns, so that every shared-memory
+// access is conflict-free: Li is read by broadcast, Ub and Uv along rows.  The result goes to
+// the unpadded copy Uv used for broadcast reads, back into Ub, and from there, lanes along
+// rows again, to the U slab.
 template <typename T>
-__device__ void form_u12(const T* __restrict__ Li, T* __restrict__ Ub, T* __restrict__ Uv, T* __restrict__ AB,
-                         T* __restrict__ US, int k0, int kw, int c0, int cw, int kl, int ku, int ldab) {
+__device__ void form_u12(const T* __restrict__ Li, int ls, T* __restrict__ Ub, T* __restrict__ Uv,
+                         const T* __restrict__ AB, T* __restrict__ US, int k0, int kw, int c0, int cw, int kl, int ku,
+                         int ldab) {
   constexpr int NB = LU_NB;
   constexpr int THREADS = lu_threads<T>();
   constexpr int PER = (NB * NB + THREADS - 1) / THREADS;
@@ -314,7 +377,7 @@ __device__ void form_u12(const T* __restrict__ Li, T* __restrict__ Ub, T* __rest
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int idx = tid + q * THREADS;
-    const int jj = idx / NB, ii = idx - jj * NB;
+    const int jj = idx / NB, ii = idx - jj * NB;          // lanes along rows
     const int i = k0 + ii, j = c0 + jj;
     v[q] = (idx < NB * NB && ii < kw && jj < cw && j - i <= ku && i - j <= kl)
                ? __ldcg(AB + (int64_t)j * ldab + (ku + i - j)) : T(0);
@@ -329,11 +392,11 @@ __device__ void form_u12(const T* __restrict__ Li, T* __restrict__ Ub, T* __rest
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int idx = tid + q * THREADS;
-    const int jj = idx / NB, ii = idx - jj * NB;
+    const int ii = idx / NB, jj = idx - ii * NB;          // lanes along columns
     T acc = T(0);
     if (idx < NB * NB) {
 #pragma unroll
-      for (int p = 0; p < NB; ++p) acc += Li[p * NB + ii] * Ub[p * SP + jj];
+      for (int p = 0; p < NB; ++p) acc += Li[p * ls + ii] * Ub[p * SP + jj];
     }
     v[q] = acc;
   }
@@ -341,20 +404,29 @@ __device__ void form_u12(const T* __restrict__ Li, T* __restrict__ Ub, T* __rest
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int idx = tid + q * THREADS;
-    const int jj = idx / NB, ii = idx - jj * NB;
-    if (idx >= NB * NB) continue;
-    Uv[ii * NB + jj] = v[q];
-    const int i = k0 + ii, j = c0 + jj;
-    if (ii < kw && jj < cw && j - i <= ku && i - j <= kl) {
-      AB[(int64_t)j * ldab + (ku + i - j)] = v[q];
-      US[usl_idx(i, j, ku)] = v[q];
+    const int ii = idx / NB, jj = idx - ii * NB;
+    if (idx < NB * NB) {
+      Uv[ii * NB + jj] = v[q];
+      Ub[ii * SP + jj] = v[q];
     }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = tid + q * THREADS;
+    const int jj = idx / NB, ii = idx - jj * NB;          // lanes along rows
+    const int i = k0 + ii, j = c0 + jj;
+    if (idx < NB * NB && ii < kw && jj < cw && j - i <= ku && i - j <= kl) US[usl_idx(i, j, ku)] = Ub[ii * SP + jj];
   }
   __syncthreads();
 }
 
 // Inverse of the unit lower triangle of a factored diagonal block (rows 0..NB-1 of the panel
-// in Pn, row stride SP), column-major into Li (shared) and dli (global).  Threads 0..NB-1.
+// in Pn, row stride SP), by warp 0 (lane j: column j, by substitution in registers), into Li
+// (shared, column-major with column stride SP, so that the lanes' stores fall in different
+// banks) and then, lanes along rows, into dli (global, column-major NB x NB, coalesced).
+// (The inverse of the upper triangle, which only the solves need, is formed afterwards from
+// the diagonal block kept in the band.)
 template <typename T>
 __device__ void unit_lower_inverse(const T* __restrict__ Pn, int kw, T* __restrict__ Li, T* __restrict__ dli) {
   constexpr int NB = LU_NB;
@@ -369,10 +441,10 @@ __device__ void unit_lower_inverse(const T* __restrict__ Pn, int kw, T* __restri
       x[i] = (i < kw) ? v : T(0);
     }
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      Li[j * NB + i] = x[i];
-      dli[j * NB + i] = x[i];
-    }
+    for (int i = 0; i < NB; ++i) Li[j * SP + i] = x[i];
+    __syncwarp();
+#pragma unroll 4
+    for (int c = 0; c < NB; ++c) dli[c * NB + j] = Li[c * SP + j];
   }
 }
 
@@ -431,10 +503,11 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);     // one mbarrier (bulk CTAs)
   T* Uv = reinterpret_cast<T*>(smem_raw + 128);              // NB x NB
-  T* Li = Uv + NB * NB;                                      // NB x NB, L11^{-1} column-major
-  T* Ub = Li + NB * NB;                                      // NB x SP
-  T* prow = Ub + NB * SP;                                    // 2 x (NB + 2) pivot rows
-  T* Pn = prow + 2 * (NB + 2);                               // critical: (NB + kl) x SP panel
+  T* Li = Uv + NB * NB;                                      // L11^{-1} column-major: NB x SP (critical),
+                                                             // NB x NB by TMA (bulk)
+  T* Ub = Li + NB * SP;                                      // NB x SP
+  T* prow = Ub + NB * SP;                                    // 2 x PR pivot rows (16-byte aligned)
+  T* Pn = prow + 2 * PR;                                     // critical: (NB + kl) x SP panel
   T* Ls = prow;                                              // bulk: NB x kl L slab (16-byte aligned)
   __shared__ int abort_flag;
   const int nblk = (n + NB - 1) / NB;
@@ -476,7 +549,7 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
       }
       __syncthreads();
       if (abort_flag) return;
-      form_u12<T>(Li, Ub, Uv, AB, US, k0, NB, c0, cw, kl, ku, ldab);
+      form_u12<T>(Li, SP, Ub, Uv, AB, US, k0, NB, c0, cw, kl, ku, ldab);
       // rows of the next panel, updated by this panel, in slices of THREADS rows: row r2 reads
       // row r2 + NB of this panel, so a slice is written back only after all its reads
       for (int q = 0; q < nslice; ++q) {
@@ -527,7 +600,7 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
       }
       __syncthreads();
       if (abort_flag) return;
-      form_u12<T>(Li, Ub, Uv, AB, US, k0, NB, c0, cw, kl, ku, ldab);
+      form_u12<T>(Li, SP, Ub, Uv, AB, US, k0, NB, c0, cw, kl, ku, ldab);
       // the row of the next panel held by this thread, updated by this panel on the way in
       {
         const int r2 = tid, i = c0 + r2, r = r2 + NB;
@@ -582,7 +655,7 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
       if (abort_flag) return;
       for (int cb = first; cb <= cbl; cb += LU_BULK) {
         const int c0 = cb * NB, cw = min(NB, n - c0);
-        form_u12<T>(Li, Ub, Uv, AB, US, k0, kw, c0, cw, kl, ku, ldab);
+        form_u12<T>(Li, NB, Ub, Uv, AB, US, k0, kw, c0, cw, kl, ku, ldab);
         // A22 -= L21 U12: warp pairs share 32 rows (lane = row), each warp one half of the columns
         const int h = warp & 1, groups = nwarp / 2;
         for (int rb = kw + (warp >> 1) * 32; rb < R; rb += groups * 32) {
@@ -616,13 +689,13 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
   }
 }
 
-// Dynamic shared memory of the LU kernel: mbarrier (128 B), Uv, Li (NB x NB each), Ub
-// (NB x SP), then the larger of [pivot rows 2 (NB + 2) + critical panel (NB + kl) x SP] and
-// the bulk slab NB x kl.
+// Dynamic shared memory of the LU kernel: mbarrier (128 B), Uv (NB x NB), Li and Ub
+// (NB x SP each), then the larger of [pivot rows 2 x PR + critical panel (NB + kl) x SP] and the
+// bulk slab NB x kl.
 template <typename T>
 size_t band_lu_smem_bytes(int kl_max) {
-  const size_t head = (size_t)2 * LU_NB * LU_NB + LU_NB * SP;
-  const size_t tail = std::max((size_t)2 * (LU_NB + 2) + (size_t)(LU_NB + kl_max) * SP, (size_t)LU_NB * kl_max);
+  const size_t head = (size_t)LU_NB * LU_NB + 2 * LU_NB * SP;
+  const size_t tail = std::max((size_t)2 * PR + (size_t)(LU_NB + kl_max) * SP, (size_t)LU_NB * kl_max);
   return 128 + (head + tail) * sizeof(T);
 }
 
