@@ -242,77 +242,112 @@ __device__ __forceinline__ void put_pivot_row(T* __restrict__ pn, const T (&a)[L
   pn[NB] = rcp;
 }
 
-// Column C of the panel factorisation: rows below the pivot take their multiplier and update
-// their tails; the owner of row C + 1 then publishes it as the next pivot row.
+// Column C of the factorisation of the diagonal block by warp 0, lane r holding row r: the
+// pivot and the tail of pivot row C are broadcast by warp shuffles, the rows below take their
+// multiplier and update their tails.
 template <int C, typename T>
-__device__ __forceinline__ void factor_column(T (&a)[LU_NB], int r, int kw, int R, int tid, T* __restrict__ prow,
-                                              bool& bad) {
-  constexpr int NB = LU_NB;
-  if (C < kw) {
-    const T* pr = prow + (C & 1) * PR;
-    T* pn = prow + ((C + 1) & 1) * PR;
-    if (r > C && r < R) {
-      const T l = a[C] * pr[NB];
-      a[C] = l;
-      axpy_tail<C>(a, l, pr);
-    }
-    if (C + 1 < kw && tid == C + 1) {
-      T piv = a[C + 1];
+__device__ __forceinline__ void diag_columns(T (&a)[LU_NB], int lane, int kw, bool& bad) {
+  if constexpr (C < LU_NB) {
+    if (C < kw) {
+      T piv = __shfl_sync(0xffffffffu, a[C], C);
       if (bad_pivot(piv)) {
         bad = true;
         piv = T(1);
       }
-      put_pivot_row(pn, a, T(1) / piv);
+      const T rcp = T(1) / piv;
+      const T l = a[C] * rcp;
+      if (lane > C) a[C] = l;
+#pragma unroll
+      for (int c2 = C + 1; c2 < LU_NB; ++c2) {
+        const T u = __shfl_sync(0xffffffffu, a[c2], C);
+        if (lane > C) a[c2] -= l * u;
+      }
+      diag_columns<C + 1>(a, lane, kw, bad);
     }
-    __syncthreads();
   }
 }
 
+// A row below the diagonal block, against the stored pivot rows (row C of Ud: U(C, .) and
+// the reciprocal of the pivot at NB), column by column with no synchronisation.
 template <int C, typename T>
-__device__ __forceinline__ void factor_columns(T (&a)[LU_NB], int r, int kw, int R, int tid, T* __restrict__ prow,
-                                               bool& bad) {
+__device__ __forceinline__ void sub_columns(T (&a)[LU_NB], int kw, const T* __restrict__ Ud) {
   if constexpr (C < LU_NB) {
-    factor_column<C>(a, r, kw, R, tid, prow, bad);
-    factor_columns<C + 1>(a, r, kw, R, tid, prow, bad);
+    if (C < kw) {
+      const T* pr = Ud + C * PR;
+      const T l = a[C] * pr[LU_NB];
+      a[C] = l;
+      axpy_tail<C>(a, l, pr);
+      sub_columns<C + 1>(a, kw, Ud);
+    }
   }
 }
 
 // Factor the panel whose rows are held in registers (row r = threadIdx.x relative to k0,
-// columns k0..k0+kw-1); the pivot row is broadcast through shared memory, one barrier per
-// column.  Writes the factor slabs, the factored diagonal block into the band (for the
-// inverses of its triangles) and the factored panel into Pn (row stride SP).  The rest of
-// the band keeps the entries before factorisation: nothing reads factored entries from it.
+// columns k0..k0+kw-1).  Warp 0 factors the diagonal block (warp shuffles, no block
+// barrier) and stores its rows, each with the reciprocal of its pivot, as the pivot rows Ud
+// (NB x PR); after one barrier every other row eliminates against them on its own.  Every
+// multiplier and update is the operation a right-looking elimination of the panel performs,
+// in the same order.  The factored rows go to shared memory only: the L part of every row into the
+// skewed buffer Lsk (NB x kl, column c at c * kl, row r at r - c - 1: the layout of the
+// block's L slab, so that one bulk copy stores it, and conflict-free for lanes along rows),
+// rows 0..NB-1 (the diagonal block) into Dt (row stride SP); those rows also write their U
+// part to the U slab and the diagonal block into the band (for the inverses of its
+// triangles).  Rows past the matrix hold zeros and fill their slots of Lsk.
 template <typename T>
 __device__ void factor_rows(T (&a)[LU_NB], int k0, int kw, int R, int kl, int ku, int ldab, T* __restrict__ AB,
-                            T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn, T* __restrict__ prow,
+                            T* __restrict__ US, T* __restrict__ Dt, T* __restrict__ Lsk, T* __restrict__ Ud,
                             int* status) {
   constexpr int NB = LU_NB;
   const int tid = threadIdx.x;
   const int r = tid, i = k0 + r;
   bool bad = false;
-  if (tid == 0) {
-    T piv = a[0];
-    if (bad_pivot(piv)) {
-      bad = true;
-      piv = T(1);
-    }
-    put_pivot_row(prow, a, T(1) / piv);
+  if (tid < NB) {
+    diag_columns<0>(a, tid, kw, bad);
+    // this lane's pivot (the same value, hence the same reciprocal, as in its column step)
+    T piv = T(0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c == tid) piv = a[c];
+    if (bad_pivot(piv)) piv = T(1);
+    put_pivot_row(Ud + tid * PR, a, T(1) / piv);
   }
   __syncthreads();
-  factor_columns<0>(a, r, kw, R, tid, prow, bad);
+  if (r >= NB && r < R) sub_columns<0>(a, kw, Ud);
   if (bad) atomicOr(status, 1);
-  if (r < R) {
+  if (r < NB + kl) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      const int o = r - c - 1;
+      if (o >= 0 && o < kl) Lsk[c * kl + o] = a[c];
+    }
+  }
+  if (r < NB && r < R) {
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       const int j = k0 + c;
-      Pn[r * SP + c] = a[c];
+      Dt[r * SP + c] = a[c];
       if (c < kw && i - j <= kl && j - i <= ku) {
-        if (r < NB) AB[(int64_t)j * ldab + (ku + i - j)] = a[c];
-        if (i > j) LS[lsl_idx(i, j, kl)] = a[c];
-        else if (i < j) US[usl_idx(i, j, ku)] = a[c];
+        AB[(int64_t)j * ldab + (ku + i - j)] = a[c];
+        if (i < j) US[usl_idx(i, j, ku)] = a[c];
       }
     }
   }
+}
+
+// Bulk copy of the skewed L buffer to the block's L slab (one thread; after a barrier that
+// follows the buffer's writes).  tma_store_wait must run before the slab is published.
+template <typename T>
+__device__ __forceinline__ void tma_store_lslab(T* __restrict__ dst, const T* __restrict__ Lsk, int kl) {
+  if (kl <= 0) return;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const unsigned src = smem_u32(Lsk);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"((unsigned)(LU_NB * kl * sizeof(T))) : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // Factor the panel held in shared memory Pn (row stride SP, rows 0..R-1 relative to k0,
@@ -506,8 +541,10 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
   T* Li = Uv + NB * NB;                                      // L11^{-1} column-major: NB x SP (critical),
                                                              // NB x NB by TMA (bulk)
   T* Ub = Li + NB * SP;                                      // NB x SP
-  T* prow = Ub + NB * SP;                                    // 2 x PR pivot rows (16-byte aligned)
-  T* Pn = prow + 2 * PR;                                     // critical: (NB + kl) x SP panel
+  T* prow = Ub + NB * SP;                                    // NB x PR pivot rows (16-byte aligned)
+  T* Pn = prow + NB * PR;                                    // critical, wide: (NB + kl) x SP panel
+  T* Dt = prow + NB * PR;                                    // critical: NB x SP diagonal block
+  T* Lsk = Dt + NB * SP;                                     // critical: NB x kl skewed L (16-byte aligned)
   T* Ls = prow;                                              // bulk: NB x kl L slab (16-byte aligned)
   __shared__ int abort_flag;
   const int nblk = (n + NB - 1) / NB;
@@ -582,11 +619,15 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
 #pragma unroll
       for (int c = 0; c < NB; ++c)
         a[c] = (r < R && c < kw && r - c <= kl && c - r <= ku) ? __ldcg(AB + (int64_t)c * ldab + (ku + r - c)) : T(0);
-      factor_rows<T>(a, 0, kw, R, kl, ku, ldab, AB, LS, US, Pn, prow, st);
+      factor_rows<T>(a, 0, kw, R, kl, ku, ldab, AB, US, Dt, Lsk, prow, st);
       __syncthreads();
-      unit_lower_inverse<T>(Pn, kw, Li, DI);
+      if (tid == 0) tma_store_lslab(LS, Lsk, kl);
+      unit_lower_inverse<T>(Dt, kw, Li, DI);
       __syncthreads();
-      if (tid == 0) st_release(flag + 0, epoch);   // release orders the CTA's writes (after the barrier)
+      if (tid == 0) {
+        tma_store_wait();
+        st_release(flag + 0, epoch);   // release orders the CTA's writes (after the barrier)
+      }
     }
     for (int kb = 0; kb + 1 < nblk; ++kb) {
       const int k0 = kb * NB, R = min(n, k0 + NB + kl) - k0;
@@ -609,14 +650,20 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
           const int j = c0 + c;
           a[c] = (r2 < R2 && c < cw && i - j <= kl && j - i <= ku) ? __ldcg(AB + (int64_t)j * ldab + (ku + i - j)) : T(0);
         }
-        if (r2 < R2 && r < R) row_update<T, NB>(a, [&](int p) { return Pn[r * SP + p]; }, Uv, 0);
+        // L(r, p) of this panel, zero outside the band
+        if (r2 < R2 && r < R)
+          row_update<T, NB>(a, [&](int p) { return r - p - 1 < kl ? Lsk[p * kl + (r - p - 1)] : T(0); }, Uv, 0);
       }
       __syncthreads();
-      factor_rows<T>(a, c0, cw, R2, kl, ku, ldab, AB, LS, US, Pn, prow, st);
+      factor_rows<T>(a, c0, cw, R2, kl, ku, ldab, AB, US, Dt, Lsk, prow, st);
       __syncthreads();
-      unit_lower_inverse<T>(Pn, cw, Li, DI + (int64_t)cb * 2 * NB * NB);
+      if (tid == 0) tma_store_lslab(LS + (int64_t)cb * NB * kl, Lsk, kl);
+      unit_lower_inverse<T>(Dt, cw, Li, DI + (int64_t)cb * 2 * NB * NB);
       __syncthreads();
-      if (tid == 0) st_release(flag + cb, epoch);
+      if (tid == 0) {
+        tma_store_wait();
+        st_release(flag + cb, epoch);
+      }
     }
   } else {
     // ------------------------------------------------ bulk CTAs: blocks p+2 .. of every panel p
@@ -690,12 +737,16 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
 }
 
 // Dynamic shared memory of the LU kernel: mbarrier (128 B), Uv (NB x NB), Li and Ub
-// (NB x SP each), then the larger of [pivot rows 2 x PR + critical panel (NB + kl) x SP] and the
-// bulk slab NB x kl.
+// (NB x SP each), then the larger of the chain CTA's part [pivot rows NB x PR, then the
+// diagonal block NB x SP and the skewed L buffer NB x kl, or (wide) the panel (NB + kl) x SP]
+// and the bulk CTAs' L slab NB x kl.
 template <typename T>
 size_t band_lu_smem_bytes(int kl_max) {
   const size_t head = (size_t)LU_NB * LU_NB + 2 * LU_NB * SP;
-  const size_t tail = std::max((size_t)2 * PR + (size_t)(LU_NB + kl_max) * SP, (size_t)LU_NB * kl_max);
+  const bool wide = LU_NB + kl_max > lu_threads<T>();
+  const size_t chain = wide ? (size_t)LU_NB * PR + (size_t)(LU_NB + kl_max) * SP
+                            : (size_t)LU_NB * PR + (size_t)LU_NB * SP + (size_t)LU_NB * kl_max;
+  const size_t tail = std::max(chain, (size_t)LU_NB * kl_max);
   return 128 + (head + tail) * sizeof(T);
 }
 
