@@ -925,8 +925,10 @@ cudaError_t launch_chol_to_lu(const SysDev* sys_chol, const SysDev* sys_lu, cons
 // completing on an mbarrier, STAGES blocks ahead of the one being solved.  Each block is
 // finished by one warp with the inverse (a GEMV), then the rows coupled to it by the band are
 // updated by all threads.  The vector lives in shared memory in precision T.
+constexpr int SOLVE_THREADS = 512;
+
 template <typename T, int STAGES, bool GV>
-__global__ void __launch_bounds__(256) band_solve_kernel(const SysDev* __restrict__ sys,
+__global__ void __launch_bounds__(SOLVE_THREADS) band_solve_kernel(const SysDev* __restrict__ sys,
                                                          const int* __restrict__ list,
                                                          const T* __restrict__ lslab, const T* __restrict__ uslab,
                                                          const T* __restrict__ dinv_all,
@@ -1005,36 +1007,37 @@ __global__ void __launch_bounds__(256) band_solve_kernel(const SysDev* __restric
     const T* Dv = stage0 + s * stage_elems;
     const T* sl = Dv + NB * NB;
     if (warp == 0) {
-      T acc = T(0);
-#pragma unroll 8
-      for (int p = 0; p < kw; ++p) acc += Dv[p * NB + lane] * v[k0 + p];
-      yb[lane] = lane < kw ? acc : T(0);
+      // four partial sums: short dependency chains
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int p = 0; p < NB; ++p)
+        if (p < kw) acc[p & 3] += Dv[p * NB + lane] * v[k0 + p];
+      yb[lane] = lane < kw ? (acc[0] + acc[1]) + (acc[2] + acc[3]) : T(0);
     }
     __syncthreads();
     if (tid < kw) v[k0 + tid] = yb[tid];
     if (fwd) {
       const int rend = min(n, k0 + kw + kl);
       for (int i = k0 + kw + tid; i < rend; i += blockDim.x) {
-        T acc = v[i];
-        // L(i, k0 + c) = sl[c * kl + (i - k0 - c - 1)], valid for 0 <= i - k0 - c - 1 < kl
-#pragma unroll 8
-        for (int c = 0; c < kw; ++c) {
-          const int o = i - k0 - c - 1;
-          if (o < kl) acc -= sl[c * w + o] * yb[c];
-        }
-        v[i] = acc;
+        // L(i, k0 + c) = sl[c * kl + (i - k0 - c - 1)], valid for 0 <= i - k0 - c - 1 < kl;
+        // four partial sums
+        const int ob = i - k0 - 1;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c < kw && ob - c < kl) acc[c & 3] += sl[c * w + (ob - c)] * yb[c];
+        v[i] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
       }
     } else {
       const int rbeg = max(0, k0 - ku);
       for (int i = rbeg + tid; i < k0; i += blockDim.x) {
-        T acc = v[i];
         // U(i, k0 + c) = sl[c * ku + (i - k0 - c + ku)], valid for 0 <= i - k0 - c + ku
-#pragma unroll 8
-        for (int c = 0; c < kw; ++c) {
-          const int o = i - k0 - c + ku;
-          if (o >= 0) acc -= sl[c * w + o] * yb[c];
-        }
-        v[i] = acc;
+        const int ob = i - k0 + ku;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c < kw && ob - c >= 0) acc[c & 3] += sl[c * w + (ob - c)] * yb[c];
+        v[i] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
       }
     }
     __syncthreads();
@@ -1062,7 +1065,7 @@ static cudaError_t launch_solve_variant(size_t smem, const SysDev* sys, const in
   cudaError_t e = cudaFuncSetAttribute(band_solve_kernel<T, STAGES, GV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  band_solve_kernel<T, STAGES, GV><<<nsys, 256, smem, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax,
+  band_solve_kernel<T, STAGES, GV><<<nsys, SOLVE_THREADS, smem, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate, kmax,
                                                             done, status, skip, vwork);
   return cudaGetLastError();
 }
