@@ -86,6 +86,10 @@ struct tpns_ctx {
   double* d_dinv_coarse = nullptr;
   void *d_lslab_local = nullptr, *d_uslab_local = nullptr;
   double *d_lslab_coarse = nullptr, *d_uslab_coarse = nullptr;
+  // FP32 factors of the coarse conduit Jacobian (FP32_IR contexts): band, slabs, inverses at
+  // the same element offsets as the FP64 coarse buffers
+  float *d_band_coarse_f = nullptr, *d_lslab_coarse_f = nullptr, *d_uslab_coarse_f = nullptr,
+        *d_dinv_coarse_f = nullptr;
   int* d_flags = nullptr;
   int* d_epoch = nullptr;
   SysDev* d_sys_chol = nullptr;
@@ -496,6 +500,14 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     TRY(dalloc(ctx, &ctx->d_uslab_coarse, ctx->uslab_coarse_len));
     CK(cudaMemset(ctx->d_lslab_coarse, 0, (size_t)ctx->lslab_coarse_len * 8));
     CK(cudaMemset(ctx->d_uslab_coarse, 0, (size_t)ctx->uslab_coarse_len * 8));
+    if (ctx->prec == TPNS_FP32_IR) {
+      TRY(dalloc(ctx, &ctx->d_band_coarse_f, ctx->band_coarse_len));
+      TRY(dalloc(ctx, &ctx->d_dinv_coarse_f, ctx->dinv_coarse_len));
+      TRY(dalloc(ctx, &ctx->d_lslab_coarse_f, ctx->lslab_coarse_len));
+      TRY(dalloc(ctx, &ctx->d_uslab_coarse_f, ctx->uslab_coarse_len));
+      CK(cudaMemset(ctx->d_lslab_coarse_f, 0, (size_t)ctx->lslab_coarse_len * 4));
+      CK(cudaMemset(ctx->d_uslab_coarse_f, 0, (size_t)ctx->uslab_coarse_len * 4));
+    }
   }
   TRY(dalloc(ctx, &ctx->d_Ke, (size_t)(ctx->ne_osl + ctx->ne_cf) * 225));
   TRY(dalloc(ctx, &ctx->d_Re, (size_t)(ctx->ne_osl + ctx->ne_cf) * 15));
@@ -744,6 +756,10 @@ static tpns_status prolong_and_glue(tpns_ctx* ctx) {
   return TPNS_OK;
 }
 
+// refinement passes of a coarse Newton correction (FP32 factors): the first residual, then
+// up to COARSE_IR_MAX - 1 solve + residual pairs; converged passes exit at once
+constexpr int COARSE_IR_MAX = 6;
+
 static tpns_status coarse_step(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   const int CF = ctx->nf, CP = ctx->nf + 1 + ctx->np;
@@ -766,16 +782,44 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
     CK(launch_oseen_elem(ctx->asmargs, ctx->e_off[CF], ctx->ne_cf, ctx->d_Ke, ctx->d_Re, st, skip));
     CK(launch_seg_reduce(ctx->d_mcf_t, ctx->d_mcf_s, ctx->n_mcf, ctx->d_Ke, ctx->d_vals, st, skip));
     CK(launch_seg_reduce(ctx->d_rcf_t, ctx->d_rcf_s, ctx->n_rcf, ctx->d_Re, ctx->d_b, st, skip));
-    CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
-                                ctx->d_band_coarse, 0, 0, st, skip));
-    CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse, ctx->d_lslab_coarse,
-                              ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_flags, ctx->flags_stride, ctx->d_epoch, ctx->d_status,
-                              st, skip));
-    CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->nblk_max_cf, ctx->d_band_coarse,
-                                ctx->d_dinv_coarse, st, skip));
-    CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->n_max_cf, ctx->kmax_cf, ctx->d_lslab_coarse,
-                                 ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_b, ctx->d_x, 0, nullptr,
-                                 ctx->d_status, st, skip));
+    if (ctx->prec == TPNS_FP32_IR) {
+      // Newton correction from FP32 band factors of the Jacobian, refined against the FP64
+      // Jacobian: FP64 arithmetic is scarce on this GPU, FP64 residuals are cheap
+      CK(launch_band_fill<float>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
+                                 ctx->d_band_coarse_f, 0, 0, st, skip));
+      CK(launch_band_lu<float>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse_f,
+                               ctx->d_lslab_coarse_f, ctx->d_uslab_coarse_f, ctx->d_dinv_coarse_f, ctx->d_flags,
+                               ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, skip));
+      CK(launch_band_dinv<float>(ctx->d_sys, ctx->d_list_cf, 1, ctx->nblk_max_cf, ctx->d_band_coarse_f,
+                                 ctx->d_dinv_coarse_f, st, skip));
+      const double tol = 1e-13;
+      CK(launch_residual(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b, ctx->d_x,
+                         ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial,
+                         ctx->d_ticket, tol, 1, st, skip));
+      CK(launch_band_solve<float>(ctx->d_sys, ctx->d_list_cf, 1, ctx->n_max_cf, ctx->kmax_cf, ctx->d_lslab_coarse_f,
+                                  ctx->d_uslab_coarse_f, ctx->d_dinv_coarse_f, ctx->d_b, ctx->d_x, 0, nullptr,
+                                  ctx->d_status, st, skip));
+      for (int r = 0; r < COARSE_IR_MAX; ++r) {
+        CK(launch_residual(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
+                           ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial,
+                           ctx->d_ticket, tol, 0, st, skip));
+        if (r + 1 < COARSE_IR_MAX)
+          CK(launch_band_solve<float>(ctx->d_sys, ctx->d_list_cf, 1, ctx->n_max_cf, ctx->kmax_cf,
+                                      ctx->d_lslab_coarse_f, ctx->d_uslab_coarse_f, ctx->d_dinv_coarse_f, ctx->d_r,
+                                      ctx->d_x, 1, ctx->d_done, ctx->d_status, st, skip));
+      }
+    } else {
+      CK(launch_band_fill<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
+                                  ctx->d_band_coarse, 0, 0, st, skip));
+      CK(launch_band_lu<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->kl_max_cf, ctx->d_band_coarse,
+                                ctx->d_lslab_coarse, ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_flags,
+                                ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, skip));
+      CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->nblk_max_cf, ctx->d_band_coarse,
+                                  ctx->d_dinv_coarse, st, skip));
+      CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cf, 1, ctx->n_max_cf, ctx->kmax_cf, ctx->d_lslab_coarse,
+                                   ctx->d_uslab_coarse, ctx->d_dinv_coarse, ctx->d_b, ctx->d_x, 0, nullptr,
+                                   ctx->d_status, st, skip));
+    }
     CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cf, ctx->nn_cf, ctx->d_x, st, skip));
     CK(launch_newton_update(ctx->d_probs + CF, ctx->d_gnode, ctx->d_vloc, L.cfl.nn, L.cfl.nvl, ctx->d_uc_new,
                             ctx->d_pc_new, ctx->d_newton_done, ctx->d_newton_iters, st));
