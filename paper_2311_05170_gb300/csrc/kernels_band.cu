@@ -351,34 +351,45 @@ __device__ __forceinline__ void tma_store_wait() {
 }
 
 // Factor the panel held in shared memory Pn (row stride SP, rows 0..R-1 relative to k0,
-// columns k0..k0+kw-1), for panels taller than the CTA: each thread updates rows tid,
-// tid + THREADS, ... one column at a time.  Same arithmetic as factor_rows (multiplier =
-// entry x reciprocal of the pivot), so both give the same factors.  Writes the slabs and the
-// factored diagonal block into the band.
+// columns k0..k0+kw-1), for panels taller than the CTA.  Warp 0 takes rows 0..NB-1 into
+// registers and factors the diagonal block as factor_rows does, leaving the pivot rows with
+// their reciprocals in Ud (NB x PR); after one barrier every thread takes its rows tid + NB,
+// tid + NB + THREADS, ... from Pn, eliminates them against Ud and puts them back.  Same
+// operations in the same order as factor_rows, so both give the same factors.  Writes the
+// slabs and the factored diagonal block into the band.
 template <typename T>
 __device__ void factor_panel_smem(int k0, int kw, int R, int kl, int ku, int ldab, T* __restrict__ AB,
-                                  T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn, int* status) {
+                                  T* __restrict__ LS, T* __restrict__ US, T* __restrict__ Pn, T* __restrict__ Ud,
+                                  int* status) {
   constexpr int NB = LU_NB;
   constexpr int THREADS = lu_threads<T>();
   const int tid = threadIdx.x;
-  for (int c = 0; c < kw; ++c) {
-    T piv = Pn[c * SP + c];
-    if (bad_pivot(piv)) {
-      if (tid == 0) atomicOr(status, 1);
-      piv = T(1);
-    }
-    const T inv = T(1) / piv;
-    const T* pr = Pn + c * SP;
-    for (int r = c + 1 + tid; r < R; r += THREADS) {
-      T* row = Pn + r * SP;
-      const T l = row[c] * inv;
-      row[c] = l;
+  bool bad = false;
+  if (tid < NB) {
+    T a[NB];
 #pragma unroll
-      for (int c2 = 0; c2 < NB; ++c2)
-        if (c2 > c) row[c2] -= l * pr[c2];
-    }
-    __syncthreads();
+    for (int c = 0; c < NB; ++c) a[c] = Pn[tid * SP + c];
+    diag_columns<0>(a, tid, kw, bad);
+    T piv = T(0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c == tid) piv = a[c];
+    if (bad_pivot(piv)) piv = T(1);
+    put_pivot_row(Ud + tid * PR, a, T(1) / piv);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Pn[tid * SP + c] = a[c];
   }
+  if (bad) atomicOr(status, 1);
+  __syncthreads();
+  for (int r = NB + tid; r < R; r += THREADS) {
+    T a[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) a[c] = Pn[r * SP + c];
+    sub_columns<0>(a, kw, Ud);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Pn[r * SP + c] = a[c];
+  }
+  __syncthreads();
   for (int r = tid; r < R; r += THREADS) {
     const int i = k0 + r;
 #pragma unroll 4
@@ -567,7 +578,7 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
           Pn[r * SP + c] = (c < kw && r - c <= kl && c - r <= ku) ? __ldcg(AB + (int64_t)c * ldab + (ku + r - c)) : T(0);
       }
       __syncthreads();
-      factor_panel_smem<T>(0, kw, R, kl, ku, ldab, AB, LS, US, Pn, st);
+      factor_panel_smem<T>(0, kw, R, kl, ku, ldab, AB, LS, US, Pn, prow, st);
       __syncthreads();
       unit_lower_inverse<T>(Pn, kw, Li, DI);
       __syncthreads();
@@ -605,7 +616,7 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
         }
       }
       __syncthreads();
-      factor_panel_smem<T>(c0, cw, R2, kl, ku, ldab, AB, LS, US, Pn, st);
+      factor_panel_smem<T>(c0, cw, R2, kl, ku, ldab, AB, LS, US, Pn, prow, st);
       __syncthreads();
       unit_lower_inverse<T>(Pn, cw, Li, DI + (int64_t)cb * 2 * NB * NB);
       __syncthreads();

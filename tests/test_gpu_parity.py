@@ -98,6 +98,21 @@ def test_wide_band_parity(native):
     assert stats["last_ir_relres_max"] <= 1e-12
 
 
+def test_widest_band_global_vector_parity(native):
+    """h = 1/128 with 2 x 2 subdomains per region: Oseen bands of kl = 1123 and 39k unknowns;
+    the solve vector no longer fits in shared memory beside one factor stage, so the solves
+    keep it in global scratch and read the slabs from L2; one step against the oracle."""
+    w = W.config_uniform(4, 32, nsub=(2, 2), nsteps=1)
+    s = native.Solver(w, precision="fp32", host_only=True)
+    info = s.debug_system(0)
+    assert info["kl"] == 1123 and len(info["rowptr"]) - 1 > 38000
+    s.close()
+    f, o, stats = run_pair(native, w, "fp32", 1)
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL["fp32"], (k, rel(f[k], o.fine[k]))
+    assert stats["last_ir_relres_max"] <= 1e-12
+
+
 def test_band_too_wide_for_fp64_is_refused(native):
     """An FP64 panel of 32 + 851 rows does not fit one CTA's shared memory: creation fails
     with TPNS_EINVAL and a message, before any device allocation."""
