@@ -64,11 +64,11 @@ cudaError_t launch_band_fill(const SysDev* sys, const int* list, int nsys, const
 }
 
 // ------------------------------------------------------------------------------ band LU
-// One thread-block cluster of LU_CLUSTER CTAs per system (the cluster keeps the CTAs of a
-// system resident together).  CTA 0 produces every panel: it keeps the current factored
+// One thread-block cluster per system (8 CTAs, or 16 for very wide bands whose trailing
+// updates outweigh the chain; the cluster keeps the CTAs of a system resident together).  CTA 0 produces every panel: it keeps the current factored
 // panel (L11, L21) in shared memory, forms U12 of the next column block, applies
 // A22 -= L21 U12 to that block while loading it into registers, factors it there (no
-// pivoting) and publishes it with a release flag.  CTAs 1..7 own the other column blocks
+// pivoting) and publishes it with a release flag.  The other CTAs own the other column blocks
 // round robin and apply every published panel to them, publishing per-block progress
 // counters that CTA 0 waits for.  Thus the chain of panels never waits for a barrier or a
 // global reload, and the bulk updates run beside it.
@@ -106,7 +106,6 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, unsigne
 template <typename T>
 __host__ __device__ constexpr int lu_threads() { return sizeof(T) == 4 ? 768 : 512; }
 constexpr int SP = LU_NB + 1;                   // padded row stride of shared tiles
-constexpr int LU_BULK = LU_CLUSTER - 1;
 constexpr int WAIT_LIMIT = 1 << 22;
 
 __device__ __forceinline__ void st_release(int* p, int v) {
@@ -525,7 +524,7 @@ __device__ __forceinline__ void row_update(T (&acc)[W], LF lf, const T* __restri
 }
 
 template <typename T, bool WIDE>
-__global__ void __cluster_dims__(LU_CLUSTER, 1, 1) __launch_bounds__(lu_threads<T>(), 1)
+__global__ void __launch_bounds__(lu_threads<T>(), 1)
 band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* __restrict__ band,
                T* __restrict__ lslab, T* __restrict__ uslab, T* __restrict__ dinv_all, int* __restrict__ sync_all,
                int sync_stride, const int* __restrict__ epoch_ptr, int* __restrict__ status, const int* skip) {
@@ -536,7 +535,8 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
   constexpr int HALF = NB / 2;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int sid = list[blockIdx.x / LU_CLUSTER];
+  const int ncta = (int)cluster.num_blocks(), nbulk = ncta - 1;
+  const int sid = list[blockIdx.x / ncta];
   const SysDev S = sys[sid];
   const int n = S.n, kl = S.kl, ku = S.ku, ldab = S.ldab;
   T* AB = band + S.band_off;
@@ -683,7 +683,7 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
       const int k0 = p * NB, kw = min(NB, n - k0), R = min(n, k0 + kw + kl) - k0;
       const int cbl = min(nblk - 1, (k0 + kw - 1 + ku) / NB);
       int first = p + 2;
-      while (first <= cbl && 1 + first % LU_BULK != rank) ++first;
+      while (first <= cbl && 1 + first % nbulk != rank) ++first;
       if (first > cbl) continue;
       if (tid == 0) {
         bool ok = wait_eq(flag + p, epoch);
@@ -711,7 +711,7 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
       ++uses;
       __syncthreads();
       if (abort_flag) return;
-      for (int cb = first; cb <= cbl; cb += LU_BULK) {
+      for (int cb = first; cb <= cbl; cb += nbulk) {
         const int c0 = cb * NB, cw = min(NB, n - c0);
         form_u12<T>(Li, NB, Ub, Uv, AB, US, k0, kw, c0, cw, kl, ku, ldab);
         // A22 -= L21 U12: warp pairs share 32 rows (lane = row), each warp one half of the columns
@@ -780,10 +780,37 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   auto kern = wide ? band_lu_kernel<T, true> : band_lu_kernel<T, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(lu_threads<T>(), 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // very wide bands: 16-CTA clusters (15 CTAs on the trailing updates) when all of them fit
+  // on the device at once and it can place them, else 8
+  int cl = LU_CLUSTER, nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (kl_max > LU_WIDE_CLUSTER_KL && nsys * 2 * LU_CLUSTER <= nsm &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    int nclusters = 0;
+    attr[0].val.clusterDim.x = 2 * LU_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * LU_CLUSTER, 1, 1);
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0) cl = 2 * LU_CLUSTER;
+    cudaGetLastError();
+  }
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(nsys * cl, 1, 1);
   count_launches(2);
   bump_kernel<<<1, 1, 0, st>>>(epoch);
-  kern<<<nsys * LU_CLUSTER, lu_threads<T>(), smem, st>>>(sys, list, band, lslab, uslab, dinv, sync, sync_stride, epoch,
-                                                          status, skip);
+  e = cudaLaunchKernelEx(&cfg, kern, sys, list, band, lslab, uslab, dinv, sync, sync_stride, (const int*)epoch, status,
+                         skip);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
