@@ -523,7 +523,7 @@ __device__ __forceinline__ void row_update(T (&acc)[W], LF lf, const T* __restri
   }
 }
 
-template <typename T, bool WIDE>
+template <typename T, bool WIDE, int CL>
 __global__ void __launch_bounds__(lu_threads<T>(), 1)
 band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* __restrict__ band,
                T* __restrict__ lslab, T* __restrict__ uslab, T* __restrict__ dinv_all, int* __restrict__ sync_all,
@@ -535,8 +535,8 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
   constexpr int HALF = NB / 2;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int ncta = (int)cluster.num_blocks(), nbulk = ncta - 1;
-  const int sid = list[blockIdx.x / ncta];
+  constexpr int nbulk = CL - 1;
+  const int sid = list[blockIdx.x / CL];
   const SysDev S = sys[sid];
   const int n = S.n, kl = S.kl, ku = S.ku, ldab = S.ldab;
   T* AB = band + S.band_off;
@@ -777,8 +777,9 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   if (kl_max < 0 || smem > (size_t)smem_max) return cudaErrorInvalidValue;
   // panels of at most one row per thread are factored from registers
   const bool wide = LU_NB + kl_max > lu_threads<T>();
-  auto kern = wide ? band_lu_kernel<T, true> : band_lu_kernel<T, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER> : band_lu_kernel<T, false, LU_CLUSTER>;
+  auto kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER> : band_lu_kernel<T, false, 2 * LU_CLUSTER>;
+  cudaError_t e = cudaFuncSetAttribute(kern8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -793,13 +794,14 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   int cl = LU_CLUSTER, nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (kl_max > LU_WIDE_CLUSTER_KL && nsys * 2 * LU_CLUSTER <= nsm &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaFuncSetAttribute(kern16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+      cudaFuncSetAttribute(kern16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     int nclusters = 0;
     attr[0].val.clusterDim.x = 2 * LU_CLUSTER;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(2 * LU_CLUSTER, 1, 1);
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0) cl = 2 * LU_CLUSTER;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern16, &cfg) == cudaSuccess && nclusters > 0) cl = 2 * LU_CLUSTER;
     cudaGetLastError();
   }
   attr[0].val.clusterDim.x = cl;
@@ -808,7 +810,7 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   cfg.gridDim = dim3(nsys * cl, 1, 1);
   count_launches(2);
   bump_kernel<<<1, 1, 0, st>>>(epoch);
-  e = cudaLaunchKernelEx(&cfg, kern, sys, list, band, lslab, uslab, dinv, sync, sync_stride, (const int*)epoch, status,
+  e = cudaLaunchKernelEx(&cfg, cl == LU_CLUSTER ? kern8 : kern16, sys, list, band, lslab, uslab, dinv, sync, sync_stride, (const int*)epoch, status,
                          skip);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
