@@ -225,7 +225,7 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
  * The scratch (band, block inverses, row index, vectors, flags) lives in one device array
  * of TPNS_NOALLOC_SCRATCH_BYTES bytes that the library declares statically; every device
  * that loads the library holds it until the process exits.  A system fits when
- *   n*(kl+ku+1)*s + ceil(n/32)*32*(kl+ku+64)*s + 4*nnz + 8*(n+34) + 4*(5+2*ceil(n/32)) + 2048
+ *   n*(kl+ku+1)*s + ceil(n/32)*32*(kl+ku+64)*s + 4*nnz + 8*(n+130) + 4*(5+2*ceil(n/32)) + 2048
  * is at most that size (s = 4 for TPNS_FP32_IR, 8 for TPNS_FP64, plus 256-byte alignment of
  * each piece); larger systems are refused with TPNS_EINVAL.  The first call on a device looks
  * up the array's device address (with that device current); make that first call before any

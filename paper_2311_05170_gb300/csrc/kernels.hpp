@@ -11,8 +11,8 @@ namespace tpns {
 int64_t launch_counter();
 void count_launches(int n);
 
-constexpr int LU_NB = 32;
-constexpr int RES_CHUNKS = 16;   // CTAs per system in the residual kernel        // panel width of the band LU and block size of the solves
+constexpr int LU_NB = 32;        // panel width of the band LU and block size of the solves
+constexpr int RES_CHUNKS = 64;   // CTAs per system in the residual kernel
 constexpr int LU_CLUSTER = 8;    // CTAs per system in the band LU
 constexpr int LU_WIDE_CLUSTER_KL = 600;   // bands wider than this get 2 x LU_CLUSTER CTAs where possible
 

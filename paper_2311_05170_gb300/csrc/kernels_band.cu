@@ -463,7 +463,6 @@ __device__ void form_u12(const T* __restrict__ Li, int ls, T* __restrict__ Ub, T
     const int i = k0 + ii, j = c0 + jj;
     if (idx < NB * NB && ii < kw && jj < cw && j - i <= ku && i - j <= kl) US[usl_idx(i, j, ku)] = Ub[ii * SP + jj];
   }
-  __syncthreads();
 }
 
 // Inverse of the unit lower triangle of a factored diagonal block (rows 0..NB-1 of the panel
@@ -1097,6 +1096,141 @@ bool band_solve_fits_smem(int n_max, int kmax) {
   return 128 + stage + ((size_t)n_max + 4) * sizeof(T) + 1024 <= (size_t)smem_max;
 }
 
+// The solve for systems whose vector lives in global scratch (too large for shared memory):
+// blocks are streamed in halves (diagonal inverse + slab columns 0..15, then columns
+// 16..31) through HS half-stages, so that several halves are in flight even for the widest
+// bands; each half's band updates run as soon as it lands.  Otherwise as band_solve_kernel.
+template <typename T, int HS>
+__global__ void __launch_bounds__(SOLVE_THREADS) band_solve_halves_kernel(
+    const SysDev* __restrict__ sys, const int* __restrict__ list, const T* __restrict__ lslab,
+    const T* __restrict__ uslab, const T* __restrict__ dinv_all, const double* __restrict__ rhs, double* __restrict__ x,
+    int accumulate, int kmax, const int* __restrict__ done, int* __restrict__ status, const int* skip,
+    T* __restrict__ vwork) {
+  if (skip && *skip) return;
+  const int sid = list[blockIdx.x];
+  if (done && done[sid]) return;
+  const SysDev S = sys[sid];
+  const int n = S.n, kl = S.kl, ku = S.ku;
+  constexpr int NB = LU_NB, HB = LU_NB / 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                  // HS mbarriers
+  T* stage0 = reinterpret_cast<T*>(smem_raw + 128);
+  const size_t stage_elems = (size_t)NB * NB + (size_t)HB * kmax;         // inverse, half slab
+  T* v = vwork + S.x_off;
+  __shared__ T yb[NB];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nblk = (n + NB - 1) / NB;
+  const int total = 4 * nblk;                                             // halves, forward then backward
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int k = 0; k < HS; ++k) mbar_init(bar + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const double* b = rhs + S.x_off;
+  for (int i = tid; i < n; i += blockDim.x) v[i] = (T)b[i];
+  __syncthreads();
+  auto issue = [&](int h) {   // thread 0 only
+    const int s = h % HS, g = h >> 1, half = h & 1;
+    const bool fwd = g < nblk;
+    const int kb = fwd ? g : 2 * nblk - 1 - g;
+    const int w = fwd ? kl : ku;
+    T* dst = stage0 + s * stage_elems;
+    const T* di = dinv_all + S.dinv_off + (int64_t)kb * 2 * NB * NB + (fwd ? 0 : NB * NB);
+    const T* sl = (fwd ? lslab + S.lslab_off : uslab + S.uslab_off) + (int64_t)kb * NB * w + (int64_t)half * HB * w;
+    const unsigned bi = half ? 0u : (unsigned)(NB * NB * sizeof(T)), bs = (unsigned)(HB * w * sizeof(T));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar + s, bi + bs);
+    if (bi) tma_bulk_g2s(dst, di, bi, bar + s);
+    if (bs) tma_bulk_g2s(dst + NB * NB, sl, bs, bar + s);
+  };
+  if (tid == 0)
+    for (int h = 0; h < HS && h < total; ++h) issue(h);
+  for (int g = 0; g < 2 * nblk; ++g) {
+    const bool fwd = g < nblk;
+    const int kb = fwd ? g : 2 * nblk - 1 - g;
+    const int k0 = kb * NB, kw = min(NB, n - k0);
+    const int w = fwd ? kl : ku;
+    for (int half = 0; half < 2; ++half) {
+      const int h = 2 * g + half, s = h % HS;
+      if (tid == 0) {
+        int it = 0;
+        while (!mbar_try_wait(bar + s, (unsigned)((h / HS) & 1))) {
+          if (++it > WAIT_LIMIT) {
+            atomicOr(status + sid, 2);
+            abort_flag = 1;
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      if (abort_flag) {
+        if (tid == 0)
+          for (int q = h + 1; q < h + HS && q < total; ++q)
+            for (int it = 0; !mbar_try_wait(bar + q % HS, (unsigned)((q / HS) & 1)) && it < WAIT_LIMIT; ++it) {
+            }
+        return;
+      }
+      const T* Dv = stage0 + s * stage_elems;
+      const T* sl = Dv + NB * NB;
+      if (half == 0) {
+        if (warp == 0) {
+          T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+          for (int p = 0; p < NB; ++p)
+            if (p < kw) acc[p & 3] += Dv[p * NB + lane] * v[k0 + p];
+          yb[lane] = lane < kw ? (acc[0] + acc[1]) + (acc[2] + acc[3]) : T(0);
+        }
+        __syncthreads();
+        if (tid < kw) v[k0 + tid] = yb[tid];
+      }
+      const int cb0 = half * HB;
+      if (fwd) {
+        const int rend = min(n, k0 + kw + kl);
+        for (int i = k0 + kw + tid; i < rend; i += blockDim.x) {
+          const int ob = i - k0 - 1;
+          T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+          for (int cc = 0; cc < HB; ++cc) {
+            const int c = cb0 + cc;
+            if (c < kw && ob - c < kl) acc[cc & 3] += sl[cc * w + (ob - c)] * yb[c];
+          }
+          v[i] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        }
+      } else {
+        const int rbeg = max(0, k0 - ku);
+        for (int i = rbeg + tid; i < k0; i += blockDim.x) {
+          const int ob = i - k0 + ku;
+          T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+          for (int cc = 0; cc < HB; ++cc) {
+            const int c = cb0 + cc;
+            if (c < kw && ob - c >= 0) acc[cc & 3] += sl[cc * w + (ob - c)] * yb[c];
+          }
+          v[i] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        }
+      }
+      __syncthreads();
+      if (tid == 0 && h + HS < total) issue(h + HS);
+    }
+  }
+  double* xo = x + S.x_off;
+  for (int i = tid; i < n; i += blockDim.x) xo[i] = accumulate ? xo[i] + (double)v[i] : (double)v[i];
+}
+
+template <typename T, int HS>
+static cudaError_t launch_solve_halves(size_t smem, const SysDev* sys, const int* list, int nsys, int kmax,
+                                       const T* lslab, const T* uslab, const T* dinv, const double* r, double* x,
+                                       int accumulate, const int* done, int* status, cudaStream_t st,
+                                       const int* skip, T* vwork) {
+  cudaError_t e = cudaFuncSetAttribute(band_solve_halves_kernel<T, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  band_solve_halves_kernel<T, HS><<<nsys, SOLVE_THREADS, smem, st>>>(sys, list, lslab, uslab, dinv, r, x, accumulate,
+                                                                     kmax, done, status, skip, vwork);
+  return cudaGetLastError();
+}
+
 template <typename T, int STAGES, bool GV>
 static cudaError_t launch_solve_variant(size_t smem, const SysDev* sys, const int* list, int nsys, int kmax,
                                         const T* lslab, const T* uslab, const T* dinv, const double* r, double* x,
@@ -1122,7 +1256,20 @@ cudaError_t launch_band_solve(const SysDev* sys, const int* list, int nsys, int 
   const size_t vec = ((size_t)n_max + 4) * sizeof(T);
   const size_t static_smem = 1024;
   count_launches(1);
-  // deepest pipeline with the vector in shared memory, else (given scratch) in global memory
+  // deepest pipeline with the vector in shared memory, else (given scratch) the vector in
+  // global memory with half-block stages, else with whole-block stages
+  if (vwork && !band_solve_fits_smem<T>(n_max, kmax)) {
+    const size_t half = ((size_t)LU_NB * LU_NB + (size_t)(LU_NB / 2) * kmax) * sizeof(T);
+    for (int hs = 3; hs >= 2; --hs) {
+      const size_t need = 128 + hs * half;
+      if (need + static_smem > (size_t)smem_max) continue;
+      if (hs == 3)
+        return launch_solve_halves<T, 3>(need, sys, list, nsys, kmax, lslab, uslab, dinv, r, x, accumulate, done,
+                                         status, st, skip, vwork);
+      return launch_solve_halves<T, 2>(need, sys, list, nsys, kmax, lslab, uslab, dinv, r, x, accumulate, done,
+                                       status, st, skip, vwork);
+    }
+  }
   for (int gv = 0; gv < 2; ++gv) {
     if (gv && !vwork) break;
     for (int stages = 3; stages >= 1; --stages) {
