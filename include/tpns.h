@@ -55,8 +55,10 @@ typedef enum {
 typedef enum {
   TPNS_FP64 = 0,       /* FP64 band LU / Cholesky */
   TPNS_FP32_IR = 1,    /* FP32 factors (FP32 FMA), FP64-residual iterative refinement */
-  TPNS_TF32_IR = 2,    /* FP32 factors whose trailing updates run on tcgen05 TF32 MMA */
-  TPNS_BF16_IR = 3     /* FP32 factors whose trailing updates run on tcgen05 BF16 MMA */
+  TPNS_TF32_IR = 2,    /* FP32 factors whose trailing (bulk) updates run on the tensor cores:
+                          mma.sync TF32 with each operand split in two TF32 parts
+                          (hi*hi + hi*lo + lo*hi, FP32 accumulation); tpns_create only */
+  TPNS_BF16_IR = 3     /* not available in this build (TPNS_EINVAL) */
 } tpns_precision;
 
 #define TPNS_MAX_COARSE_ROWS 64

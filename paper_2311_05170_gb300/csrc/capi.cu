@@ -500,7 +500,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     TRY(dalloc(ctx, &ctx->d_uslab_coarse, ctx->uslab_coarse_len));
     CK(cudaMemset(ctx->d_lslab_coarse, 0, (size_t)ctx->lslab_coarse_len * 8));
     CK(cudaMemset(ctx->d_uslab_coarse, 0, (size_t)ctx->uslab_coarse_len * 8));
-    if (ctx->prec == TPNS_FP32_IR) {
+    if (ctx->prec != TPNS_FP64) {
       TRY(dalloc(ctx, &ctx->d_band_coarse_f, ctx->band_coarse_len));
       TRY(dalloc(ctx, &ctx->d_dinv_coarse_f, ctx->dinv_coarse_len));
       TRY(dalloc(ctx, &ctx->d_lslab_coarse_f, ctx->lslab_coarse_len));
@@ -782,7 +782,7 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
     CK(launch_oseen_elem(ctx->asmargs, ctx->e_off[CF], ctx->ne_cf, ctx->d_Ke, ctx->d_Re, st, skip));
     CK(launch_seg_reduce(ctx->d_mcf_t, ctx->d_mcf_s, ctx->n_mcf, ctx->d_Ke, ctx->d_vals, st, skip));
     CK(launch_seg_reduce(ctx->d_rcf_t, ctx->d_rcf_s, ctx->n_rcf, ctx->d_Re, ctx->d_b, st, skip));
-    if (ctx->prec == TPNS_FP32_IR) {
+    if (ctx->prec != TPNS_FP64) {
       // Newton correction from FP32 band factors of the Jacobian, refined against the FP64
       // Jacobian: FP64 arithmetic is scarce on this GPU, FP64 residuals are cheap
       CK(launch_band_fill<float>(ctx->d_sys, ctx->d_list_cf, 1, ctx->d_rowof, ctx->d_colidx, ctx->d_vals,
@@ -860,7 +860,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   ph_end(ctx, PH_BAND_FILL);
   ph_begin(ctx, PH_BAND_LU);
   CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, lslab, uslab, dinv, ctx->d_flags,
-                       ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr));
+                       ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr, ctx->prec == TPNS_TF32_IR));
   CK(launch_band_dinv<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->nblk_max_osl, band, dinv, st, nullptr));
   ph_end(ctx, PH_BAND_LU);
   // a8: solves with FP64-residual iterative refinement
@@ -1239,7 +1239,7 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   *out = nullptr;
   if (!mesh || !params || !part || !data) { g_err = "NULL argument"; return TPNS_EINVAL; }
   if (!(dt > 0)) { g_err = "dt must be positive"; return TPNS_EINVAL; }
-  if (precision != TPNS_FP64 && precision != TPNS_FP32_IR) {
+  if (precision != TPNS_FP64 && precision != TPNS_FP32_IR && precision != TPNS_TF32_IR) {
     g_err = "precision not available in this build";
     return TPNS_EINVAL;
   }

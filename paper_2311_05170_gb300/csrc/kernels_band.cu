@@ -522,7 +522,83 @@ __device__ __forceinline__ void row_update(T (&acc)[W], LF lf, const T* __restri
   }
 }
 
-template <typename T, bool WIDE, int CL>
+// Tensor-core trailing update (TPNS_TF32_IR): mma.sync m16n8k8 with TF32 operands and FP32
+// accumulation; each operand is split as x = hi + lo (hi, lo TF32) and the product taken as
+// hi*hi + hi*lo + lo*hi, which keeps the update close to FP32 accuracy.
+__device__ __forceinline__ unsigned to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// A22(rows rb..rb+31, columns cs..cs+15) -= L21 U12 on the tensor cores, one warp: the tile
+// is 2 x 2 fragments of 16 x 8 (rows g, g+8 and columns 2t, 2t+1 of each, g = lane / 4,
+// t = lane % 4); L(r, k0 + q) = Ls[q kl + r - q - 1] inside the band, U12 = Uv (row-major).
+__device__ void tc_update_tile(float* __restrict__ AB, const float* __restrict__ Ls, const float* __restrict__ Uv,
+                               int k0, int kw, int R, int rb, int c0, int cw, int cs, int hcol, int kl, int ku,
+                               int ldab) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float c[2][2][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = rb + mt * 16 + g + (e >> 1) * 8, j = cs + nt * 8 + 2 * t + (e & 1), i = k0 + r;
+        c[mt][nt][e] = (r < R && j < c0 + cw && i - j <= kl && j - i <= ku)
+                           ? __ldcg(AB + (int64_t)j * ldab + (ku + i - j)) : 0.0f;
+      }
+#pragma unroll
+  for (int kk = 0; kk < LU_NB; kk += 8) {
+    unsigned ah[2][4], al[2][4], bh[2][2], bl[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = rb + mt * 16 + g + (e & 1) * 8, q = kk + t + (e >> 1) * 4, o = r - q - 1;
+        const float val = (r < R && q < kw && o >= 0 && o < kl) ? -Ls[q * kl + o] : 0.0f;
+        split_tf32(val, ah[mt][e], al[mt][e]);
+      }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float val = Uv[(kk + t + e * 4) * LU_NB + hcol + nt * 8 + g];
+        split_tf32(val, bh[nt][e], bl[nt][e]);
+      }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        mma_tf32(c[mt][nt], al[mt], bh[nt]);
+        mma_tf32(c[mt][nt], ah[mt], bl[nt]);
+        mma_tf32(c[mt][nt], ah[mt], bh[nt]);
+      }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = rb + mt * 16 + g + (e >> 1) * 8, j = cs + nt * 8 + 2 * t + (e & 1), i = k0 + r;
+        if (r < R && j < c0 + cw && i - j <= kl && j - i <= ku) AB[(int64_t)j * ldab + (ku + i - j)] = c[mt][nt][e];
+      }
+}
+
+template <typename T, bool WIDE, int CL, bool TC>
 __global__ void __launch_bounds__(lu_threads<T>(), 1)
 band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* __restrict__ band,
                T* __restrict__ lslab, T* __restrict__ uslab, T* __restrict__ dinv_all, int* __restrict__ sync_all,
@@ -715,6 +791,12 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
         form_u12<T>(Li, NB, Ub, Uv, AB, US, k0, kw, c0, cw, kl, ku, ldab);
         // A22 -= L21 U12: warp pairs share 32 rows (lane = row), each warp one half of the columns
         const int h = warp & 1, groups = nwarp / 2;
+        if constexpr (TC && sizeof(T) == 4) {
+          for (int rb = kw + (warp >> 1) * 32; rb < R; rb += groups * 32)
+            tc_update_tile(reinterpret_cast<float*>(AB), reinterpret_cast<const float*>(Ls),
+                           reinterpret_cast<const float*>(Uv), k0, kw, R, rb, c0, cw, c0 + h * HALF, h * HALF, kl, ku,
+                           ldab);
+        } else
         for (int rb = kw + (warp >> 1) * 32; rb < R; rb += groups * 32) {
           const int r = rb + lane;
           if (r < R) {
@@ -767,7 +849,7 @@ __global__ void bump_kernel(int* p) { *p = (*p % 0x7FFFF) + 1; }
 template <typename T>
 cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_max, T* band, T* lslab, T* uslab,
                            T* dinv, int* sync, int sync_stride, int* epoch, int* status, cudaStream_t st,
-                           const int* skip) {
+                           const int* skip, bool tc) {
   if (nsys == 0) return cudaSuccess;
   const size_t smem = band_lu_smem_bytes<T>(kl_max);
   int dev = 0, smem_max = 0;
@@ -776,8 +858,14 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   if (kl_max < 0 || smem > (size_t)smem_max) return cudaErrorInvalidValue;
   // panels of at most one row per thread are factored from registers
   const bool wide = LU_NB + kl_max > lu_threads<T>();
-  auto kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER> : band_lu_kernel<T, false, LU_CLUSTER>;
-  auto kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER> : band_lu_kernel<T, false, 2 * LU_CLUSTER>;
+  auto kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER, false> : band_lu_kernel<T, false, LU_CLUSTER, false>;
+  auto kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER, false> : band_lu_kernel<T, false, 2 * LU_CLUSTER, false>;
+  if constexpr (sizeof(T) == 4) {
+    if (tc) {
+      kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER, true> : band_lu_kernel<T, false, LU_CLUSTER, true>;
+      kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER, true> : band_lu_kernel<T, false, 2 * LU_CLUSTER, true>;
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(kern8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
@@ -1395,7 +1483,7 @@ cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const 
   template cudaError_t launch_band_fill<T>(const SysDev*, const int*, int, const int32_t*, const int32_t*,  \
                                            const double*, T*, int, int64_t, cudaStream_t, const int*);      \
   template cudaError_t launch_band_lu<T>(const SysDev*, const int*, int, int, T*, T*, T*, T*, int*, int, int*,\
-                                         int*, cudaStream_t, const int*);                                   \
+                                         int*, cudaStream_t, const int*, bool);                                   \
   template cudaError_t launch_band_dinv<T>(const SysDev*, const int*, int, int, const T*, T*, cudaStream_t, \
                                            const int*);                                                     \
   template cudaError_t launch_band_to_slab<T>(const SysDev*, const int*, int, const T*, T*, T*,             \

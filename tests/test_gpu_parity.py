@@ -12,7 +12,7 @@ from oracle.scheme import TwoGridOracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-8}
+TOL = {"fp64": 1e-10, "fp32": 1e-8, "tf32": 1e-8}
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +54,7 @@ def test_patch_field_exact_on_gpu(native, prec):
         assert np.abs(f[k] - ex[k]).max() < 1e-11, k
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
 def test_small_2d_parity(native, prec):
     w = W.config_small(nsteps=10)
     f, o, stats = run_pair(native, w, prec, 10)
@@ -63,7 +63,7 @@ def test_small_2d_parity(native, prec):
     assert stats["last_ir_relres_max"] <= 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
 def test_graded_full_size_parity(native, prec):
     """The bench workload at full size (130,966 fine dofs, 16 + 48 local systems of 1.4k to
     8.3k unknowns), three steps."""
