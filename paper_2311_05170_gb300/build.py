@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libtpns.so")
-UNITS = ["setup.cpp", "kernels_band.cu", "kernels_assemble.cu", "capi.cu"]
+UNITS = ["setup.cpp", "kernels_band_f32.cu", "kernels_band_f64.cu", "kernels_assemble.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -23,6 +23,7 @@ def build(verbose=False, force=False):
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = [os.path.join(SRC, u) for u in UNITS]
     deps = srcs + [os.path.join(SRC, h) for h in os.listdir(SRC) if h.endswith((".hpp", ".cuh"))]
+    deps.append(os.path.join(SRC, "kernels_band.cu"))   # included by the two kernels_band_* units
     deps.append(os.path.join(ROOT, "include", "tpns.h"))
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
         return LIB

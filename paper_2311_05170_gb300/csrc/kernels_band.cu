@@ -545,7 +545,7 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], 
 // A22(rows rb..rb+31, columns cs..cs+15) -= L21 U12 on the tensor cores, one warp: the tile
 // is 2 x 2 fragments of 16 x 8 (rows g, g+8 and columns 2t, 2t+1 of each, g = lane / 4,
 // t = lane % 4); L(r, k0 + q) = Ls[q kl + r - q - 1] inside the band, U12 = Uv (row-major).
-__device__ void tc_update_tile(float* __restrict__ AB, const float* __restrict__ Ls, const float* __restrict__ Uv,
+static __device__ void tc_update_tile(float* __restrict__ AB, const float* __restrict__ Ls, const float* __restrict__ Uv,
                                int k0, int kw, int R, int rb, int c0, int cw, int cs, int hcol, int kl, int ku,
                                int ldab) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -844,7 +844,7 @@ size_t band_lu_smem_bytes(int kl_max) {
 
 // a new tag for the next factorisation (kept on the device so that a captured graph replays
 // with fresh tags)
-__global__ void bump_kernel(int* p) { *p = (*p % 0x7FFFF) + 1; }
+static __global__ void bump_kernel(int* p) { *p = (*p % 0x7FFFF) + 1; }
 
 template <typename T>
 cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_max, T* band, T* lslab, T* uslab,
@@ -1379,6 +1379,7 @@ cudaError_t launch_band_solve(const SysDev* sys, const int* list, int nsys, int 
   return cudaErrorInvalidValue;
 }
 
+#if TPNS_BAND_PART == 1
 // ------------------------------------------------------------------------------ residual
 // r = b - A x (FP64 CSR), relative residual and refinement control.  RES_CHUNKS CTAs per
 // system each handle a slice of rows and store partial sums of ||r||^2 and ||b||^2; the last
@@ -1479,6 +1480,8 @@ cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const 
   return cudaGetLastError();
 }
 
+#endif  // TPNS_BAND_PART == 1
+
 #define TPNS_INST(T)                                                                                       \
   template cudaError_t launch_band_fill<T>(const SysDev*, const int*, int, const int32_t*, const int32_t*,  \
                                            const double*, T*, int, int64_t, cudaStream_t, const int*);      \
@@ -1496,7 +1499,13 @@ cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const 
                                             cudaStream_t, const int*, T*);                                  \
   template bool band_solve_fits_smem<T>(int, int);                                                          \
   template size_t band_lu_smem_bytes<T>(int);
+// this file is compiled once per element type (kernels_band_f32.cu, kernels_band_f64.cu)
+#if TPNS_BAND_PART == 1
 TPNS_INST(float)
+#elif TPNS_BAND_PART == 2
 TPNS_INST(double)
+#else
+#error "compile kernels_band_f32.cu or kernels_band_f64.cu"
+#endif
 
 }  // namespace tpns
