@@ -301,11 +301,12 @@ def main():
             "refused_for_budget": int(sum_over_ranks(sstats["refused_for_budget"], on, device="cuda")),
             "step_latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,
             "step_latency_ms_p99": float(np.percentile(lat, 99)) if lat.size else None,
+            "tick_ms_max_p50": max_over_ranks(sstats["tick_ms_p50"] or 0.0, on, device="cuda"),
             "dof_steps_per_s": sum_over_ranks(sum(r.dofs * r.done_steps for r in done), on, device="cuda") / wall,
             "sample": (f"first {args.serving_requests} of the 512 seeded requests (Poisson arrivals, 20/s), "
                        f"{args.serving_steps} steps each, sharded over {world} GPU(s) by estimated work, "
-                       f"HBM budget 64 GiB per GPU; latency = duration of the batched tick that advanced "
-                       f"the request; wall includes context creation"),
+                       f"HBM budget 64 GiB per GPU; step latency = device time of a request's step within "
+                       f"its batched tick (other requests running beside it); wall includes context creation"),
         }
     # ---------------------------------------------------------------- CPU baseline (oracle)
     cpu = None

@@ -111,6 +111,9 @@ typedef struct {
                                      n (kl + ku) s + ceil(n / 32) 2048 s + 24 n, s = factor
                                      element size (factor slabs, diagonal-block inverses, FP64
                                      right-hand side read and solution read + write) */
+  double last_step_ms;            /* device time of the context's last step in tpns_batch_step,
+                                     from the step's start on its stream to its end (with the
+                                     other contexts of the batch running beside it) */
 } tpns_stats;
 
 typedef struct tpns_ctx tpns_ctx;

@@ -63,6 +63,7 @@ struct tpns_ctx {
   bool own_stream = false;
   cudaGraphExec_t g_full = nullptr, g_local = nullptr;
   int64_t kernels_full = 0, kernels_local = 0;   // kernels in each captured graph
+  cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;   // bracket the context's step in tpns_batch_step
   // device
   ProbDev* d_probs = nullptr;
   int32_t *d_eprob = nullptr, *d_e6 = nullptr, *d_e3 = nullptr;
@@ -1561,30 +1562,44 @@ tpns_status tpns_batch_step(tpns_ctx** ctxs, int32_t n) {
     tpns_ctx* ctx = ctxs[i];
     ctx->err.clear();
     ctx->traj_base = -1000000000;
+    if (!ctx->ev_s0 && (cudaEventCreate(&ctx->ev_s0) != cudaSuccess || cudaEventCreate(&ctx->ev_s1) != cudaSuccess)) {
+      g_err = ctx->err = "cudaEventCreate failed";
+      return TPNS_EDEVICE;
+    }
+    // the capture of a first step records no work, so the step's start is marked after it
     bool graph = ctx->use_graph && !ctx->timing;
+    if (graph && !ctx->g_full && !capture_step(ctx, true, &ctx->g_full)) {
+      ctx->use_graph = false;
+      graph = false;
+    }
+    if (cudaEventRecord(ctx->ev_s0, ctx->stream) != cudaSuccess) {
+      g_err = ctx->err = "cudaEventRecord failed";
+      return TPNS_EDEVICE;
+    }
     if (graph) {
-      if (!ctx->g_full && !capture_step(ctx, true, &ctx->g_full)) {
-        ctx->use_graph = false;
-        graph = false;
-      }
-      if (graph && cudaGraphLaunch(ctx->g_full, ctx->stream) != cudaSuccess) {
+      if (cudaGraphLaunch(ctx->g_full, ctx->stream) != cudaSuccess) {
         g_err = ctx->err = "cudaGraphLaunch failed";
         return TPNS_EDEVICE;
       }
-      if (graph) count_launches((int)ctx->kernels_full);
-    }
-    if (!graph) {
+      count_launches((int)ctx->kernels_full);
+    } else {
       tpns_status s = enqueue_step(ctx, true);
       if (s != TPNS_OK) {
         g_err = ctx->err;
         return s;
       }
     }
+    if (cudaEventRecord(ctx->ev_s1, ctx->stream) != cudaSuccess) {
+      g_err = ctx->err = "cudaEventRecord failed";
+      return TPNS_EDEVICE;
+    }
     ctx->step += 1;
   }
   tpns_status worst = TPNS_OK;
   for (int i = 0; i < n; ++i) {
     tpns_status s = read_stats(ctxs[i]);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctxs[i]->ev_s0, ctxs[i]->ev_s1) == cudaSuccess) ctxs[i]->stats.last_step_ms = ms;
     if (s != TPNS_OK && worst == TPNS_OK) {
       worst = s;
       g_err = ctxs[i]->err;
@@ -1624,6 +1639,8 @@ void tpns_destroy(tpns_ctx* ctx) {
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   for (void* p : ctx->allocs) cudaFree(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->ev_s0) cudaEventDestroy(ctx->ev_s0);
+  if (ctx->ev_s1) cudaEventDestroy(ctx->ev_s1);
   for (auto& p : ctx->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
   for (double* p : ctx->traj) {
     (void)p;

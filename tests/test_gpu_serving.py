@@ -33,6 +33,9 @@ def test_results_equal_alone_and_in_the_mix(native):
     stats, done = run_serving(reqs, hbm_budget_bytes=8 << 30, keep_fields=True)
     assert stats["requests"] == 6 and stats["max_concurrency"] >= 2
     assert stats["step_latency_ms_p50"] is not None and stats["step_latency_ms_p99"] >= stats["step_latency_ms_p50"]
+    # a request's own step time is positive and within the tick that carried it
+    assert all(x > 0 for r in done for x in r.latencies_ms)
+    assert stats["step_latency_ms_p99"] <= stats["tick_ms_p99"] + 1.0
     for r in done:
         ref = _alone(native, r.w, r.nsteps)
         for k in ref:
