@@ -359,7 +359,10 @@ def reference_arm(args, rank):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": d["secs"] * 1e3 / d["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD}, "impl": "reference", "cpu_baseline": cpu,
+            "config": {"workload": WORKLOAD, "fine_dofs": 130966, "local_systems_per_step": 64, "replicas": 1,
+                       "parallelism": "oracle on the host cores (one thread)",
+                       "timed": "full time steps of the oracle (coarse solve, all local solves, glue)"},
+            "impl": "reference", "cpu_baseline": cpu,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
