@@ -140,6 +140,10 @@ def band_sizes(solver, n_fluid, n_porous):
     return out
 
 
+def ndofs_of(st):
+    return st["n_fine_dofs"]
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -222,6 +226,20 @@ def main():
     f = s_chk.fields()
     s_chk.close()
     rel = {k: float(np.linalg.norm(f[k] - f64[k]) / np.linalg.norm(f64[k])) for k in f}
+    # the tensor-core variants of the factorisation, same steps, error against the FP64 fields
+    variants = {}
+    for vp in ("tf32", "bf16"):
+        try:
+            sv, msv, _, _, _ = timed_hot(vp)
+            fv = sv.fields()
+            stv = sv.stats()
+            sv.close()
+            variants[vp] = {"ms_per_step": msv / K, "value": ndofs_of(stv) * K * world / (msv / 1e3),
+                            "relL2_vs_fp64_gpu_max": max(float(np.linalg.norm(fv[k] - f64[k]) / np.linalg.norm(f64[k]))
+                                                         for k in fv),
+                            "ir_iters_max": stv["last_ir_iters_max"], "ir_relres_max": stv["last_ir_relres_max"]}
+        except Exception as ex:
+            variants[vp] = {"error": str(ex)[:120]}
     solve_bytes_step = phases.pop("_solve_bytes") / K
     ph = {k: v[0] / K for k, v in phases.items()}
     phn = {k: v[1] for k, v in phases.items()}
@@ -330,6 +348,10 @@ def main():
                                 "from K further steps launched kernel by kernel"},
             "valid": valid, "relL2_vs_fp64_gpu": rel,
             "fp64_gpu": {"value": value64, "ms_per_step": ms64 / K},
+            "tensor_core_variants": {
+                "what": "trailing band-LU updates on the tensor cores (mma.sync): tf32 = TF32 with split "
+                        "operands, bf16 = plain BF16; FP32 factors, FP64-residual refinement",
+                **variants},
             "speedup_vs_fp64_gpu": value / value64,
             "roofline": roof, "kernels": kernels,
             "phases_ms_per_step": ph,

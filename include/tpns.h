@@ -58,7 +58,10 @@ typedef enum {
   TPNS_TF32_IR = 2,    /* FP32 factors whose trailing (bulk) updates run on the tensor cores:
                           mma.sync TF32 with each operand split in two TF32 parts
                           (hi*hi + hi*lo + lo*hi, FP32 accumulation); tpns_create only */
-  TPNS_BF16_IR = 3     /* not available in this build (TPNS_EINVAL) */
+  TPNS_BF16_IR = 3     /* FP32 factors whose trailing (bulk) updates run on the tensor cores in
+                          plain BF16 (mma.sync, each operand rounded once, FP32 accumulation);
+                          the refinement must win back BF16-level factor error and may stop
+                          with TPNS_ENOTCONV; tpns_create only */
 } tpns_precision;
 
 #define TPNS_MAX_COARSE_ROWS 64

@@ -861,7 +861,8 @@ static tpns_status local_step(tpns_ctx* ctx) {
   ph_end(ctx, PH_BAND_FILL);
   ph_begin(ctx, PH_BAND_LU);
   CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, lslab, uslab, dinv, ctx->d_flags,
-                       ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr, ctx->prec == TPNS_TF32_IR));
+                       ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr,
+                       ctx->prec == TPNS_TF32_IR ? 1 : ctx->prec == TPNS_BF16_IR ? 2 : 0));
   CK(launch_band_dinv<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->nblk_max_osl, band, dinv, st, nullptr));
   ph_end(ctx, PH_BAND_LU);
   // a8: solves with FP64-residual iterative refinement
@@ -1240,7 +1241,8 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   *out = nullptr;
   if (!mesh || !params || !part || !data) { g_err = "NULL argument"; return TPNS_EINVAL; }
   if (!(dt > 0)) { g_err = "dt must be positive"; return TPNS_EINVAL; }
-  if (precision != TPNS_FP64 && precision != TPNS_FP32_IR && precision != TPNS_TF32_IR) {
+  if (precision != TPNS_FP64 && precision != TPNS_FP32_IR && precision != TPNS_TF32_IR &&
+      precision != TPNS_BF16_IR) {
     g_err = "precision not available in this build";
     return TPNS_EINVAL;
   }

@@ -6,6 +6,7 @@
 // (the unpivoted LU of a band matrix stays inside the band).  Cholesky: lower band,
 // L(i, j) at band[j * ldab + i - j], ldab = kl + 1.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -598,7 +599,73 @@ static __device__ void tc_update_tile(float* __restrict__ AB, const float* __res
       }
 }
 
-template <typename T, bool WIDE, int CL, bool TC>
+// The same tile in plain BF16 (TPNS_BF16_IR): mma.sync m16n8k16 with BF16 operands (each value
+// rounded once) and FP32 accumulation; the factors then carry BF16-level error, which the
+// FP64-residual refinement has to win back.
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<unsigned*>(&v);
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+static __device__ void tc_update_tile_bf16(float* __restrict__ AB, const float* __restrict__ Ls,
+                                           const float* __restrict__ Uv, int k0, int kw, int R, int rb, int c0, int cw,
+                                           int cs, int hcol, int kl, int ku, int ldab) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float c[2][2][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = rb + mt * 16 + g + (e >> 1) * 8, j = cs + nt * 8 + 2 * t + (e & 1), i = k0 + r;
+        c[mt][nt][e] = (r < R && j < c0 + cw && i - j <= kl && j - i <= ku)
+                           ? __ldcg(AB + (int64_t)j * ldab + (ku + i - j)) : 0.0f;
+      }
+  auto lval = [&](int r, int q) -> float {
+    const int o = r - q - 1;
+    return (r < R && q < kw && o >= 0 && o < kl) ? -Ls[q * kl + o] : 0.0f;
+  };
+#pragma unroll
+  for (int kk = 0; kk < LU_NB; kk += 16) {
+    unsigned a[2][4], b[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = rb + mt * 16 + g + (e & 1) * 8, q = kk + 2 * t + (e >> 1) * 8;
+        a[mt][e] = pack_bf16(lval(r, q), lval(r, q + 1));
+      }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int q = kk + 2 * t + e * 8, col = hcol + nt * 8 + g;
+        b[nt][e] = pack_bf16(Uv[q * LU_NB + col], Uv[(q + 1) * LU_NB + col]);
+      }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) mma_bf16(c[mt][nt], a[mt], b[nt]);
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = rb + mt * 16 + g + (e >> 1) * 8, j = cs + nt * 8 + 2 * t + (e & 1), i = k0 + r;
+        if (r < R && j < c0 + cw && i - j <= kl && j - i <= ku) AB[(int64_t)j * ldab + (ku + i - j)] = c[mt][nt][e];
+      }
+}
+
+template <typename T, bool WIDE, int CL, int TC>
 __global__ void __launch_bounds__(lu_threads<T>(), 1)
 band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* __restrict__ band,
                T* __restrict__ lslab, T* __restrict__ uslab, T* __restrict__ dinv_all, int* __restrict__ sync_all,
@@ -791,11 +858,16 @@ band_lu_kernel(const SysDev* __restrict__ sys, const int* __restrict__ list, T* 
         form_u12<T>(Li, NB, Ub, Uv, AB, US, k0, kw, c0, cw, kl, ku, ldab);
         // A22 -= L21 U12: warp pairs share 32 rows (lane = row), each warp one half of the columns
         const int h = warp & 1, groups = nwarp / 2;
-        if constexpr (TC && sizeof(T) == 4) {
+        if constexpr (TC == 1 && sizeof(T) == 4) {
           for (int rb = kw + (warp >> 1) * 32; rb < R; rb += groups * 32)
             tc_update_tile(reinterpret_cast<float*>(AB), reinterpret_cast<const float*>(Ls),
                            reinterpret_cast<const float*>(Uv), k0, kw, R, rb, c0, cw, c0 + h * HALF, h * HALF, kl, ku,
                            ldab);
+        } else if constexpr (TC == 2 && sizeof(T) == 4) {
+          for (int rb = kw + (warp >> 1) * 32; rb < R; rb += groups * 32)
+            tc_update_tile_bf16(reinterpret_cast<float*>(AB), reinterpret_cast<const float*>(Ls),
+                                reinterpret_cast<const float*>(Uv), k0, kw, R, rb, c0, cw, c0 + h * HALF, h * HALF, kl,
+                                ku, ldab);
         } else
         for (int rb = kw + (warp >> 1) * 32; rb < R; rb += groups * 32) {
           const int r = rb + lane;
@@ -849,7 +921,7 @@ static __global__ void bump_kernel(int* p) { *p = (*p % 0x7FFFF) + 1; }
 template <typename T>
 cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_max, T* band, T* lslab, T* uslab,
                            T* dinv, int* sync, int sync_stride, int* epoch, int* status, cudaStream_t st,
-                           const int* skip, bool tc) {
+                           const int* skip, int tc) {
   if (nsys == 0) return cudaSuccess;
   const size_t smem = band_lu_smem_bytes<T>(kl_max);
   int dev = 0, smem_max = 0;
@@ -858,12 +930,15 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   if (kl_max < 0 || smem > (size_t)smem_max) return cudaErrorInvalidValue;
   // panels of at most one row per thread are factored from registers
   const bool wide = LU_NB + kl_max > lu_threads<T>();
-  auto kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER, false> : band_lu_kernel<T, false, LU_CLUSTER, false>;
-  auto kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER, false> : band_lu_kernel<T, false, 2 * LU_CLUSTER, false>;
+  auto kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER, 0> : band_lu_kernel<T, false, LU_CLUSTER, 0>;
+  auto kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER, 0> : band_lu_kernel<T, false, 2 * LU_CLUSTER, 0>;
   if constexpr (sizeof(T) == 4) {
-    if (tc) {
-      kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER, true> : band_lu_kernel<T, false, LU_CLUSTER, true>;
-      kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER, true> : band_lu_kernel<T, false, 2 * LU_CLUSTER, true>;
+    if (tc == 1) {
+      kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER, 1> : band_lu_kernel<T, false, LU_CLUSTER, 1>;
+      kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER, 1> : band_lu_kernel<T, false, 2 * LU_CLUSTER, 1>;
+    } else if (tc == 2) {
+      kern8 = wide ? band_lu_kernel<T, true, LU_CLUSTER, 2> : band_lu_kernel<T, false, LU_CLUSTER, 2>;
+      kern16 = wide ? band_lu_kernel<T, true, 2 * LU_CLUSTER, 2> : band_lu_kernel<T, false, 2 * LU_CLUSTER, 2>;
     }
   }
   cudaError_t e = cudaFuncSetAttribute(kern8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1486,7 +1561,7 @@ cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const 
   template cudaError_t launch_band_fill<T>(const SysDev*, const int*, int, const int32_t*, const int32_t*,  \
                                            const double*, T*, int, int64_t, cudaStream_t, const int*);      \
   template cudaError_t launch_band_lu<T>(const SysDev*, const int*, int, int, T*, T*, T*, T*, int*, int, int*,\
-                                         int*, cudaStream_t, const int*, bool);                                   \
+                                         int*, cudaStream_t, const int*, int);                                   \
   template cudaError_t launch_band_dinv<T>(const SysDev*, const int*, int, int, const T*, T*, cudaStream_t, \
                                            const int*);                                                     \
   template cudaError_t launch_band_to_slab<T>(const SysDev*, const int*, int, const T*, T*, T*,             \

@@ -12,7 +12,7 @@ from oracle.scheme import TwoGridOracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-8, "tf32": 1e-8}
+TOL = {"fp64": 1e-10, "fp32": 1e-8, "tf32": 1e-8, "bf16": 1e-8}
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +54,7 @@ def test_patch_field_exact_on_gpu(native, prec):
         assert np.abs(f[k] - ex[k]).max() < 1e-11, k
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 def test_small_2d_parity(native, prec):
     w = W.config_small(nsteps=10)
     f, o, stats = run_pair(native, w, prec, 10)
