@@ -117,6 +117,9 @@ typedef struct {
   double last_step_ms;            /* device time of the context's last step in tpns_batch_step,
                                      from the step's start on its stream to its end (with the
                                      other contexts of the batch running beside it) */
+  int64_t lu_cluster_ctas;        /* CTAs per cluster of the Oseen band LU: 8, or 16 where all
+                                     clusters fit the device and tpns_create measured 16 faster
+                                     on the context's own systems */
 } tpns_stats;
 
 typedef struct tpns_ctx tpns_ctx;

@@ -64,6 +64,7 @@ struct tpns_ctx {
   cudaGraphExec_t g_full = nullptr, g_local = nullptr;
   int64_t kernels_full = 0, kernels_local = 0;   // kernels in each captured graph
   cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;   // bracket the context's step in tpns_batch_step
+  int lu_cl = 0;                                   // CTAs per cluster of the Oseen LU, picked at create
   // device
   ProbDev* d_probs = nullptr;
   int32_t *d_eprob = nullptr, *d_e6 = nullptr, *d_e3 = nullptr;
@@ -862,7 +863,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   ph_begin(ctx, PH_BAND_LU);
   CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, lslab, uslab, dinv, ctx->d_flags,
                        ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr,
-                       ctx->prec == TPNS_TF32_IR ? 1 : ctx->prec == TPNS_BF16_IR ? 2 : 0));
+                       ctx->prec == TPNS_TF32_IR ? 1 : ctx->prec == TPNS_BF16_IR ? 2 : 0, ctx->lu_cl));
   CK(launch_band_dinv<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->nblk_max_osl, band, dinv, st, nullptr));
   ph_end(ctx, PH_BAND_LU);
   // a8: solves with FP64-residual iterative refinement
@@ -1023,6 +1024,54 @@ static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
     ctx->step += 1;
   }
   return read_stats(ctx);
+}
+
+// Launch tuning of the Oseen band LU on the context's own systems: where both 8- and 16-CTA
+// clusters can be placed, factor the (zeroed) bands with each twice and keep the faster;
+// the work of an unpivoted band LU does not depend on the values.  Runs before the Darcy
+// factors exist; it writes only in-band slab entries (those outside the matrix stay zero) and
+// the status words are reset afterwards.
+template <typename T>
+static tpns_status tune_lu(tpns_ctx* ctx) {
+  const int nosl = (int)ctx->list_osl.size();
+  ctx->lu_cl = LU_CLUSTER;
+  if (nosl == 0) return TPNS_OK;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nosl * 2 * LU_CLUSTER > nsm) return TPNS_OK;   // only 8-CTA clusters fit at once
+  cudaStream_t st = ctx->stream;
+  T* band = reinterpret_cast<T*>(ctx->d_band_local);
+  const int tc = ctx->prec == TPNS_TF32_IR ? 1 : ctx->prec == TPNS_BF16_IR ? 2 : 0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int pick = LU_CLUSTER;
+  for (int cl : {LU_CLUSTER, 2 * LU_CLUSTER}) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaMemsetAsync(band, 0, (size_t)ctx->band_local_len * sizeof(T), st));
+      CK(cudaEventRecord(e0, st));
+      CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band,
+                           reinterpret_cast<T*>(ctx->d_lslab_local), reinterpret_cast<T*>(ctx->d_uslab_local),
+                           reinterpret_cast<T*>(ctx->d_dinv_local), ctx->d_flags, ctx->flags_stride, ctx->d_epoch,
+                           ctx->d_status, st, nullptr, tc, cl));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    if (ms < best) {
+      best = ms;
+      pick = cl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->lu_cl = pick;
+  CK(cudaMemsetAsync(ctx->d_status, 0, ctx->nsys * sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  return TPNS_OK;
 }
 
 static tpns_status setup_factors(tpns_ctx* ctx) {
@@ -1271,6 +1320,9 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   P.dt = dt;
   P.mms = data->mms_id;
   tpns_status s = build_ctx(ctx, *mesh, *part, hbm_budget_bytes);
+  // the tuning runs before the Darcy factors are formed: it overwrites the local bands, and
+  // setup_factors then writes the Darcy bands, slabs and inverses from scratch
+  if (s == TPNS_OK) s = ctx->prec == TPNS_FP64 ? tune_lu<double>(ctx) : tune_lu<float>(ctx);
   if (s == TPNS_OK) s = setup_factors(ctx);
   if (s != TPNS_OK) {
     g_err = ctx->err;
@@ -1281,6 +1333,7 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   ctx->stats.n_local_systems = (int64_t)ctx->list_local.size();
   ctx->stats.device_bytes = (int64_t)ctx->bytes;
   ctx->stats.band_lu_flops = ctx->lu_flops_step;
+  ctx->stats.lu_cluster_ctas = ctx->lu_cl;
   *out = ctx;
   return TPNS_OK;
 }

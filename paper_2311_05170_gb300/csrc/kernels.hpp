@@ -28,8 +28,9 @@ template <typename T>
 // epoch: device counter, bumped before the factorisation starts
 cudaError_t launch_band_lu(const SysDev* sys, const int* sys_list, int nsys, int kl_max, T* band, T* lslab,
                            T* uslab, T* dinv, int* sync, int sync_stride, int* epoch, int* status, cudaStream_t st,
-                           const int* skip, int tc = 0);   // tc (FP32 bands): trailing updates on the tensor
-                                                           // cores, 1 = TF32 split operands, 2 = plain BF16
+                           const int* skip, int tc = 0, int cl_force = 0);
+// tc (FP32 bands): trailing updates on the tensor cores, 1 = TF32 split operands, 2 = plain BF16;
+// cl_force: CTAs per cluster (8 or 16, 16 only where all clusters fit; 0 = by band width)
 template <typename T>
 cudaError_t launch_band_dinv(const SysDev* sys, const int* sys_list, int nsys, int nblk_max, const T* band,
                              T* dinv, cudaStream_t st, const int* skip);

@@ -921,7 +921,7 @@ static __global__ void bump_kernel(int* p) { *p = (*p % 0x7FFFF) + 1; }
 template <typename T>
 cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_max, T* band, T* lslab, T* uslab,
                            T* dinv, int* sync, int sync_stride, int* epoch, int* status, cudaStream_t st,
-                           const int* skip, int tc) {
+                           const int* skip, int tc, int cl_force) {
   if (nsys == 0) return cudaSuccess;
   const size_t smem = band_lu_smem_bytes<T>(kl_max);
   int dev = 0, smem_max = 0;
@@ -951,11 +951,12 @@ cudaError_t launch_band_lu(const SysDev* sys, const int* list, int nsys, int kl_
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  // very wide bands: 16-CTA clusters (15 CTAs on the trailing updates) when all of them fit
-  // on the device at once and it can place them, else 8
+  // very wide bands (or cl_force = 16): 16-CTA clusters (15 CTAs on the trailing updates)
+  // when all of them fit on the device at once and it can place them, else 8
   int cl = LU_CLUSTER, nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (kl_max > LU_WIDE_CLUSTER_KL && nsys * 2 * LU_CLUSTER <= nsm &&
+  const bool want16 = cl_force == 2 * LU_CLUSTER || (cl_force == 0 && kl_max > LU_WIDE_CLUSTER_KL);
+  if (want16 && nsys * 2 * LU_CLUSTER <= nsm &&
       cudaFuncSetAttribute(kern16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
       cudaFuncSetAttribute(kern16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     int nclusters = 0;
@@ -1561,7 +1562,7 @@ cudaError_t launch_residual(const SysDev* sys, const int* list, int nsys, const 
   template cudaError_t launch_band_fill<T>(const SysDev*, const int*, int, const int32_t*, const int32_t*,  \
                                            const double*, T*, int, int64_t, cudaStream_t, const int*);      \
   template cudaError_t launch_band_lu<T>(const SysDev*, const int*, int, int, T*, T*, T*, T*, int*, int, int*,\
-                                         int*, cudaStream_t, const int*, int);                                   \
+                                         int*, cudaStream_t, const int*, int, int);                                   \
   template cudaError_t launch_band_dinv<T>(const SysDev*, const int*, int, int, const T*, T*, cudaStream_t, \
                                            const int*);                                                     \
   template cudaError_t launch_band_to_slab<T>(const SysDev*, const int*, int, const T*, T*, T*,             \

@@ -39,7 +39,8 @@ class Stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("last_ir_iters_max", C.c_int32), ("last_newton_iters", C.c_int32),
                 ("last_ir_relres_max", C.c_double), ("n_fine_dofs", C.c_int64), ("n_local_systems", C.c_int64),
                 ("device_bytes", C.c_int64), ("band_lu_flops", C.c_double), ("h2d_bytes", C.c_int64),
-                ("last_ir_solves", C.c_int64), ("last_solve_bytes", C.c_double), ("last_step_ms", C.c_double)]
+                ("last_ir_solves", C.c_int64), ("last_solve_bytes", C.c_double), ("last_step_ms", C.c_double),
+                ("lu_cluster_ctas", C.c_int64)]
 
 
 class TpnsError(RuntimeError):

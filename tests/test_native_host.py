@@ -163,7 +163,18 @@ def test_invalid_arguments_are_status_codes(native):
     s = native.Solver(w, host_only=True)
     assert lib.tpns_step(s.ctx, 1) == native.TPNS_EINVAL
     assert lib.tpns_set_timing(s.ctx, 1) == native.TPNS_EINVAL
+    # a batched step with a host-only context (or a NULL one, or a negative count) is refused
+    # before anything is enqueued
+    arr = (C.c_void_p * 2)(s.ctx, None)
+    assert lib.tpns_batch_step(arr, 1) == native.TPNS_EINVAL
+    assert lib.tpns_batch_step(arr, 2) == native.TPNS_EINVAL
+    assert lib.tpns_batch_step(arr, -1) == native.TPNS_EINVAL
+    assert lib.tpns_batch_step(None, 1) == native.TPNS_EINVAL
     s.close()
+    # the precisions outside the enum are refused
+    md, pr, pd, dd = native.descriptors(w)
+    st = lib.tpns_create(C.byref(md), C.byref(pr), C.byref(pd), C.byref(dd), 0.01, 9, 0, None, C.byref(ctx))
+    assert st == native.TPNS_EINVAL
 
 
 def test_budget_refusal_before_any_allocation(native):
