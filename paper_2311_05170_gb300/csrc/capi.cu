@@ -453,6 +453,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(dalloc(ctx, &ctx->d_vals, ctx->vals_tot));
   TRY(dalloc(ctx, &ctx->d_b, ctx->xvec_tot));
   TRY(dalloc(ctx, &ctx->d_x, ctx->xvec_tot));
+  CK(cudaMemset(ctx->d_x, 0, (size_t)ctx->xvec_tot * 8));   // the first step's initial local iterates
   TRY(dalloc(ctx, &ctx->d_r, ctx->xvec_tot));
   TRY(dalloc(ctx, &ctx->d_rel, ctx->nsys));
   TRY(dalloc(ctx, &ctx->d_relprev, ctx->nsys));
@@ -870,14 +871,16 @@ static tpns_status local_step(tpns_ctx* ctx) {
   const bool fp64 = ctx->prec == TPNS_FP64;
   const int maxit = fp64 ? 2 : 12;
   const double tol = fp64 ? 1e-14 : 1e-13;
+  // the refinement starts from the previous step's local solutions (still in x): the local
+  // problems change by O(dt) from one step to the next, so the first residual is already small
   ph_begin(ctx, PH_RESIDUAL);
   CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
-                     ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial, ctx->d_ticket, tol, 1, st,
+                     ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial, ctx->d_ticket, tol, 2, st,
                      nullptr));
   ph_end(ctx, PH_RESIDUAL);
   ph_begin(ctx, PH_SOLVE);
   CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, lslab, uslab, dinv,
-                          ctx->d_b, ctx->d_x, 0, nullptr, ctx->d_status, st, nullptr, vwork));
+                          ctx->d_r, ctx->d_x, 1, ctx->d_done, ctx->d_status, st, nullptr, vwork));
   ph_end(ctx, PH_SOLVE);
   for (int it = 0; it < maxit; ++it) {
     ph_begin(ctx, PH_RESIDUAL);

@@ -56,7 +56,8 @@ bool band_solve_fits_smem(int n_max, int kmax);
 // dynamic shared memory of the LU kernel for a band of kl_max sub-diagonals
 template <typename T>
 size_t band_lu_smem_bytes(int kl_max);
-// r = b - A x in FP64, convergence bookkeeping (relative residual <= tol, or stagnation)
+// r = b - A x in FP64, convergence bookkeeping (relative residual <= tol, or stagnation);
+// first: 0 = a refinement step, 1 = start from x = 0 (r = b), 2 = start from the given x
 // partial: nsys * RES_CHUNKS * 2 doubles; ticket: nsys ints, zero before the first call
 cudaError_t launch_residual(const SysDev* sys, const int* sys_list, int nsys, const int32_t* rowptr,
                             const int32_t* colidx, const double* vals, const double* b,

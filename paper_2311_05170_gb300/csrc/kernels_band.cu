@@ -1489,7 +1489,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const SysDev* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = r0 + warp; i < r1; i += nw) {
     double acc = 0.0;
-    if (!first)
+    if (first != 1)
       for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) acc += va[k] * xx[ci[k]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -1532,10 +1532,12 @@ __global__ void __launch_bounds__(256) residual_kernel(const SysDev* __restrict_
   const double nb = sqrt(tb);
   const double relres = nb > 0 ? sqrt(tr) / nb : 0.0;
   if (first) {
-    done[sid] = (nb == 0.0) ? 1 : 0;
+    // first == 1: x = 0, r = b; first == 2: r = b - A x for the caller's initial x, which may
+    // already be converged
     iters[sid] = 0;
     rel_prev[sid] = 1.0;
-    rel[sid] = nb == 0.0 ? 0.0 : 1.0;
+    rel[sid] = nb == 0.0 ? 0.0 : (first == 2 ? relres : 1.0);
+    done[sid] = (nb == 0.0 || (first == 2 && relres <= tol)) ? 1 : 0;
   } else {
     iters[sid] += 1;
     const double prev = rel[sid];
