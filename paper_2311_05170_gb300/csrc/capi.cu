@@ -115,6 +115,7 @@ struct tpns_ctx {
   double *d_gc_w = nullptr, *d_gp_w = nullptr, *d_gv_w = nullptr;
   double* d_tnow = nullptr;
   int64_t* d_step = nullptr;
+  double* d_xprev = nullptr;
   int *d_newton_done = nullptr, *d_newton_iters = nullptr;
   // coarse trajectory for tpns_local_step
   std::vector<double*> traj;          // per stored step: uc, pc, pd (concatenated)
@@ -453,6 +454,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(dalloc(ctx, &ctx->d_vals, ctx->vals_tot));
   TRY(dalloc(ctx, &ctx->d_b, ctx->xvec_tot));
   TRY(dalloc(ctx, &ctx->d_x, ctx->xvec_tot));
+  TRY(dalloc(ctx, &ctx->d_xprev, ctx->xvec_tot));
+  CK(cudaMemset(ctx->d_xprev, 0, (size_t)ctx->xvec_tot * 8));
   CK(cudaMemset(ctx->d_x, 0, (size_t)ctx->xvec_tot * 8));   // the first step's initial local iterates
   TRY(dalloc(ctx, &ctx->d_r, ctx->xvec_tot));
   TRY(dalloc(ctx, &ctx->d_rel, ctx->nsys));
@@ -871,9 +874,11 @@ static tpns_status local_step(tpns_ctx* ctx) {
   const bool fp64 = ctx->prec == TPNS_FP64;
   const int maxit = fp64 ? 2 : 12;
   const double tol = fp64 ? 1e-14 : 1e-13;
-  // the refinement starts from the previous step's local solutions (still in x): the local
-  // problems change by O(dt) from one step to the next, so the first residual is already small
+  // the refinement starts from a prediction of the local solutions from the last two steps
+  // (2 x^n - x^{n-1}; x^n alone at the second step): the local problems change smoothly in
+  // time, so the first residual is already small (and often one refinement pass is saved)
   ph_begin(ctx, PH_RESIDUAL);
+  CK(launch_predict(ctx->d_x, ctx->d_xprev, ctx->xvec_tot, ctx->d_step, st));
   CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
                      ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial, ctx->d_ticket, tol, 2, st,
                      nullptr));

@@ -114,6 +114,8 @@ cudaError_t launch_glue(const GlueArgs& g, cudaStream_t st);
 cudaError_t launch_newton_update(const ProbDev* prob, const int32_t* gnode, const int32_t* vloc,
                                  int nn, int nvl, double* u, double* p, int* done, int* iters,
                                  cudaStream_t st);
+// x <- 2 x - xprev once *step >= 2 (else x unchanged), xprev <- the old x: initial local iterates
+cudaError_t launch_predict(double* x, double* xprev, int64_t n, const int64_t* step, cudaStream_t st);
 cudaError_t launch_set_time(double* tnow, int64_t* step, double dt, int advance, cudaStream_t st);
 
 }  // namespace tpns

@@ -600,6 +600,24 @@ cudaError_t launch_newton_update(const ProbDev* prob, const int32_t* gnode, cons
   return cudaGetLastError();
 }
 
+// Second-order prediction of the local iterates from the last two steps' solutions:
+// x <- 2 x - x_prev once two steps are done (x unchanged before), x_prev <- the old x.
+__global__ void predict_kernel(double* __restrict__ x, double* __restrict__ xprev, int64_t n,
+                               const int64_t* __restrict__ step) {
+  const bool extrap = *step >= 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = x[i];
+    if (extrap) x[i] = 2.0 * t - xprev[i];
+    xprev[i] = t;
+  }
+}
+
+cudaError_t launch_predict(double* x, double* xprev, int64_t n, const int64_t* step, cudaStream_t st) {
+  count_launches(1);
+  predict_kernel<<<148, 256, 0, st>>>(x, xprev, n, step);
+  return cudaGetLastError();
+}
+
 __global__ void set_time_kernel(double* tnow, int64_t* step, double dt, int advance) {
   if (advance) *step += 1;
   *tnow = (double)(*step + 1) * dt;
