@@ -1485,19 +1485,24 @@ __global__ void __launch_bounds__(256) residual_kernel(const SysDev* __restrict_
   const int chunk = (S.n + RES_CHUNKS - 1) / RES_CHUNKS;
   const int r0 = blockIdx.x * chunk, r1 = min(S.n, r0 + chunk);
   double sr = 0, sb = 0;
-  // one warp per row: lanes stride over the row's entries
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = r0 + warp; i < r1; i += nw) {
+  // four lanes per row (rows hold 10 to 50 entries), eight rows per warp at a time, so that
+  // each warp keeps eight rows' dependent loads (row pointers, entries, x) in flight
+  const int sl = threadIdx.x & 3, slot = threadIdx.x >> 2, per_pass = blockDim.x >> 2;
+  for (int i0 = r0; i0 < r1; i0 += per_pass) {
+    const int i = i0 + slot;
     double acc = 0.0;
-    if (first != 1)
-      for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) acc += va[k] * xx[ci[k]];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const double ri = bb[i] - acc;
+    if (i < r1 && first != 1) {
+      const int k1 = rp[i + 1];
+#pragma unroll 4
+      for (int k = rp[i] + sl; k < k1; k += 4) acc += va[k] * xx[ci[k]];
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (sl == 0 && i < r1) {
+      const double bi = bb[i], ri = bi - acc;
       rr[i] = ri;
       sr += ri * ri;
-      sb += bb[i] * bb[i];
+      sb += bi * bi;
     }
   }
   __shared__ double red[2][256];
