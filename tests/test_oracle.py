@@ -1,7 +1,9 @@
 """Pins of the CPU oracle against facts fixed by the paper and by mathematics
 (quadrature exactness, element invariants, the strong form of Sec. 2, exact reproduction
 of P2/P1 fields, H = h, a brute-force global Newton step, closed-form interface sums,
-discrete mass balance, and the convergence rates of Theorem 5.4 / Table T1)."""
+discrete mass balance, and the convergence rates of Theorem 5.4 / Table T1), and checks
+that planted mistakes in the oracle (a dropped or transposed convection term, a flipped
+coupling sign, a wrong exchange coefficient) break the pins meant to catch them."""
 import json
 import math
 import os
@@ -168,10 +170,9 @@ def test_mesh_counts_and_nesting():
 
 
 # ------------------------------------------------------------------ exact reproduction
-@pytest.mark.parametrize("graded", [False, True])
-def test_patch_field_reproduced_exactly(graded):
-    """A steady field with P2 velocity, P1 pressure and P2 Darcy pressures is reproduced
-    by Algorithm 3 at every step (backward Euler and all lagging are exact for it)."""
+def _patch_deviation(graded):
+    """Largest deviation, per field, of Algorithm 3's fine fields from a steady field with P2
+    velocity, P1 pressure and P2 Darcy pressures after three steps."""
     w = W.config_patch(nx_coarse=2, r=2, nsub=(2, 2), nsteps=3)
     if graded:
         w.nx_coarse, w.ny_coarse, w.fine_per_coarse_x = 4, 4, 2
@@ -179,8 +180,15 @@ def test_patch_field_reproduced_exactly(graded):
     o = TwoGridOracle(w)
     o.run(3)
     ex = o.exact_fine()
-    for k in o.fine:
-        assert np.abs(o.fine[k] - ex[k]).max() < 1e-11, k
+    return {k: float(np.abs(o.fine[k] - ex[k]).max()) for k in o.fine}
+
+
+@pytest.mark.parametrize("graded", [False, True])
+def test_patch_field_reproduced_exactly(graded):
+    """The steady P2/P1 field is reproduced by Algorithm 3 at every step (backward Euler and
+    all lagging are exact for it)."""
+    for k, d in _patch_deviation(graded).items():
+        assert d < 1e-11, k
 
 
 def test_H_equals_h_gives_zero_correction():
@@ -193,11 +201,9 @@ def test_H_equals_h_gives_zero_correction():
 
 
 # ------------------------------------------------------------------ brute force
-def test_single_subdomain_equals_global_newton_step():
-    """With one subdomain per region, u_H + e is one Newton step of the global fine
-    backward-Euler problem about the coarse solution (coarse Gamma data).  The Jacobian
-    is formed by central differences of the residual (exact for a quadratic residual) and
-    the step solved densely with numpy.linalg.solve."""
+def _newton_step_deviation():
+    """Largest deviations (velocity, pressure, Darcy pressures) of the oracle's step from one
+    Newton step of the global fine backward-Euler problem (see the test below)."""
     w = W.config_uniform(2, 2, nsub=(1, 1), overlap=1, nsteps=1, dt=0.05)
     o = TwoGridOracle(w)
     prev = dict(o.fine)
@@ -232,9 +238,8 @@ def test_single_subdomain_equals_global_newton_step():
     x[fixed] += dB
     x[free] += np.linalg.solve(J[np.ix_(free, free)], -F(x0)[free] - J[np.ix_(free, fixed)] @ dB)
     u_bf = x[:2 * nn].reshape(nn, 2)
-    assert np.abs(u_bf[:, 0] - o.fine["ux"]).max() < 1e-10
-    assert np.abs(u_bf[:, 1] - o.fine["uy"]).max() < 1e-10
-    assert np.abs(x[2 * nn:] - o.fine["p"]).max() < 1e-9
+    du = max(np.abs(u_bf[:, 0] - o.fine["ux"]).max(), np.abs(u_bf[:, 1] - o.fine["uy"]).max())
+    dpr = np.abs(x[2 * nn:] - o.fine["p"]).max()
     # Darcy: the fine backward-Euler step with partners lagged at the fine state
     Rp = region_whole(o.mph, "p")
     Op = Ops(Rp, o.prm, o.dt)
@@ -248,6 +253,7 @@ def test_single_subdomain_equals_global_newton_step():
     ucn[o.gam_p_h] = -(o.Pc2 @ uH0[:, 1])[o.gam_c_h]
     dp = o._region_dirichlet(o.mph, "p")
     freep = np.setdiff1d(np.arange(o.mph.nn), dp)
+    dd = 0.0
     for i, key in enumerate(("pF", "pf", "pm")):
         A = Op.darcy_matrix(i).toarray()
         b = Op.darcy_load(m.q(i, Rp.xq[..., 0], Rp.xq[..., 1], t)) + prm.phiC[i] / o.dt * Mf @ pn[i]
@@ -259,7 +265,55 @@ def test_single_subdomain_equals_global_newton_step():
         x = np.zeros(o.mph.nn)
         x[dp] = m.pd(i, o.mph.node[dp, 0], o.mph.node[dp, 1], t)
         x[freep] = np.linalg.solve(A[np.ix_(freep, freep)], b[freep] - A[np.ix_(freep, dp)] @ x[dp])
-        assert np.abs(x - o.fine[key]).max() < 1e-11, key
+        dd = max(dd, np.abs(x - o.fine[key]).max())
+    return du, dpr, dd
+
+
+def test_single_subdomain_equals_global_newton_step():
+    """With one subdomain per region, u_H + e is one Newton step of the global fine
+    backward-Euler problem about the coarse solution (coarse Gamma data).  The Jacobian
+    is formed by central differences of the residual (exact for a quadratic residual) and
+    the step solved densely with numpy.linalg.solve."""
+    du, dp, dd = _newton_step_deviation()
+    assert du < 1e-10 and dp < 1e-9 and dd < 1e-11
+
+
+# ------------------------------------------------------------------ planted mistakes
+# Each test plants one plausible mistake in the oracle (on the CPU, for this test only) and
+# checks that the pin meant to guard against it no longer holds.
+@pytest.mark.parametrize("mistake", ["drop b_N(e, w, v)", "sign of b(v, delta)", "transposed grad w"])
+def test_newton_pin_catches_planted_operator_mistakes(monkeypatch, mistake):
+    good = fe.oseen_blocks
+
+    def planted(W_, G, GP, w, Gw, dt, prm):
+        if mistake == "drop b_N(e, w, v)":
+            return good(W_, G, GP, w, np.zeros_like(Gw), dt, prm)
+        if mistake == "transposed grad w":
+            return good(W_, G, GP, w, np.swapaxes(Gw, 2, 3), dt, prm)
+        Kvv, Kvp, Kpv = good(W_, G, GP, w, Gw, dt, prm)
+        return Kvv, -Kvp, Kpv
+
+    monkeypatch.setattr(fe, "oseen_blocks", planted)
+    try:
+        du, dp, _ = _newton_step_deviation()
+    except (ArithmeticError, np.linalg.LinAlgError, RuntimeError):
+        return                                   # the scheme broke down: caught as well
+    assert max(du, dp) > 1e-6
+
+
+def test_patch_pin_catches_planted_exchange_coefficient(monkeypatch):
+    """Dropping the sigma* k_f / mu part of the fracture pressure's exchange coefficient
+    (the coefficient c_f of the second Darcy equation)."""
+    good = Ops.darcy_coeffs
+
+    def planted(self):
+        c = good(self)
+        p = self.prm
+        c[1] = (c[1][0] - p.sigma_star * p.k[1] / p.mu, c[1][1])
+        return c
+
+    monkeypatch.setattr(Ops, "darcy_coeffs", planted)
+    assert max(_patch_deviation(False).values()) > 1e-6
 
 
 # ------------------------------------------------------------------ closed-form interface sums
