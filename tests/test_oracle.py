@@ -3,7 +3,8 @@
 of P2/P1 fields, H = h, a brute-force global Newton step, closed-form interface sums,
 discrete mass balance, and the convergence rates of Theorem 5.4 / Table T1), and checks
 that planted mistakes in the oracle (a dropped or transposed convection term, a flipped
-coupling sign, a wrong exchange coefficient) break the pins meant to catch them."""
+coupling sign, a wrong exchange coefficient, unnormalised glue weights) break the pins meant
+to catch them."""
 import json
 import math
 import os
@@ -198,6 +199,38 @@ def test_H_equals_h_gives_zero_correction():
     assert max(np.abs(e).max() for e in o.ec) < 1e-12
     assert max(np.abs(e).max() for e in o.ep) < 1e-12
     assert max(np.abs(d).max() for d in o.dc) < 1e-11
+
+
+# ------------------------------------------------------------------ glue (Step 4)
+def _glue_deviation():
+    """Corrections that all restrict one fine field g (velocity, pressure and the three Darcy
+    pressures) must glue to I_h u_H + g: the weights form a partition of unity over the D_j
+    covering each node (4 x 2 fluid and porous subdomains, overlapping)."""
+    w = W.config_uniform(4, 2, nsub=(4, 2), overlap=3, nsteps=1)
+    o = TwoGridOracle(w)
+    rng = np.random.default_rng(0)
+    gu = rng.standard_normal((o.mch.nn, 2))
+    gp = rng.standard_normal(o.mch.nv)
+    gd = rng.standard_normal((3, o.mph.nn))
+    o.ec = [gu[s.gnode] for (s, _) in o.sub_c]
+    o.dc = [gp[s.gvert] for (s, _) in o.sub_c]
+    o.ep = [gd[:, s.gnode] for (s, _) in o.sub_p]
+    f = o.glue()
+    dev = [np.abs(f["ux"] - o.Pc2 @ o.uH[:, 0] - gu[:, 0]).max(),
+           np.abs(f["uy"] - o.Pc2 @ o.uH[:, 1] - gu[:, 1]).max(),
+           np.abs(f["p"] - o.Pc1 @ o.pH - gp).max()]
+    dev += [np.abs(f[k] - o.Pp2 @ o.pdH[i] - gd[i]).max() for i, k in enumerate(("pF", "pf", "pm"))]
+    return max(dev)
+
+
+def test_glue_is_a_partition_of_unity():
+    assert _glue_deviation() < 1e-14
+
+
+def test_glue_pin_catches_planted_unnormalised_weights(monkeypatch):
+    """Weights of 1 on every D_j instead of 1 / (number of D_j holding the node)."""
+    monkeypatch.setattr(TwoGridOracle, "_pou", staticmethod(lambda subs, nn: np.ones(nn)))
+    assert _glue_deviation() > 0.1
 
 
 # ------------------------------------------------------------------ brute force
