@@ -3,8 +3,8 @@
 of P2/P1 fields, H = h, a brute-force global Newton step, closed-form interface sums,
 discrete mass balance, and the convergence rates of Theorem 5.4 / Table T1), and checks
 that planted mistakes in the oracle (a dropped or transposed convection term, a flipped
-coupling sign, a wrong exchange coefficient, unnormalised glue weights) break the pins meant
-to catch them."""
+coupling sign, a wrong exchange coefficient, unnormalised glue weights, a misordered P2
+basis in the prolongation) break the pins meant to catch them."""
 import json
 import math
 import os
@@ -199,6 +199,47 @@ def test_H_equals_h_gives_zero_correction():
     assert max(np.abs(e).max() for e in o.ec) < 1e-12
     assert max(np.abs(e).max() for e in o.ep) < 1e-12
     assert max(np.abs(d).max() for d in o.dc) < 1e-11
+
+
+# ------------------------------------------------------------------ prolongation (Step 3 data)
+def _prolongation_deviation(graded):
+    """Nested meshes: the fine interpolant of a coarse P2 (P1) function is that function, so
+    prolongating the coarse nodal values of a quadratic (linear) polynomial must give its
+    values at the fine nodes (vertices) exactly."""
+    from oracle.scheme import prolongation
+    w = W.config_graded() if graded else W.config_uniform(4, 2, nsub=(2, 2))
+    b = region_breaks(w)
+    dev = 0.0
+    for reg in ("c", "p"):
+        mH, mh = Mesh2D(b["xs_H"], b[reg]["ys_H"]), Mesh2D(b["xs_h"], b[reg]["ys_h"])
+
+        def q(x, y):
+            return 0.3 + 1.7 * x - 0.4 * y + 2.1 * x * x - 1.3 * x * y + 0.9 * y * y
+
+        def l(x, y):
+            return 0.3 + 1.7 * x - 0.4 * y
+
+        P2, P1 = prolongation(mH, mh, "p2"), prolongation(mH, mh, "p1")
+        dev = max(dev, np.abs(P2 @ q(mH.node[:, 0], mH.node[:, 1]) - q(mh.node[:, 0], mh.node[:, 1])).max(),
+                  np.abs(P1 @ l(mH.vert[:, 0], mH.vert[:, 1]) - l(mh.vert[:, 0], mh.vert[:, 1])).max())
+    return dev
+
+
+@pytest.mark.parametrize("graded", [False, True])
+def test_prolongation_exact_on_polynomials(graded):
+    assert _prolongation_deviation(graded) < 1e-13
+
+
+def test_prolongation_pin_catches_planted_basis_order(monkeypatch):
+    """The two last P2 basis functions (edge midpoints) swapped."""
+    good = fe.p2_basis
+
+    def planted(pts):
+        N, dN = good(pts)
+        return N[:, [0, 1, 2, 3, 5, 4]], dN
+
+    monkeypatch.setattr(fe, "p2_basis", planted)
+    assert _prolongation_deviation(False) > 1e-3
 
 
 # ------------------------------------------------------------------ glue (Step 4)
