@@ -3,8 +3,9 @@
 of P2/P1 fields, H = h, a brute-force global Newton step, closed-form interface sums,
 discrete mass balance, and the convergence rates of Theorem 5.4 / Table T1), and checks
 that planted mistakes in the oracle (a dropped or transposed convection term, a flipped
-coupling sign, a wrong exchange coefficient, unnormalised glue weights, a misordered P2
-basis in the prolongation) break the pins meant to catch them."""
+coupling sign, a wrong exchange coefficient, a wrong Beavers-Joseph-Saffman edge mass,
+unnormalised glue weights, a misordered P2 basis in the prolongation) break the pins meant
+to catch them."""
 import json
 import math
 import os
@@ -375,18 +376,25 @@ def test_newton_pin_catches_planted_operator_mistakes(monkeypatch, mistake):
     assert max(du, dp) > 1e-6
 
 
-def test_patch_pin_catches_planted_exchange_coefficient(monkeypatch):
+@pytest.mark.parametrize("mistake", ["exchange coefficient", "Gamma edge mass"])
+def test_patch_pin_catches_planted_coefficient_mistakes(monkeypatch, mistake):
     """Dropping the sigma* k_f / mu part of the fracture pressure's exchange coefficient
-    (the coefficient c_f of the second Darcy equation)."""
-    good = Ops.darcy_coeffs
+    (the coefficient c_f of the second Darcy equation), or doubling the Gamma edge mass that
+    carries the Beavers-Joseph-Saffman term."""
+    from oracle import scheme
+    if mistake == "exchange coefficient":
+        good = Ops.darcy_coeffs
 
-    def planted(self):
-        c = good(self)
-        p = self.prm
-        c[1] = (c[1][0] - p.sigma_star * p.k[1] / p.mu, c[1][1])
-        return c
+        def planted(self):
+            c = good(self)
+            p = self.prm
+            c[1] = (c[1][0] - p.sigma_star * p.k[1] / p.mu, c[1][1])
+            return c
 
-    monkeypatch.setattr(Ops, "darcy_coeffs", planted)
+        monkeypatch.setattr(Ops, "darcy_coeffs", planted)
+    else:
+        good_m = scheme.Region.gamma_mass
+        monkeypatch.setattr(scheme.Region, "gamma_mass", lambda self: 2.0 * good_m(self))
     assert max(_patch_deviation(False).values()) > 1e-6
 
 
