@@ -5,9 +5,10 @@ H = 1/8, h_x = 1/128, h_y from 1/128 at Gamma to 1/32, 4 x 4 subdomains per regi
 overlap 2 fine layers, log-uniform permeabilities (seed 0), dt = 0.005 -- 130,966 fine
 dofs, 16 Oseen systems (3.3k-8.3k unknowns) and 48 Darcy systems per step.
 
-Metric: fine dof-steps per second of the hot path, mixed precision (FP32 band factors and
-solves, FP64 assembly and refinement residuals), valid only if every field is within
-relative L2 1e-8 of the FP64 GPU path on the same steps.  One JSON line on rank 0.
+Metric: fine dof-steps per second of the hot path, mixed precision (FP32 multifrontal factors
+with tensor-core trailing updates, FP32 solves, FP64 assembly and refinement residuals), valid
+only if every field is within relative L2 1e-8 of the FP64 GPU path on the same steps.  One
+JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -27,7 +28,7 @@ METRIC = "fine DOF-steps/s at relL2<=1e-8, mixed vs FP64 GPU"
 UNIT = "DOF-steps/s"
 WORKLOAD = "2d_graded_H8_h128_to_h32_4x4sub_overlap2h_dt0.005 (130,966 fine dofs)"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max SM clock
+TF32_PER_BF16 = 0.5                                      # nominal dense TF32 / BF16 tensor rate (1.1 / 2.25)
 
 
 def parse():
@@ -127,19 +128,6 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-# ----------------------------------------------------------------------------- roofline
-def band_sizes(solver, n_fluid, n_porous):
-    out = []
-    for j in range(n_fluid + n_porous):
-        info = solver.debug_system(j)
-        n = len(info["node"])
-        reps = 1 if j < n_fluid else 3
-        kl = info["kl"]
-        ku = info["ku"] if j < n_fluid else kl
-        out += [(n, kl, ku, j < n_fluid)] * reps
-    return out
-
-
 def ndofs_of(st):
     return st["n_fine_dofs"]
 
@@ -172,11 +160,11 @@ def main():
     stream = torch.cuda.Stream()
     handle = stream.cuda_stream
 
-    def timed_hot(prec, with_phases=False):
+    def timed_hot(prec, with_phases=False, **opts):
         """K hot-path steps replayed from the captured CUDA graph (the timed region); then,
         optionally, the same number of steps launched kernel by kernel with per-phase CUDA
         events (the phase breakdown used for the roofline)."""
-        s = Solver(w, precision=prec, stream=handle)
+        s = Solver(w, precision=prec, stream=handle, **opts)
         s.coarse_precompute(Wm + 2 * K)
         s.local_step(Wm)
         torch.cuda.synchronize()
@@ -196,6 +184,7 @@ def main():
         ms = e0.elapsed_time(e1)
         launches = launch_count() - l0
         ms = max_over_ranks(ms, dist is not None, device="cuda")
+        fields = s.fields()   # after Wm + K steps, before any further step
         phases = None
         if with_phases:
             # one step per call so that each step's solve passes (systems converge after
@@ -209,37 +198,33 @@ def main():
             phases = s.timings()
             phases["_solve_bytes"] = solve_bytes
             s.set_timing(False)
-        return s, ms, launches, clocks, phases
+        return s, ms, launches, clocks, phases, fields
 
-    s64, ms64, _, _, _ = timed_hot("fp64")
-    f64 = s64.fields()
+    s64, ms64, _, _, _, f64 = timed_hot("fp64")
     st64 = s64.stats()
     s64.close()
-    s, ms, launches, clocks, phases = timed_hot(args.precision, with_phases=True)
+    s, ms, launches, clocks, phases, f = timed_hot(args.precision, with_phases=True)
     launches = int(sum_over_ranks(launches, dist is not None, device="cuda"))   # the whole job's
-    f = s.fields()
     st = s.stats()
-    # both runs stopped after Wm + K graph steps (the mixed run then took K eager steps more)
-    s_chk = Solver(w, precision=args.precision, stream=handle)
-    s_chk.coarse_precompute(Wm + K)
-    s_chk.local_step(Wm + K)
-    f = s_chk.fields()
-    s_chk.close()
+    # both fields were read after the same Wm + K steps
     rel = {k: float(np.linalg.norm(f[k] - f64[k]) / np.linalg.norm(f64[k])) for k in f}
-    # the tensor-core variants of the factorisation, same steps, error against the FP64 fields
+    # other factorisations of the local Oseen systems, same steps, error against the FP64 fields
     variants = {}
-    for vp in ("tf32", "bf16"):
+    for name, vp, opts in (("mf_fp32_cuda_cores", "fp32", {"cuda_cores": True}),
+                           ("band_fp32", "fp32", {"factor": "band"}),
+                           ("band_tf32_mma_sync", "tf32", {"factor": "band"}),
+                           ("band_bf16_mma_sync", "bf16", {"factor": "band"})):
         try:
-            sv, msv, _, _, _ = timed_hot(vp)
-            fv = sv.fields()
+            sv, msv, _, _, phv, fv = timed_hot(vp, with_phases=True, **opts)
             stv = sv.stats()
             sv.close()
-            variants[vp] = {"ms_per_step": msv / K, "value": ndofs_of(stv) * K * world / (msv / 1e3),
-                            "relL2_vs_fp64_gpu_max": max(float(np.linalg.norm(fv[k] - f64[k]) / np.linalg.norm(f64[k]))
-                                                         for k in fv),
-                            "ir_iters_max": stv["last_ir_iters_max"], "ir_relres_max": stv["last_ir_relres_max"]}
+            variants[name] = {"ms_per_step": msv / K, "value": ndofs_of(stv) * K * world / (msv / 1e3),
+                              "factor_ms_per_step": phv["band_lu"][0] / K,
+                              "relL2_vs_fp64_gpu_max": max(float(np.linalg.norm(fv[k] - f64[k]) / np.linalg.norm(f64[k]))
+                                                           for k in fv),
+                              "ir_iters_max": stv["last_ir_iters_max"], "ir_relres_max": stv["last_ir_relres_max"]}
         except Exception as ex:
-            variants[vp] = {"error": str(ex)[:120]}
+            variants[name] = {"error": str(ex)[:160]}
     solve_bytes_step = phases.pop("_solve_bytes") / K
     ph = {k: v[0] / K for k, v in phases.items()}
     phn = {k: v[1] for k, v in phases.items()}
@@ -250,20 +235,36 @@ def main():
     # ---------------------------------------------------------------- roofline
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    n_fluid = 16                      # 4 x 4 conduit subdomains
-    sizes = band_sizes(s, n_fluid, 16)
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
     tsz = 4 if args.precision == "fp32" else 8
     lu_ms = ph["band_lu"]
     lu_tflops = st["band_lu_flops"] / (lu_ms / 1e3) / 1e12
-    # all solve launches of a step (the active passes and the ones that find every system
-    # converged) against the bytes of the active passes
-    solve_gbs = solve_bytes_step / (ph["solve"] / 1e3) / 1e9
+    # algorithmic bytes of the HBM-bound phases (per step):
+    #   Oseen assembly + scatter: CSR values 8 nnz + right-hand side 8 n + element inputs
+    #     (11 FP64 geometry, 9 int32 ids, 6 nodes x 6 FP64 coarse / previous fields, 3 vertices
+    #     x 2 FP64) = 88 + 36 + 288 + 48 = 460 bytes per element
+    #   Darcy right-hand sides: 8 n (3 fields) + element inputs (88 + 24 + 6 x 9 x 8) = 544 B
+    #   state + glue: read e_j and I_h u_H, write the glued field: 3 x 8 bytes per fine dof
+    #   solves: the factor entries and block inverses of every active pass plus 24 n (see
+    #     tpns_stats.last_solve_bytes), over all solve launches of a step
+    asm_bytes = 8 * st["oseen_nnz"] + 8 * st["oseen_unknowns"] + 460 * st["oseen_elements"]
+    darcy_bytes = 8 * st["darcy_unknowns"] + 544 * st["darcy_elements"]
+    glue_bytes = 24 * ndofs
+
+    def hbm(bytes_, ms_):
+        gbs = bytes_ / (ms_ / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "ms_per_step": ms_, "bytes_per_step": bytes_}
     kernels = {
-        "band_lu": {"bound": "alu", "achieved": lu_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": lu_tflops / FP32_PEAK_TFLOPS, "ms_per_step": lu_ms},
-        "band_solve": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm_peak, "unit": "GB/s",
-                       "frac": solve_gbs / hbm_peak, "ms_per_step": ph["solve"],
-                       "bytes_per_step": solve_bytes_step, "launches_per_step": phn["solve"] / K},
+        "mf_factor": {"bound": "tensor", "achieved": lu_tflops, "peak": tf32_peak, "unit": "TFLOP/s",
+                      "frac": lu_tflops / tf32_peak, "ms_per_step": lu_ms,
+                      "flops_per_step": st["band_lu_flops"], "fronts": st["mf_fronts"],
+                      "note": "algorithmic flops of the nested-dissection partial factorisations; the "
+                              "trailing updates issue 3 TF32 products per multiply-add (split operands)"},
+        "solves": {**hbm(solve_bytes_step, ph["solve"]), "launches_per_step": phn["solve"] / K},
+        "oseen_assembly": hbm(asm_bytes, ph["asm_oseen"] + ph["scatter"]),
+        "darcy_rhs": hbm(darcy_bytes, ph["asm_darcy"]),
+        "state_glue": hbm(glue_bytes, ph["state_glue"]),
     }
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     traffic = None
@@ -273,18 +274,19 @@ def main():
             traffic = json.load(open(tfile)).get(dom)
         except Exception:
             traffic = None
-    roof = dict(kernels[dom])
-    roof.pop("ms_per_step")
+    roof = {k: v for k, v in kernels[dom].items() if k in ("bound", "achieved", "peak", "unit", "frac")}
     roof["kernel"] = dom
     roof["traffic"] = traffic
-    roof["peak_source"] = ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if roof["bound"] == "alu"
-                           else "measured hbm_gbs (MEASURED_PEAKS.json)")
+    roof["peak_source"] = ("measured bf16_tflops (MEASURED_PEAKS.json) x 1/2, the nominal TF32/BF16 ratio"
+                           if roof["bound"] == "tensor" else "measured hbm_gbs (MEASURED_PEAKS.json)")
     s.close()
     # ---------------------------------------------------------------- end to end (public API, host buffers)
     torch.cuda.synchronize()
     pinned = {}
     t0 = time.perf_counter()
     e = Solver(w, precision=args.precision, stream=handle)
+    torch.cuda.synchronize()
+    t_created = time.perf_counter()
     d2h = 0
     for _ in range(K):
         e.step(1)
@@ -295,11 +297,13 @@ def main():
             e.field(k, out=buf)
             d2h += buf.nbytes
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist is not None, device="cuda")
+    t_end = time.perf_counter()
+    e2e_s = max_over_ranks(t_end - t0, dist is not None, device="cuda")
+    steps_s = max_over_ranks(t_end - t_created, dist is not None, device="cuda")
     st_e = e.stats()
     e.close()
     e2e_val = ndofs * K * world / e2e_s
-    full_ms = e2e_s * 1e3 / K
+    full_ms = steps_s * 1e3 / K
     # ---------------------------------------------------------------- serving (bounded sample)
     serving = None
     if args.serving_requests > 0:
@@ -340,17 +344,20 @@ def main():
             "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "fine_dofs": ndofs, "local_systems_per_step": st["n_local_systems"],
-                       "replicas": world, "l2": "inputs larger than L2 (band factors %.0f MB per replica)"
-                       % (sum(n * (kl + ku + 1) for n, kl, ku, _ in sizes) * tsz / 1e6),
+                       "replicas": world, "l2": "inputs larger than L2 (multifrontal fronts %.0f MB per replica)"
+                       % (st["factor_entries"] * tsz / 1e6),
                        "parallelism": "independent replicas (no data-path collective)",
-                       "timed": "K hot-path steps (prolongation, assembly, band LU, solves + FP64 refinement, glue) "
-                                "replayed from a CUDA graph on coarse states precomputed in HBM; per-phase times "
-                                "from K further steps launched kernel by kernel"},
+                       "factorisation": "multifrontal (nested dissection), FP32 fronts, tcgen05 split-TF32 "
+                                        "trailing updates",
+                       "timed": "K hot-path steps (prolongation, assembly, multifrontal LU, solves + FP64 "
+                                "refinement, glue) replayed from a CUDA graph on coarse states precomputed in HBM; "
+                                "per-phase times from K further steps launched kernel by kernel"},
             "valid": valid, "relL2_vs_fp64_gpu": rel,
             "fp64_gpu": {"value": value64, "ms_per_step": ms64 / K},
-            "tensor_core_variants": {
-                "what": "trailing band-LU updates on the tensor cores (mma.sync): tf32 = TF32 with split "
-                        "operands, bf16 = plain BF16; FP32 factors, FP64-residual refinement",
+            "factorisation_variants": {
+                "what": "other factorisations of the local Oseen systems on the same steps: the multifrontal "
+                        "LU with CUDA-core trailing updates, and the band LU (FP32 FMA; mma.sync TF32 with "
+                        "split operands; mma.sync plain BF16); FP64-residual refinement throughout",
                 **variants},
             "speedup_vs_fp64_gpu": value / value64,
             "roofline": roof, "kernels": kernels,
@@ -358,9 +365,13 @@ def main():
             "ir": {"iters_max": st["last_ir_iters_max"], "relres_max": st["last_ir_relres_max"]},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": st_e["h2d_bytes"] / K,
                     "d2h_bytes_per_step": d2h / K,
-                    "what": "tpns_create from host descriptors + K x (tpns_step incl. coarse solve + "
-                            "tpns_get_field of all 6 fields into pinned host memory)",
-                    "full_step_ms": full_ms},
+                    "what": "tpns_create from host descriptors (its uploads amortised over the K steps) + K x "
+                            "(tpns_step incl. the coarse solve + tpns_get_field of all 6 fields into pinned host "
+                            "memory)",
+                    "create_ms": (t_created - t0) * 1e3, "create_ms_library": st_e["create_ms"],
+                    "full_step_ms": full_ms,
+                    "full_step_what": "one tpns_step (coarse solve + hot path) plus the read-back of all fields, "
+                                      "create excluded"},
             "gpu_launches": launches,
             "serving": serving,
             "clocks": clocks,

@@ -107,7 +107,9 @@ typedef struct {
   int64_t n_fine_dofs;            /* all global fine dofs of all fields */
   int64_t n_local_systems;        /* Oseen + Darcy local systems per step */
   int64_t device_bytes;           /* device footprint of the context */
-  double band_lu_flops;           /* algorithmic flops of one step's Oseen band LUs */
+  double band_lu_flops;           /* algorithmic flops of one step's Oseen factorisations: band
+                                     LU: sum over columns of l + 2 l u; multifrontal: sum over
+                                     fronts and pivots of r + 2 r^2, r = rows below the pivot */
   int64_t h2d_bytes;              /* bytes copied host -> device by tpns_create */
   int64_t last_ir_solves;         /* band solve passes over all local systems, last step */
   double last_solve_bytes;        /* algorithmic bytes of those passes: per pass and system
@@ -117,12 +119,40 @@ typedef struct {
   double last_step_ms;            /* device time of the context's last step in tpns_batch_step,
                                      from the step's start on its stream to its end (with the
                                      other contexts of the batch running beside it) */
-  int64_t lu_cluster_ctas;        /* CTAs per cluster of the Oseen band LU: 8, or 16 where all
-                                     clusters fit the device and tpns_create measured 16 faster
-                                     on the context's own systems */
+  int64_t lu_cluster_ctas;        /* band LU: CTAs per cluster of the Oseen band LU, 8, or 16
+                                     where all clusters fit the device and tpns_create measured
+                                     16 faster on the context's own systems; 0 with the
+                                     multifrontal factorisation */
+  /* sizes of one step's local problems (for algorithmic byte counts) */
+  int64_t oseen_unknowns, oseen_nnz, oseen_elements;   /* all local Oseen systems */
+  int64_t darcy_unknowns, darcy_elements;             /* all local Darcy systems (x 3 fields) */
+  double factor_entries;          /* stored entries of one step's Oseen factors (L and U) */
+  int64_t mf_fronts;              /* multifrontal: fronts per step (0 with the band LU) */
+  double create_ms;               /* host wall time of tpns_create for this context */
 } tpns_stats;
 
 typedef struct tpns_ctx tpns_ctx;
+
+/* Factorisation of the local Oseen systems of Algorithm 3 Step 3(2) (eq. uclocalFully; the
+ * paper leaves the solver open).  The Darcy systems always use the one-time band Cholesky. */
+typedef enum {
+  TPNS_FACTOR_MULTIFRONTAL = 0,   /* nested dissection of the subdomain's node grid, dense
+                                     fronts factorised level by level (default) */
+  TPNS_FACTOR_BAND = 1            /* unpivoted band LU in the band ordering */
+} tpns_factor;
+
+/* Options of tpns_create_ex; a zero-filled struct (or NULL) gives the defaults. */
+typedef struct {
+  int32_t local_factor;     /* tpns_factor */
+  int32_t mf_leaf;          /* multifrontal: boxes of at most this many unknowns are not
+                               dissected further (0 = 96) */
+  int32_t mf_cuda_cores;    /* multifrontal, FP32 factors: 1 = trailing updates on the CUDA
+                               cores; 0 = on the tensor cores (tcgen05, each operand split in
+                               two TF32 parts, FP32 accumulation) */
+  int32_t mf_ctas;          /* multifrontal: CTAs of the factorisation and solve launches
+                               (0 = as many as are resident at once: one per SM for the
+                               tensor-core factorisation) */
+} tpns_options;
 
 /* Build meshes, subdomains, sparsity, scatter maps and band orderings on the host, upload
  * them, factor the time-invariant Darcy blocks and set the initial state (nodal
@@ -138,9 +168,18 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params,
                         double dt, tpns_precision precision, size_t hbm_budget_bytes,
                         void* cuda_stream, tpns_ctx** out);
 
+/* tpns_create with options (see tpns_options; NULL = defaults).  TPNS_BF16_IR is available
+ * with TPNS_FACTOR_BAND only. */
+tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params,
+                           const tpns_partition_desc* part, const tpns_data_desc* data,
+                           double dt, tpns_precision precision, size_t hbm_budget_bytes,
+                           void* cuda_stream, const tpns_options* options, tpns_ctx** out);
+
 /* Advance nsteps time steps (Algorithm 3 Steps 1, 3, 4 each step), enqueued on the
- * context's stream; returns after the work is enqueued and the step's status word read
- * back (one device-to-host copy of a few bytes per call). */
+ * context's stream.  Cost on the host: after the last step is enqueued the call reads the
+ * status words, refinement counters and residuals of every local system back (a few
+ * device-to-host copies), so it synchronises the stream once per call; callers that want
+ * work in flight across calls pass a larger nsteps. */
 tpns_status tpns_step(tpns_ctx* ctx, int32_t nsteps);
 
 /* Run Step 1 (coarse decoupled solves) for the next nsteps steps ahead and keep the coarse
@@ -154,19 +193,27 @@ tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps);
  * glue) only.  Fails with TPNS_EINVAL if fewer coarse states are stored. */
 tpns_status tpns_local_step(tpns_ctx* ctx, int32_t nsteps);
 
-/* Number of global fine values of a field (see field ids above). */
+/* Number of global fine values of a field (see field ids above): the dimension of the
+ * fine finite element space of that unknown (Sec. 3.2: X_h, Q_h for the conduit, X_ph for
+ * each Darcy pressure), Dirichlet nodes included. */
 tpns_status tpns_num_dofs(const tpns_ctx* ctx, int32_t field, size_t* n);
 
-/* Copy the glued global fine field into dst (n values, FP64).  dst_on_device != 0: dst is
- * a device pointer on the context's device (copied on the context's stream, then the
- * stream is synchronised). */
+/* Copy the glued global fine field of the last step into dst (n values, FP64): the
+ * corrected solution u^h = I_h u_H^{n+1} + sum_j w_j e_j^{n+1} of Algorithm 3 Step 4
+ * ("correction of data"), in the global fine numbering.  n must equal tpns_num_dofs.
+ * dst_on_device != 0: dst is a device pointer on the context's device (copied on the
+ * context's stream, then the stream is synchronised); otherwise a host pointer. */
 tpns_status tpns_get_field(tpns_ctx* ctx, int32_t field, double* dst, size_t n,
                            int32_t dst_on_device);
 
-/* Counters of the last step and sizes of the context. */
+/* Counters of the last step and sizes of the context.  The paper has no counterpart: it
+ * reports only run times (Sec. 6, Tables 1-4) and leaves the linear solvers unspecified;
+ * these counters describe this library's factorisations and refinement. */
 tpns_status tpns_get_stats(tpns_ctx* ctx, tpns_stats* out);
 
-/* Serving: one time step of each of n contexts.  The steps of all contexts are enqueued
+/* Serving: one time step of each of n contexts (Algorithm 3 Steps 1, 3, 4 of independent
+ * simulations; the paper runs one simulation at a time, so batching them has no
+ * counterpart there).  The steps of all contexts are enqueued
  * first, each on its context's stream (graph replays), so that their assembly, factorisation,
  * solves and glue kernels run side by side on the device; then every context's status is
  * collected.  All contexts must live on the same device.  Returns the first failure
@@ -187,9 +234,12 @@ tpns_status tpns_get_timings(const tpns_ctx* ctx, double* ms, int64_t* count, in
 int64_t tpns_launch_count(void);
 
 /* Last error message of a context (never NULL; "" when none).  ctx may be NULL for errors
- * raised before a context existed. */
+ * raised before a context existed or outside one; that message is kept per host thread.
+ * No counterpart in the paper. */
 const char* tpns_last_error(const tpns_ctx* ctx);
 
+/* Release every device and host resource of a context (waits for its stream first).
+ * NULL is ignored.  No counterpart in the paper. */
 void tpns_destroy(tpns_ctx* ctx);
 
 /* ---- introspection (tests) ----------------------------------------------------------
@@ -214,7 +264,7 @@ tpns_status tpns_debug_system(const tpns_ctx* ctx, int32_t j, int32_t* n_unknown
  * triangular solves with FP64-residual iterative refinement (stop at ||b - A x|| <= 1e-13
  * ||b||, on stagnation, or after 12 corrections).
  *   n            unknowns; kl, ku: lower / upper bandwidth of A (every entry a_ij != 0 has
- *                i - j <= kl and j - i <= ku); kl + 32 <= 512.
+ *                i - j <= kl and j - i <= ku); kl + 32 <= 512 and ku + 32 <= 512.
  *   rowptr, colidx, vals, b, x: DEVICE pointers (CSR int32 / FP64, b and x FP64, n each);
  *                x is overwritten.
  *   precision    TPNS_FP64 or TPNS_FP32_IR; stream: cudaStream_t (NULL = legacy stream).
@@ -229,19 +279,23 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
                             double* relres_out);
 
 /* Same operation and arguments as tpns_band_solve, for callers that cannot allocate device
- * memory: code that runs while a CUDA stream is being captured into a graph (cudaMalloc is
- * not allowed there), hosts whose device memory is owned by another allocator that must not
- * see foreign allocations, and loops where an allocation's latency or failure at solve time
- * is not acceptable.  No part of the paper corresponds to it.
- * The scratch (band, block inverses, row index, vectors, flags) lives in one device array
- * of TPNS_NOALLOC_SCRATCH_BYTES bytes that the library declares statically; every device
- * that loads the library holds it until the process exits.  A system fits when
- *   n*(kl+ku+1)*s + ceil(n/32)*32*(kl+ku+64)*s + 4*nnz + 8*(n+130) + 4*(5+2*ceil(n/32)) + 2048
- * is at most that size (s = 4 for TPNS_FP32_IR, 8 for TPNS_FP64, plus 256-byte alignment of
- * each piece); larger systems are refused with TPNS_EINVAL.  The first call on a device looks
- * up the array's device address (with that device current); make that first call before any
- * stream capture.  All calls share the one array and it keeps the last call's contents, so
- * calls that overlap on the GPU (different streams or threads) race: serialise them. */
+ * memory: hosts whose device memory belongs to another allocator that must not see foreign
+ * allocations, and loops where the latency or the failure of an allocation at solve time is
+ * not acceptable.  No part of the paper corresponds to it.
+ * The scratch (band, block inverses, solve vector, row index, vectors, flags) lives in one
+ * device array of TPNS_NOALLOC_SCRATCH_BYTES bytes that the library declares statically;
+ * every device that loads the library holds it until the process exits.  With s = 4 for
+ * TPNS_FP32_IR and 8 for TPNS_FP64, a system fits when the sum of these pieces, each rounded
+ * up to a multiple of 256 bytes,
+ *   n*(kl+ku+1)*s  +  ceil(n/32)*2048*s  +  ceil(n/32)*32*kl*s  +  ceil(n/32)*32*ku*s
+ *   + n*s  +  sizeof(SysDev) (< 256)  +  4*(6+2*ceil(n/32))  +  4*nnz  +  8*(n+130)
+ * is at most that size; larger systems are refused with TPNS_EINVAL.  kl and ku are each at
+ * most 480.  The call reads nnz from rowptr[n] and the final status back to the host and
+ * synchronises the stream (also on every failure after its first launch), so when it
+ * returns no work of it is still running.  The first call on a device looks up the array's
+ * device address with that device current.  All calls share the one array and it keeps the
+ * last call's contents, so calls that overlap on the GPU (issued from different host threads)
+ * race: serialise them. */
 #define TPNS_NOALLOC_SCRATCH_BYTES (32u << 20)
 tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int32_t* rowptr,
                                     const int32_t* colidx, const double* vals, const double* b,
@@ -253,6 +307,27 @@ tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int
  * returns TPNS_EINVAL.  Release with tpns_destroy. */
 tpns_status tpns_layout_create(const tpns_mesh_desc* mesh, const tpns_partition_desc* part,
                                tpns_ctx** out);
+
+/* tpns_layout_create with options (only local_factor and mf_leaf are read; NULL = defaults). */
+tpns_status tpns_layout_create_ex(const tpns_mesh_desc* mesh, const tpns_partition_desc* part,
+                                  const tpns_options* options, tpns_ctx** out);
+
+/* Multifrontal structure of local Oseen system j (0 .. number of conduit subdomains - 1) as
+ * the library analysed it, for an independent check of the symbolic factorisation.  what:
+ *   0  [number of fronts, number of levels]
+ *   1  per front (postorder, children before parents): m, p, level, parent, nchild,
+ *      child0, child1 (7 int32; -1 = none)
+ *   2  front rows: per front its m unknowns (system numbering of tpns_debug_system), own
+ *      pivots first in elimination order, then the update set
+ *   3  per front its update set mapped into the parent's rows (m - p int32)
+ *   4  per front m + 1 column pointers into the front's originals (from 0)
+ *   5  originals: CSR entry index within the system, per front and column
+ *   6  originals: row of the entry in the front
+ *   7  per front 2 m int32: column of child 0 / child 1 added into column j (or -1)
+ *   8  elimination order (n unknowns)
+ * Returns the number of int32 values in *n when dst is NULL.  TPNS_EINVAL without a
+ * multifrontal analysis. */
+tpns_status tpns_debug_fronts(const tpns_ctx* ctx, int32_t j, int32_t what, int32_t* dst, size_t* n);
 
 /* FP64 CSR values (nnz entries, pattern of tpns_debug_system) and right-hand side (n
  * entries) of local system j as assembled in the last step (Darcy: field 0..2 selects the

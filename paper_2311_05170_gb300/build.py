@@ -10,7 +10,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libtpns.so")
-UNITS = ["setup.cpp", "kernels_band_f32.cu", "kernels_band_f64.cu", "kernels_assemble.cu", "capi.cu"]
+UNITS = ["setup.cpp", "mf_symbolic.cpp", "kernels_band_f32.cu", "kernels_band_f64.cu", "kernels_assemble.cu",
+         "kernels_mf.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

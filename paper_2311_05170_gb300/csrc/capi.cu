@@ -6,7 +6,10 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <string>
+#include <atomic>
+#include <chrono>
 #include <mutex>
 #include <vector>
 
@@ -65,6 +68,18 @@ struct tpns_ctx {
   int64_t kernels_full = 0, kernels_local = 0;   // kernels in each captured graph
   cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;   // bracket the context's step in tpns_batch_step
   int lu_cl = 0;                                   // CTAs per cluster of the Oseen LU, picked at create
+  // multifrontal factorisation of the local Oseen systems
+  bool mf = false;
+  int mf_leaf = 96, mf_tc = 1, mf_m_max = 1;
+  double mf_flops = 0, mf_factor_entries = 0, mf_dinv_entries = 0;
+  MFLaunch mfl{};
+  std::vector<MFSysDev> h_mfsys;
+  int64_t mf_F_len = 0, mf_dinv_len = 0, mf_upd_len = 0;
+  void *d_mf_F = nullptr, *d_mf_dinv = nullptr, *d_mf_y = nullptr, *d_mf_d = nullptr, *d_mf_upd = nullptr;
+  // band solves: every local system (band LU) or the Darcy systems only (multifrontal)
+  std::vector<int> list_band;
+  int* d_list_band = nullptr;
+  int n_max_band = 0, kmax_band = 0;
   // device
   ProbDev* d_probs = nullptr;
   int32_t *d_eprob = nullptr, *d_e6 = nullptr, *d_e3 = nullptr;
@@ -134,6 +149,8 @@ struct tpns_ctx {
   GlueArgs glue{};
 };
 
+// message of the last failure raised without a context (per host thread, so concurrent
+// callers do not overwrite each other's message)
 static thread_local std::string g_err;
 
 
@@ -222,7 +239,7 @@ static std::vector<int32_t> inverse_map(const std::vector<int32_t>& g, int n) {
 static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns_partition_desc& pd,
                              size_t budget) {
   Layout& L = ctx->L;
-  std::string msg = build_layout(md, pd, L);
+  std::string msg = build_layout(md, pd, L, ctx->mf ? ctx->mf_leaf : 0);
   if (!msg.empty()) {
     ctx->err = msg;
     return TPNS_EINVAL;
@@ -294,6 +311,9 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
         C.band_off = ctx->band_chol_coarse_len; ctx->band_chol_coarse_len += (int64_t)S.n * C.ldab;
         S.lslab_off = ctx->lslab_coarse_len; ctx->lslab_coarse_len += round32(llen);
         S.uslab_off = ctx->uslab_coarse_len; ctx->uslab_coarse_len += round32(ulen);
+      } else if (ctx->mf && P.kind == PK_OSEEN) {
+        // factored by the multifrontal LU: no band storage
+        S.band_off = 0; S.dinv_off = 0; S.lslab_off = 0; S.uslab_off = 0; C.band_off = 0;
       } else {
         S.band_off = bl; bl += blen;
         S.dinv_off = ctx->dinv_local_len; ctx->dinv_local_len += dlen;
@@ -306,7 +326,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       ctx->hchol.push_back(P.kind == PK_DARCY ? 1 : 0);
     }
     rp += P.n + 1; nz += (int64_t)P.colidx.size();
-    if (P.kind == PK_OSEEN && !coarse) ctx->lu_flops_step += P.lu_flops;
+    if (P.kind == PK_OSEEN && !coarse) ctx->lu_flops_step += ctx->mf ? P.mf.flops : P.lu_flops;
   }
   ctx->nsys = (int)ctx->hsys.size();
   ctx->nnz_tot = nz; ctx->vals_tot = vals; ctx->xvec_tot = xo;
@@ -319,6 +339,11 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   ctx->list_cp = {ctx->sys_first[CP], ctx->sys_first[CP] + 1, ctx->sys_first[CP] + 2};
   ctx->list_local = ctx->list_osl;
   ctx->list_local.insert(ctx->list_local.end(), ctx->list_dl.begin(), ctx->list_dl.end());
+  ctx->list_band = ctx->mf ? ctx->list_dl : ctx->list_local;
+  for (int s : ctx->list_band) {
+    ctx->n_max_band = std::max(ctx->n_max_band, ctx->hsys[s].n);
+    ctx->kmax_band = std::max(ctx->kmax_band, std::max(ctx->hsys[s].kl, ctx->hsys[s].ku));
+  }
   for (int s : ctx->list_osl) ctx->kl_max_osl = std::max(ctx->kl_max_osl, ctx->hsys[s].kl);
   for (int s : ctx->list_local) {
     ctx->n_max_local = std::max(ctx->n_max_local, ctx->hsys[s].n);
@@ -334,11 +359,67 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   ctx->kl_max_cf = ctx->hsys[ctx->list_cf[0]].kl;
   ctx->n_max_cf = ctx->hsys[ctx->list_cf[0]].n;
   for (int s : ctx->list_cp) ctx->n_max_cp = std::max(ctx->n_max_cp, ctx->hsys[s].n);
+  // multifrontal layout of the local Oseen systems: the fronts of all systems in level
+  // order (leaves first), so that a front's children always precede it
+  std::vector<MFFrontDev> h_fronts;
+  std::vector<int32_t> h_mrows, h_relmap, h_origk, h_origi;
+  std::vector<int64_t> h_colptr;
+  if (ctx->mf) {
+    ctx->h_mfsys.clear();
+    ctx->mf_flops = ctx->mf_factor_entries = ctx->mf_dinv_entries = 0;
+    struct Key { int level, q, t; };
+    std::vector<Key> keys;
+    std::vector<std::vector<int>> newid(ctx->nf);
+    for (int q = 0; q < ctx->nf; ++q) {
+      const MFSymbolic& M = ctx->probs[q]->mf;
+      newid[q].assign(M.fronts.size(), -1);
+      for (int t = 0; t < (int)M.fronts.size(); ++t) keys.push_back({M.fronts[t].level, q, t});
+      const SysDev& Sd = ctx->hsys[ctx->sys_first[q]];
+      MFSysDev D{};
+      D.sid = ctx->sys_first[q]; D.n = ctx->probs[q]->n; D.x_off = Sd.x_off; D.val_off = Sd.val_off;
+      ctx->h_mfsys.push_back(D);
+      ctx->mf_flops += M.flops;
+      ctx->mf_factor_entries += M.factor_entries;
+    }
+    std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) { return a.level < b.level; });
+    for (size_t i = 0; i < keys.size(); ++i) newid[keys[i].q][keys[i].t] = (int)i;
+    for (const Key& k : keys) {
+      const MFFront& F = ctx->probs[k.q]->mf.fronts[k.t];
+      if (F.m >= 32768) {
+        ctx->err = "a multifrontal front of order " + std::to_string(F.m) + " exceeds 32767";
+        return TPNS_EINVAL;
+      }
+      MFFrontDev FD{};
+      FD.m = F.m; FD.p = F.p; FD.ld = (F.m + 3) & ~3; FD.sys = k.q;
+      FD.f_off = ctx->mf_F_len; ctx->mf_F_len += (int64_t)FD.ld * F.m;
+      const int nb = (F.p + MF_NB - 1) / MF_NB;
+      FD.dinv_off = ctx->mf_dinv_len; ctx->mf_dinv_len += (int64_t)nb * 2 * MF_NB * MF_NB;
+      FD.upd_off = ctx->mf_upd_len; ctx->mf_upd_len += F.m - F.p;
+      FD.nchild = F.nchild;
+      FD.child0 = F.nchild > 0 ? newid[k.q][F.child[0]] : -1;
+      FD.child1 = F.nchild > 1 ? newid[k.q][F.child[1]] : -1;
+      FD.parent = F.parent >= 0 ? newid[k.q][F.parent] : -1;
+      FD.rows_off = (int32_t)h_mrows.size();
+      h_mrows.insert(h_mrows.end(), F.rows.begin(), F.rows.end());
+      FD.relmap_off = (int32_t)h_relmap.size();
+      h_relmap.insert(h_relmap.end(), F.relmap.begin(), F.relmap.end());
+      FD.colptr_off = (int32_t)h_colptr.size();
+      const int64_t ob = (int64_t)h_origk.size();
+      for (int j = 0; j <= F.m; ++j) h_colptr.push_back(ob + F.col_ptr[j]);
+      h_origk.insert(h_origk.end(), F.orig_k.begin(), F.orig_k.end());
+      for (int j = 0; j < F.m; ++j)
+        for (int q = F.col_ptr[j]; q < F.col_ptr[j + 1]; ++q) h_origi.push_back(F.orig_i[q] | (j << 16));
+      ctx->mf_m_max = std::max(ctx->mf_m_max, F.m);
+      ctx->mf_dinv_entries += (double)nb * 2 * MF_NB * MF_NB;
+      h_fronts.push_back(FD);
+    }
+  }
   // footprint check before any allocation
   const size_t Tsz = ctx->prec == TPNS_FP64 ? 8 : 4;
   size_t est = (size_t)ctx->band_local_len * Tsz + (size_t)ctx->band_coarse_len * 8 +
                (size_t)(ctx->ne_osl + ctx->ne_cf) * (225 + 15) * 8 + (size_t)ctx->vals_tot * 8 +
-               (size_t)ctx->nnz_tot * 8 + (size_t)ctx->xvec_tot * 3 * 8 + (size_t)ctx->ne_tot * 11 * 8;
+               (size_t)ctx->nnz_tot * 8 + (size_t)ctx->xvec_tot * 3 * 8 + (size_t)ctx->ne_tot * 11 * 8 +
+               (size_t)(ctx->mf_F_len + ctx->mf_dinv_len + ctx->mf_upd_len + 2 * (ctx->mf ? ctx->xvec_tot : 0)) * Tsz;
   ctx->budget = budget;
   if (budget > 0 && est > budget) {
     ctx->err = "device footprint " + std::to_string(est) + " B exceeds the budget";
@@ -355,8 +436,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     }
     const size_t need_local = ctx->prec == TPNS_FP64 ? band_lu_smem_bytes<double>(ctx->kl_max_osl)
                                                      : band_lu_smem_bytes<float>(ctx->kl_max_osl);
-    if (need_local > (size_t)smem_max || band_lu_smem_bytes<double>(ctx->kl_max_cf) > (size_t)smem_max) {
-      ctx->err = "band width kl = " + std::to_string(std::max(ctx->kl_max_osl, ctx->kl_max_cf)) +
+    if ((!ctx->mf && need_local > (size_t)smem_max) || band_lu_smem_bytes<double>(ctx->kl_max_cf) > (size_t)smem_max) {
+      ctx->err = "band width kl = " + std::to_string(std::max(ctx->mf ? 0 : ctx->kl_max_osl, ctx->kl_max_cf)) +
                  " needs more shared memory per CTA than the device has (" + std::to_string(smem_max) +
                  " B); use more subdomains or the FP32 precision";
       return TPNS_EINVAL;
@@ -473,7 +554,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     TRY(dalloc(ctx, &d, ctx->dinv_local_len));
     ctx->d_band_local = b;
     ctx->d_dinv_local = d;
-    if (!band_solve_fits_smem<double>(ctx->n_max_local, ctx->kmax_local)) {
+    if (!band_solve_fits_smem<double>(ctx->n_max_band, ctx->kmax_band)) {
       double* v;
       TRY(dalloc(ctx, &v, ctx->xvec_tot));
       ctx->d_vwork = v;
@@ -484,11 +565,48 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     TRY(dalloc(ctx, &d, ctx->dinv_local_len));
     ctx->d_band_local = b;
     ctx->d_dinv_local = d;
-    if (!band_solve_fits_smem<float>(ctx->n_max_local, ctx->kmax_local)) {
+    if (!band_solve_fits_smem<float>(ctx->n_max_band, ctx->kmax_band)) {
       float* v;
       TRY(dalloc(ctx, &v, ctx->xvec_tot));
       ctx->d_vwork = v;
     }
+  }
+  TRY(upload(ctx, &ctx->d_list_band, ctx->list_band));
+  if (ctx->mf) {
+    MFSysDev* d_mfsys;
+    MFFrontDev* d_fronts;
+    int32_t *d_rows, *d_relmap, *d_ok, *d_oi;
+    int64_t* d_cp;
+    TRY(upload(ctx, &d_mfsys, ctx->h_mfsys));
+    TRY(upload(ctx, &d_fronts, h_fronts));
+    TRY(upload(ctx, &d_rows, h_mrows));
+    if (h_relmap.empty()) h_relmap.push_back(0);
+    if (h_origk.empty()) { h_origk.push_back(0); h_origi.push_back(0); }
+    TRY(upload(ctx, &d_relmap, h_relmap));
+    TRY(upload(ctx, &d_cp, h_colptr));
+    TRY(upload(ctx, &d_ok, h_origk));
+    TRY(upload(ctx, &d_oi, h_origi));
+    // scheduling words: task counters and finished-CTA counts at 0, epochs from 1 (the flags
+    // start at 0, so no flag of a launch is set before the launch sets it)
+    const int nfr = (int)h_fronts.size();
+    std::vector<int32_t> sched = {0, 0, 1, 0, 0, 0, 1, 0};
+    std::vector<int32_t> flags((size_t)3 * std::max(nfr, 1), 0);
+    int32_t *d_sched, *d_flags;
+    TRY(upload(ctx, &d_sched, sched));
+    TRY(upload(ctx, &d_flags, flags));
+    MFLaunch& M = ctx->mfl;
+    M.sys = d_mfsys; M.nsys = (int)ctx->h_mfsys.size(); M.fronts = d_fronts; M.nfront = nfr; M.rows = d_rows; M.relmap = d_relmap; M.colptr = d_cp;
+    M.orig_k = d_ok; M.orig_ij = d_oi;
+    M.vals = nullptr; M.status = nullptr;   // set below once the values and status words exist
+    M.sched = d_sched; M.fflag = d_flags; M.sflag = d_flags + nfr;
+    const size_t ts = ctx->prec == TPNS_FP64 ? 8 : 4;
+    unsigned char *F, *dv, *y, *d, *u;
+    TRY(dalloc(ctx, &F, (size_t)std::max<int64_t>(ctx->mf_F_len, 1) * ts));
+    TRY(dalloc(ctx, &dv, (size_t)std::max<int64_t>(ctx->mf_dinv_len, 1) * ts));
+    TRY(dalloc(ctx, &y, (size_t)ctx->xvec_tot * ts));
+    TRY(dalloc(ctx, &d, (size_t)ctx->xvec_tot * ts));
+    TRY(dalloc(ctx, &u, (size_t)std::max<int64_t>(ctx->mf_upd_len, 1) * ts));
+    ctx->d_mf_F = F; ctx->d_mf_dinv = dv; ctx->d_mf_y = y; ctx->d_mf_d = d; ctx->d_mf_upd = u;
   }
   TRY(dalloc(ctx, &ctx->d_band_coarse, ctx->band_coarse_len));
   TRY(dalloc(ctx, &ctx->d_dinv_coarse, ctx->dinv_coarse_len));
@@ -712,6 +830,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   G.FW1 = ctx->d_FW1; G.FP1 = ctx->d_FP1; G.FPD1 = ctx->d_FPD1;
   G.out_u = ctx->d_out_u; G.out_p = ctx->d_out_p; G.out_pd = ctx->d_out_pd;
   G.nnc = nnc; G.nvc = nvc; G.nnp = nnp;
+  ctx->mfl.vals = ctx->d_vals;
+  ctx->mfl.status = ctx->d_status;
   return TPNS_OK;
 }
 
@@ -859,17 +979,35 @@ static tpns_status local_step(tpns_ctx* ctx) {
   CK(launch_darcy_elem(ctx->asmargs, ctx->eD0, ctx->ne_dl, ctx->d_ReD, nullptr, st));
   CK(launch_seg_reduce(ctx->d_rd_t, ctx->d_rd_s, ctx->n_rd, ctx->d_ReD, ctx->d_b, st, nullptr));
   ph_end(ctx, PH_ASM_DARCY);
-  // a6: band LU of every Oseen system
-  ph_begin(ctx, PH_BAND_FILL);
-  CK(launch_band_fill<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 0, 0, st,
-                         nullptr));
-  ph_end(ctx, PH_BAND_FILL);
-  ph_begin(ctx, PH_BAND_LU);
-  CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, lslab, uslab, dinv, ctx->d_flags,
-                       ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr,
-                       ctx->prec == TPNS_TF32_IR ? 1 : ctx->prec == TPNS_BF16_IR ? 2 : 0, ctx->lu_cl));
-  CK(launch_band_dinv<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->nblk_max_osl, band, dinv, st, nullptr));
-  ph_end(ctx, PH_BAND_LU);
+  // a6: LU of every Oseen system (multifrontal fronts or band)
+  T* mfF = reinterpret_cast<T*>(ctx->d_mf_F);
+  T* mfD = reinterpret_cast<T*>(ctx->d_mf_dinv);
+  if (ctx->mf) {
+    ph_begin(ctx, PH_BAND_LU);
+    CK(launch_mf_factor<T>(ctx->mfl, mfF, mfD, ctx->mf_tc, st));
+    ph_end(ctx, PH_BAND_LU);
+  } else {
+    ph_begin(ctx, PH_BAND_FILL);
+    CK(launch_band_fill<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->d_rowof, ctx->d_colidx, ctx->d_vals, band, 0, 0,
+                           st, nullptr));
+    ph_end(ctx, PH_BAND_FILL);
+    ph_begin(ctx, PH_BAND_LU);
+    CK(launch_band_lu<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->kl_max_osl, band, lslab, uslab, dinv, ctx->d_flags,
+                         ctx->flags_stride, ctx->d_epoch, ctx->d_status, st, nullptr,
+                         ctx->prec == TPNS_TF32_IR ? 1 : ctx->prec == TPNS_BF16_IR ? 2 : 0, ctx->lu_cl));
+    CK(launch_band_dinv<T>(ctx->d_sys, ctx->d_list_osl, nosl, ctx->nblk_max_osl, band, dinv, st, nullptr));
+    ph_end(ctx, PH_BAND_LU);
+  }
+  const int nband = (int)ctx->list_band.size();
+  auto solve_pass = [&]() -> tpns_status {
+    CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_band, nband, ctx->n_max_band, ctx->kmax_band, lslab, uslab, dinv,
+                            ctx->d_r, ctx->d_x, 1, ctx->d_done, ctx->d_status, st, nullptr, vwork));
+    if (ctx->mf)
+      CK(launch_mf_solve<T>(ctx->mfl, mfF, mfD, ctx->d_r, ctx->d_x, 1, ctx->d_done, reinterpret_cast<T*>(ctx->d_mf_y),
+                            reinterpret_cast<T*>(ctx->d_mf_d), reinterpret_cast<T*>(ctx->d_mf_upd), ctx->mf_m_max,
+                            st));
+    return TPNS_OK;
+  };
   // a8: solves with FP64-residual iterative refinement
   const bool fp64 = ctx->prec == TPNS_FP64;
   const int maxit = fp64 ? 2 : 12;
@@ -884,8 +1022,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
                      nullptr));
   ph_end(ctx, PH_RESIDUAL);
   ph_begin(ctx, PH_SOLVE);
-  CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, lslab, uslab, dinv,
-                          ctx->d_r, ctx->d_x, 1, ctx->d_done, ctx->d_status, st, nullptr, vwork));
+  TRY(solve_pass());
   ph_end(ctx, PH_SOLVE);
   for (int it = 0; it < maxit; ++it) {
     ph_begin(ctx, PH_RESIDUAL);
@@ -895,8 +1032,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
     ph_end(ctx, PH_RESIDUAL);
     if (it + 1 < maxit) {
       ph_begin(ctx, PH_SOLVE);
-      CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_local, nloc, ctx->n_max_local, ctx->kmax_local, lslab, uslab,
-                              dinv, ctx->d_r, ctx->d_x, 1, ctx->d_done, ctx->d_status, st, nullptr, vwork));
+      TRY(solve_pass());
       ph_end(ctx, PH_SOLVE);
     }
   }
@@ -978,9 +1114,18 @@ static tpns_status read_stats(tpns_ctx* ctx) {
     // each residual after a solve counts one iteration, so iters = solve passes this step
     const SysDev& S = ctx->hsys[s];
     passes += it[s];
-    bytes += (double)it[s] * ((double)S.n * (S.kl + S.ku) * tsz + (double)((S.n + 31) / 32) * 2048.0 * tsz +
-                              24.0 * S.n);
+    if (!(ctx->mf && s < ctx->nf))
+      bytes += (double)it[s] * ((double)S.n * (S.kl + S.ku) * tsz + (double)((S.n + 31) / 32) * 2048.0 * tsz +
+                                24.0 * S.n);
   }
+  if (ctx->mf)
+    for (int q = 0; q < ctx->nf; ++q) {
+      const MFSymbolic& M = ctx->probs[q]->mf;
+      const int s = ctx->sys_first[q];
+      double dv = 0;
+      for (const MFFront& F : M.fronts) dv += (double)((F.p + MF_NB - 1) / MF_NB) * 2 * MF_NB * MF_NB;
+      bytes += (double)it[s] * ((M.factor_entries + dv) * tsz + 24.0 * ctx->hsys[s].n);
+    }
   ctx->stats.last_ir_solves = passes;
   ctx->stats.last_solve_bytes = bytes;
   ctx->stats.step = ctx->step;
@@ -1172,13 +1317,15 @@ __global__ void csr_rowof_kernel(const int32_t* __restrict__ rowptr, int n, int3
 // Run the band solver on one system whose descriptors and scratch live at caller-chosen
 // device addresses (`sysd`: SysDev, `listd`: int 0, `vecs`: r, rel, relprev, done, iters,
 // status, flags).  The band and dinv buffers must hold n * (kl + ku + 1) and
-// ceil(n / 32) * 2048 elements of T.
+// ceil(n / 32) * 2048 elements of T; vwork holds n elements of T (the solve vector of a
+// system too large for shared memory).  Every return, failed or not, leaves the stream
+// synchronised, so no work of the call still touches the scratch afterwards.
 template <typename T>
 static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, const int32_t* colidx,
                                   const double* vals, const double* b, double* x, cudaStream_t st, SysDev* sysd,
-                                  int* listd, int32_t* rowof, T* band, T* dinv, T* lslab, T* uslab, double* r,
-                                  double* rel, double* relprev, int* done, int* iters, int* status, int* flags,
-                                  int epoch, double* relres_out, std::string& err) {
+                                  int* listd, int32_t* rowof, T* band, T* dinv, T* lslab, T* uslab, T* vwork,
+                                  double* r, double* rel, double* relprev, int* done, int* iters, int* status,
+                                  int* flags, int epoch, double* relres_out, std::string& err) {
   // the residual's partial sums follow the vector r; its ticket follows the status word
   double* partial = r + n + 2;
   int* ticket = status + 1;
@@ -1187,6 +1334,7 @@ static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, 
     cudaError_t e_ = (call);                                                \
     if (e_ != cudaSuccess) {                                                \
       err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+      cudaStreamSynchronize(st);                                            \
       return TPNS_EDEVICE;                                                  \
     }                                                                       \
   } while (0)
@@ -1220,12 +1368,14 @@ static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, 
   CKS(cudaMemsetAsync(ticket, 0, sizeof(int), st));
   CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, partial, ticket, tol, 1,
                       st, nullptr));
-  CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, lslab, uslab, dinv, b, x, 0, nullptr, status, st, nullptr));
+  CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, lslab, uslab, dinv, b, x, 0, nullptr, status, st, nullptr,
+                           vwork));
   for (int it = 0; it < maxit; ++it) {
     CKS(launch_residual(sysd, listd, 1, rowptr, colidx, vals, b, x, r, rel, relprev, done, iters, partial, ticket, tol,
                         0, st, nullptr));
     if (it + 1 < maxit)
-      CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, lslab, uslab, dinv, r, x, 1, done, status, st, nullptr));
+      CKS(launch_band_solve<T>(sysd, listd, 1, n, kmax, lslab, uslab, dinv, r, x, 1, done, status, st, nullptr,
+                               vwork));
   }
   int hst = 0;
   double hrel = 0;
@@ -1245,11 +1395,13 @@ static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, 
 #undef CKS
 }
 
-static int g_solve_epoch = 0;
+// epoch tag of the standalone solves' panel flags (shared by all host threads)
+static std::atomic<int> g_solve_epoch{0};
 
 static tpns_status band_solve_check(int32_t n, int32_t kl, int32_t ku, const int32_t* rowptr, const int32_t* colidx,
                                     const double* vals, const double* b, double* x, tpns_precision precision) {
-  if (n <= 0 || kl < 0 || ku < 1 || kl + LU_NB > 512 || !rowptr || !colidx || !vals || !b || !x) {
+  if (n <= 0 || kl < 0 || ku < 1 || kl + LU_NB > 512 || ku + LU_NB > 512 || !rowptr || !colidx || !vals || !b ||
+      !x) {
     g_err = "invalid band solve arguments";
     return TPNS_EINVAL;
   }
@@ -1293,7 +1445,30 @@ extern "C" {
 tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, const tpns_partition_desc* part,
                         const tpns_data_desc* data, double dt, tpns_precision precision, size_t hbm_budget_bytes,
                         void* cuda_stream, tpns_ctx** out) {
+  return tpns_create_ex(mesh, params, part, data, dt, precision, hbm_budget_bytes, cuda_stream, nullptr, out);
+}
+
+static bool read_options(const tpns_options* o, tpns_options& opt) {
+  opt = tpns_options{};
+  if (o) opt = *o;
+  if (opt.local_factor != TPNS_FACTOR_MULTIFRONTAL && opt.local_factor != TPNS_FACTOR_BAND) return false;
+  if (opt.mf_leaf < 0 || opt.mf_ctas < 0) return false;
+  if (opt.mf_leaf == 0) opt.mf_leaf = 96;
+  if (opt.mf_leaf < 8) return false;
+  return true;
+}
+
+tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params, const tpns_partition_desc* part,
+                           const tpns_data_desc* data, double dt, tpns_precision precision, size_t hbm_budget_bytes,
+                           void* cuda_stream, const tpns_options* options, tpns_ctx** out) {
   g_err.clear();
+  const auto t_create = std::chrono::steady_clock::now();
+  tpns_options opt;
+  if (!read_options(options, opt)) { g_err = "invalid options"; return TPNS_EINVAL; }
+  if (opt.local_factor == TPNS_FACTOR_MULTIFRONTAL && precision == TPNS_BF16_IR) {
+    g_err = "TPNS_BF16_IR is available with the band factorisation only";
+    return TPNS_EINVAL;
+  }
   if (!out) { g_err = "out is NULL"; return TPNS_EINVAL; }
   *out = nullptr;
   if (!mesh || !params || !part || !data) { g_err = "NULL argument"; return TPNS_EINVAL; }
@@ -1321,6 +1496,10 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   }
   ctx->prec = precision;
   ctx->dt = dt;
+  ctx->mf = opt.local_factor == TPNS_FACTOR_MULTIFRONTAL;
+  ctx->mf_leaf = opt.mf_leaf;
+  ctx->mf_tc = precision != TPNS_FP64 && !opt.mf_cuda_cores;
+  ctx->mfl.grid_cap = opt.mf_ctas;
   Phys& P = ctx->phys;
   P.nu = params->nu; P.eta = params->eta; P.rho = params->rho; P.mu = params->mu; P.alpha = params->alpha;
   P.sigma = params->sigma; P.sigma_star = params->sigma_star;
@@ -1330,7 +1509,7 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   tpns_status s = build_ctx(ctx, *mesh, *part, hbm_budget_bytes);
   // the tuning runs before the Darcy factors are formed: it overwrites the local bands, and
   // setup_factors then writes the Darcy bands, slabs and inverses from scratch
-  if (s == TPNS_OK) s = ctx->prec == TPNS_FP64 ? tune_lu<double>(ctx) : tune_lu<float>(ctx);
+  if (s == TPNS_OK && !ctx->mf) s = ctx->prec == TPNS_FP64 ? tune_lu<double>(ctx) : tune_lu<float>(ctx);
   if (s == TPNS_OK) s = setup_factors(ctx);
   if (s != TPNS_OK) {
     g_err = ctx->err;
@@ -1341,19 +1520,47 @@ tpns_status tpns_create(const tpns_mesh_desc* mesh, const tpns_params* params, c
   ctx->stats.n_local_systems = (int64_t)ctx->list_local.size();
   ctx->stats.device_bytes = (int64_t)ctx->bytes;
   ctx->stats.band_lu_flops = ctx->lu_flops_step;
-  ctx->stats.lu_cluster_ctas = ctx->lu_cl;
+  ctx->stats.lu_cluster_ctas = ctx->mf ? 0 : ctx->lu_cl;
+  for (int q = 0; q < ctx->nf; ++q) {
+    const Problem& P = *ctx->probs[q];
+    ctx->stats.oseen_unknowns += P.n;
+    ctx->stats.oseen_nnz += (int64_t)P.colidx.size();
+    ctx->stats.oseen_elements += P.ne;
+    if (ctx->mf) ctx->stats.mf_fronts += (int64_t)P.mf.fronts.size();
+    if (!ctx->mf) {
+      for (int j = 0; j < P.n; ++j) {
+        const double l = std::min(P.kl, P.n - 1 - j), u = std::min(P.ku, P.n - 1 - j);
+        ctx->stats.factor_entries += 1 + l + u;
+      }
+    }
+  }
+  if (ctx->mf) ctx->stats.factor_entries = ctx->mf_factor_entries;
+  for (int q = ctx->nf + 1; q < ctx->nf + 1 + ctx->np; ++q) {
+    ctx->stats.darcy_unknowns += 3 * (int64_t)ctx->probs[q]->n;
+    ctx->stats.darcy_elements += ctx->probs[q]->ne;
+  }
+  ctx->stats.create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_create).count();
   *out = ctx;
   return TPNS_OK;
 }
 
 tpns_status tpns_layout_create(const tpns_mesh_desc* mesh, const tpns_partition_desc* part, tpns_ctx** out) {
+  return tpns_layout_create_ex(mesh, part, nullptr, out);
+}
+
+tpns_status tpns_layout_create_ex(const tpns_mesh_desc* mesh, const tpns_partition_desc* part,
+                                  const tpns_options* options, tpns_ctx** out) {
   g_err.clear();
   if (!out || !mesh || !part) { g_err = "NULL argument"; return TPNS_EINVAL; }
   *out = nullptr;
+  tpns_options opt;
+  if (!read_options(options, opt)) { g_err = "invalid options"; return TPNS_EINVAL; }
   tpns_ctx* ctx = new (std::nothrow) tpns_ctx();
   if (!ctx) return TPNS_ENOMEM;
   ctx->host_only = true;
-  std::string msg = build_layout(*mesh, *part, ctx->L);
+  ctx->mf = opt.local_factor == TPNS_FACTOR_MULTIFRONTAL;
+  ctx->mf_leaf = opt.mf_leaf;
+  std::string msg = build_layout(*mesh, *part, ctx->L, ctx->mf ? ctx->mf_leaf : 0);
   if (!msg.empty()) {
     g_err = msg;
     delete ctx;
@@ -1390,12 +1597,13 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
   void* dinv = get((size_t)nblk * 2 * LU_NB * LU_NB * tsz);
   void* lsl = get((size_t)nblk * LU_NB * kl * tsz);
   void* usl = get((size_t)nblk * LU_NB * ku * tsz);
+  void* vw = get((size_t)n * tsz);
   SysDev* sysd = (SysDev*)get(sizeof(SysDev));
   int* ints = (int*)get(sizeof(int) * (6 + 2 * (size_t)nblk));
   int32_t* rowof = (int32_t*)get(sizeof(int32_t) * (size_t)std::max(nnz, 1));
   double* dbl = (double*)get(sizeof(double) * ((size_t)n + 2 + 2 * RES_CHUNKS));
   tpns_status out;
-  if (!band || !dinv || !lsl || !usl || !sysd || !ints || !rowof || !dbl) {
+  if (!band || !dinv || !lsl || !usl || !vw || !sysd || !ints || !rowof || !dbl) {
     g_err = "cudaMalloc failed";
     out = TPNS_ENOMEM;
   } else {
@@ -1411,12 +1619,12 @@ tpns_status tpns_band_solve(int32_t n, int32_t kl, int32_t ku, const int32_t* ro
     const int epoch = ++g_solve_epoch;
     if (precision == TPNS_FP64)
       out = band_solve_run<double>(n, kl, ku, rowptr, colidx, vals, b, x, st, sysd, listd, rowof, (double*)band,
-                                   (double*)dinv, (double*)lsl, (double*)usl, r, rel, relprev, done, iters, status,
-                                   flags, epoch, relres_out, g_err);
+                                   (double*)dinv, (double*)lsl, (double*)usl, (double*)vw, r, rel, relprev, done,
+                                   iters, status, flags, epoch, relres_out, g_err);
     else
       out = band_solve_run<float>(n, kl, ku, rowptr, colidx, vals, b, x, st, sysd, listd, rowof, (float*)band,
-                                  (float*)dinv, (float*)lsl, (float*)usl, r, rel, relprev, done, iters, status, flags,
-                                  epoch, relres_out, g_err);
+                                  (float*)dinv, (float*)lsl, (float*)usl, (float*)vw, r, rel, relprev, done, iters,
+                                  status, flags, epoch, relres_out, g_err);
   }
   cudaStreamSynchronize(st);
   for (void* p : mem) cudaFree(p);
@@ -1452,6 +1660,7 @@ tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int
   const size_t o_dinv = take((size_t)nblk * 2 * LU_NB * LU_NB * tsz);
   const size_t o_lsl = take((size_t)nblk * LU_NB * kl * tsz);
   const size_t o_usl = take((size_t)nblk * LU_NB * ku * tsz);
+  const size_t o_vw = take((size_t)n * tsz);
   const size_t o_sys = take(sizeof(SysDev));
   const size_t o_ints = take(sizeof(int) * (6 + 2 * (size_t)nblk));
   const size_t o_rowof = take(sizeof(int32_t) * (size_t)std::max(nnz, 1));
@@ -1474,13 +1683,43 @@ tpns_status tpns_band_solve_noalloc(int32_t n, int32_t kl, int32_t ku, const int
                                   ints, reinterpret_cast<int32_t*>(base + o_rowof),
                                   reinterpret_cast<double*>(base + o_band), reinterpret_cast<double*>(base + o_dinv),
                                   reinterpret_cast<double*>(base + o_lsl), reinterpret_cast<double*>(base + o_usl),
-                                  dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2, ints + 3, ints + 5, epoch, relres_out,
+                                  reinterpret_cast<double*>(base + o_vw), dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2, ints + 3, ints + 5, epoch, relres_out,
                                   g_err);
   return band_solve_run<float>(n, kl, ku, rowptr, colidx, vals, b, x, st, reinterpret_cast<SysDev*>(base + o_sys), ints,
                                reinterpret_cast<int32_t*>(base + o_rowof), reinterpret_cast<float*>(base + o_band),
                                reinterpret_cast<float*>(base + o_dinv), reinterpret_cast<float*>(base + o_lsl),
-                               reinterpret_cast<float*>(base + o_usl), dbl, dbl + n, dbl + n + 1, ints + 1, ints + 2,
+                               reinterpret_cast<float*>(base + o_usl), reinterpret_cast<float*>(base + o_vw), dbl,
+                               dbl + n, dbl + n + 1, ints + 1, ints + 2,
                                ints + 3, ints + 5, epoch, relres_out, g_err);
+}
+
+tpns_status tpns_debug_fronts(const tpns_ctx* ctx, int32_t j, int32_t what, int32_t* dst, size_t* n) {
+  if (!ctx || !n || !ctx->mf || j < 0 || j >= (int)ctx->L.fluid.size()) return TPNS_EINVAL;
+  const MFSymbolic& M = ctx->L.fluid[j].mf;
+  std::vector<int32_t> v;
+  switch (what) {
+    case 0: v = {(int32_t)M.fronts.size(), M.nlevels}; break;
+    case 1:
+      for (const MFFront& F : M.fronts) {
+        const int32_t r[7] = {F.m, F.p, F.level, F.parent, F.nchild, F.child[0], F.child[1]};
+        v.insert(v.end(), r, r + 7);
+      }
+      break;
+    case 2: for (const MFFront& F : M.fronts) v.insert(v.end(), F.rows.begin(), F.rows.end()); break;
+    case 3: for (const MFFront& F : M.fronts) v.insert(v.end(), F.relmap.begin(), F.relmap.end()); break;
+    case 4: for (const MFFront& F : M.fronts) v.insert(v.end(), F.col_ptr.begin(), F.col_ptr.end()); break;
+    case 5: for (const MFFront& F : M.fronts) v.insert(v.end(), F.orig_k.begin(), F.orig_k.end()); break;
+    case 6: for (const MFFront& F : M.fronts) v.insert(v.end(), F.orig_i.begin(), F.orig_i.end()); break;
+    case 7: for (const MFFront& F : M.fronts) v.insert(v.end(), F.col_child.begin(), F.col_child.end()); break;
+    case 8: v = M.order; break;
+    default: return TPNS_EINVAL;
+  }
+  if (dst) {
+    if (*n < v.size()) return TPNS_EINVAL;
+    std::copy(v.begin(), v.end(), dst);
+  }
+  *n = v.size();
+  return TPNS_OK;
 }
 
 tpns_status tpns_debug_values(tpns_ctx* ctx, int32_t j, int32_t field, double* vals, double* rhs) {

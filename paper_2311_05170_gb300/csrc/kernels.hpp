@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "device.cuh"
+#include "mf.hpp"
 
 namespace tpns {
 
@@ -64,6 +65,20 @@ cudaError_t launch_residual(const SysDev* sys, const int* sys_list, int nsys, co
                             const double* x, double* r, double* rel, double* rel_prev, int* done,
                             int* iters, double* partial, int* ticket, double tol, int first,
                             cudaStream_t st, const int* skip);
+
+// ---- multifrontal LU of the local Oseen systems (kernels_mf.cu); `T` = float or double
+// Factor every front of every system of L in one persistent launch (dataflow over the
+// elimination trees).  tc (float fronts): trailing updates on the tensor cores (tcgen05,
+// split TF32).
+template <typename T>
+cudaError_t launch_mf_factor(const MFLaunch& L, T* F, T* dinv, int tc, cudaStream_t st);
+// One refinement pass: x (+)= (LU)^{-1} r for every system of L whose done flag is clear.
+// yv, dv: vectors of T at the systems' x offsets; upd: update vectors of the fronts.
+template <typename T>
+cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const double* r, double* x, int accumulate,
+                            const int* done, T* yv, T* dv, T* upd, int m_max, cudaStream_t st);
+template <typename T>
+size_t mf_factor_smem(bool tc);
 
 // ---- assembly (kernels_assemble.cu)
 struct AsmArgs {

@@ -1,0 +1,833 @@
+// Multifrontal LU and triangular solves of the local Oseen systems (Algorithm 3 Step 3(2),
+// eq. uclocalFully), scheduled as a dataflow over the elimination trees of all systems.
+//
+// One persistent launch factors every front of every system.  The fronts are numbered in
+// level order (all leaves first); each CTA takes the next front from an atomic counter,
+// waits until the front's children are finished (a flag per front, tagged with the
+// launch's epoch, bounded wait) and factors the whole front itself.  A CTA only waits for
+// fronts that CTAs which started before it have taken, so no launch geometry or
+// co-residency is needed for progress, and a parent starts as soon as its own children
+// are done (no level barriers).  Per front (dense, column-major, unpivoted):
+//   assembly   every column: zero, the CSR values the front owns, then the Schur
+//              complements of the children added column by column (extend-add), one warp
+//              per column, children in a fixed order: no atomics, deterministic;
+//   panel k    warp 0 factors the 32 x 32 pivot block (shuffles), two warps form the
+//              inverses of its unit-lower and upper triangles, then all threads form
+//              L21 = A21 U11^{-1} and U12 = L11^{-1} A12 in place;
+//   update k   A22 -= L21 U12.  FP32 fronts: 256 x 256 chunks; the threads write both
+//              operands into shared memory as core-matrix tiles with every value split into
+//              two TF32 parts, one thread issues tcgen05.mma kind::tf32 (hi*hi + hi*lo +
+//              lo*hi, FP32 accumulation) into four 128 x 128 tensor-memory accumulators, and
+//              all warps read them back with tcgen05.ld and subtract them from the front.
+//              FP64 fronts (and FP32 fronts on request) use a CUDA-core tile product.
+// The Schur complement left in a front's trailing block is consumed by its parent.
+//
+// Solves (one pass of iterative refinement), one launch with the same scheduling: the
+// forward tasks in level order (a front waits for its children: right-hand side plus the
+// children's update vectors, the pivot blocks through the inverses of L11's diagonal
+// blocks, then the L columns below), then the backward tasks in reverse order (a front
+// waits for its own forward task and its parent: U12 against the ancestors' correction,
+// then the inverses of U11's diagonal blocks), adding the correction to x.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <type_traits>
+
+#include "kernels.hpp"
+#include "mf.hpp"
+
+namespace tpns {
+namespace {
+
+constexpr int MF_THREADS = 256;
+constexpr int MF_WAIT_LIMIT = 1 << 22;
+constexpr int MF_CN = 2 * MF_TILE;         // columns of one tensor-core update chunk (rows: MF_TILE)
+constexpr int MF_TMEM_COLS = MF_CN;        // one 128 x 256 FP32 accumulator
+constexpr int DS = MF_NB + 1;              // padded stride of the 32 x 32 shared tiles
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mb_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mb_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false if the limit was reached
+__device__ __forceinline__ bool mb_wait(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < MF_WAIT_LIMIT; ++it)
+    if (mb_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// bounded wait for a flag to reach value v; false if the limit was reached
+__device__ __forceinline__ bool wait_flag(const int* p, int v) {
+  for (int it = 0; ld_acquire(p) != v; ++it) {
+    if (it > MF_WAIT_LIMIT) return false;
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// tensor memory and the fifth-generation tensor core
+__device__ __forceinline__ void tm_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma_tf32(uint32_t dtm, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns of tensor memory, one lane per thread (the
+// registers are valid after tm_wait_ld)
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major: 8-row x 16-byte core matrices;
+// lbo = byte distance of core matrices along K, sbo = along M/N (8-row groups).
+__device__ __forceinline__ uint64_t sm_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 256.
+constexpr uint32_t MF_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(MF_CN >> 3) << 17) |
+                              ((uint32_t)(MF_TILE >> 4) << 24);
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+// offset (elements) of (row, k) in packed rows x 32 operand tiles: core matrices of 8 rows
+// x 4 values; the K-chunks of a row group are adjacent (128 bytes apart), row groups follow
+// each other (1024 bytes apart)
+__device__ __forceinline__ int pack_idx(int r, int k) { return ((r >> 3) * 8 + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
+
+__device__ __forceinline__ bool bad_val(float v) { return !(fabsf(v) > 0.0f) || !(fabsf(v) < INFINITY); }
+__device__ __forceinline__ bool bad_val(double v) { return !(fabs(v) > 0.0) || !(fabs(v) < (double)INFINITY); }
+
+// The phases of a front are separate (not inlined) device functions: each then keeps its
+// register arrays in registers instead of sharing one allocation with every other phase.
+
+// ---------------------------------------------------------------- pivot block
+template <typename T>
+struct alignas(16) PanelSmem {
+  T D[MF_NB][DS];      // pivot block, then its LU (unit L below, U on and above the diagonal)
+  T Li[MF_NB][DS];     // inverse of the unit-lower triangle
+  T Ui[MF_NB][DS];     // inverse of the upper triangle
+  T R[MF_NB];          // reciprocals of the pivots
+};
+
+// Factor the pivot block of rows / columns k0 .. k0 + kb - 1 (padded to 32 with the
+// identity) and form both triangular inverses.  All threads call; a zero or non-finite
+// pivot sets bit 0 of *s_flag.  Warp 0 holds one column per lane, eliminates with
+// shuffles and keeps the pivots' reciprocals, so the inverses need no division.
+template <typename T>
+__device__ __noinline__ void pivot_block(PanelSmem<T>& S, const T* __restrict__ F, int ld, int k0, int kb,
+                                         int* s_flag) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    T a[MF_NB];   // lane j holds column j
+    const T* col = F + (int64_t)(k0 + (lane < kb ? lane : 0)) * ld + k0;
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i) a[i] = ldcg(col + (i < kb ? i : 0));
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i)
+      if (i >= kb || lane >= kb) a[i] = (i == lane) ? T(1) : T(0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < MF_NB; ++k) {
+      const T piv = __shfl_sync(0xffffffffu, a[k], k);
+      if (k < kb) bad |= bad_val(piv);
+      const T rp = T(1) / piv;
+      if (lane == 0) S.R[k] = rp;
+      // lane k turns its column into the multipliers l_i; lanes right of it apply them
+#pragma unroll
+      for (int i = k + 1; i < MF_NB; ++i) {
+        const T li = __shfl_sync(0xffffffffu, a[i], k) * rp;
+        const T upd = a[i] - li * a[k];
+        a[i] = lane == k ? li : (lane > k ? upd : a[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i) S.D[i][lane] = a[i];
+    if (lane == 0 && bad) atomicOr(s_flag, 1);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // column `lane` of U^{-1}, right-looking: x_i = s_i / u_ii, then s_k -= u_ki x_i (k < i)
+    T s[MF_NB];
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i) s[i] = (i == lane) ? T(1) : T(0);
+#pragma unroll
+    for (int i = MF_NB - 1; i >= 0; --i) {
+      s[i] = s[i] * S.R[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s[k] -= S.D[k][i] * s[i];
+    }
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i) S.Ui[i][lane] = s[i];
+  } else if (warp == 1) {
+    // column `lane` of L^{-1} (unit diagonal), right-looking
+    T s[MF_NB];
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i) s[i] = (i == lane) ? T(1) : T(0);
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i) {
+#pragma unroll
+      for (int k = i + 1; k < MF_NB; ++k) s[k] -= S.D[k][i] * s[i];
+    }
+#pragma unroll
+    for (int i = 0; i < MF_NB; ++i) S.Li[i][lane] = s[i];
+  }
+  __syncthreads();
+}
+
+// L rows r in [k1, m): F[r, k0:k0+kb] <- F[r, k0:k0+kb] U11^{-1}; U columns c in [k1, m):
+// F[k0:k0+kb, c] <- L11^{-1} F[k0:k0+kb, c].  One thread per row or column.
+template <typename T>
+__device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, int ld, int m, int k0, int kb, int k1) {
+  const int rest = m - k1;
+  for (int q = threadIdx.x; q < 2 * rest; q += blockDim.x) {
+    const bool row = q < rest;
+    const int idx = k1 + (row ? q : q - rest);
+    T a[MF_NB];
+    // every load from a valid address first (clamped), masked afterwards
+    const T* base = row ? F + (int64_t)k0 * ld + idx : F + (int64_t)idx * ld + k0;
+    const int64_t step = row ? ld : 1;
+#pragma unroll
+    for (int c = 0; c < MF_NB; ++c) a[c] = ldcg(base + (c < kb ? c : 0) * step);
+#pragma unroll
+    for (int c = 0; c < MF_NB; ++c)
+      if (c >= kb) a[c] = T(0);
+    T o[MF_NB];
+#pragma unroll
+    for (int c2 = 0; c2 < MF_NB; ++c2) {
+      T s = T(0);
+      if (row) {
+#pragma unroll
+        for (int c = 0; c <= c2; ++c) s += a[c] * S.Ui[c][c2];
+      } else {
+#pragma unroll
+        for (int c = 0; c <= c2; ++c) s += S.Li[c2][c] * a[c];
+      }
+      o[c2] = s;
+    }
+    if (row) {
+#pragma unroll
+      for (int c2 = 0; c2 < MF_NB; ++c2)
+        if (c2 < kb) F[(int64_t)(k0 + c2) * ld + idx] = o[c2];
+    } else {
+#pragma unroll
+      for (int c2 = 0; c2 < MF_NB; ++c2)
+        if (c2 < kb) F[(int64_t)idx * ld + k0 + c2] = o[c2];
+    }
+  }
+  __syncthreads();
+}
+
+// CUDA-core tile update: F[r0:r0+128, c0:c0+128] -= L21 U12 (K = kb), reading the panel
+// from the front.  Thread (tx, ty) owns rows tx + 16 a and columns ty + 16 b.
+template <typename T>
+__device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, int k0, int kb, int r0, int c0, T* As, T* Bs) {
+  constexpr int W = MF_TILE + 4;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int u = 0; u < MF_NB * MF_TILE / MF_THREADS; ++u) {
+    const int q = tid + u * MF_THREADS;
+    const int k = q / MF_TILE, r = q % MF_TILE;
+    As[k * W + r] = (k < kb && r0 + r < m) ? ldcg(F + (int64_t)(k0 + k) * ld + r0 + r) : T(0);
+    const int c = q / MF_NB, kk = q % MF_NB;
+    Bs[kk * W + c] = (kk < kb && c0 + c < m) ? ldcg(F + (int64_t)(c0 + c) * ld + k0 + kk) : T(0);
+  }
+  __syncthreads();
+  T acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = T(0);
+  for (int k = 0; k < kb; ++k) {
+    T av[8], bv[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) av[a] = As[k * W + tx + 16 * a];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) bv[b] = Bs[k * W + ty + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] += av[a] * bv[b];
+  }
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int c = c0 + ty + 16 * b;
+    if (c >= m) continue;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int r = r0 + tx + 16 * a;
+      if (r < m) {
+        T* p = F + (int64_t)c * ld + r;
+        *p = ldcg(p) - acc[a][b];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Shared memory of the FP32 tensor-core path: operand chunks (A = 128 rows of L21, B = 256
+// columns of U12, 32 values each, TF32 hi and lo parts), the pivot block, barrier, TMEM
+// address.  About 110 KB: two CTAs per SM, each with half of the SM's tensor memory.
+struct TcSmem {
+  float Ahi[MF_TILE * MF_NB], Alo[MF_TILE * MF_NB], Bhi[MF_CN * MF_NB], Blo[MF_CN * MF_NB];
+  PanelSmem<float> P;
+  uint64_t bar;
+  uint32_t tmem;
+};
+
+// Pack rows (or columns) [l0, l0 + n) of the panel into core-matrix tiles, each value split
+// into TF32 hi and lo parts: row: L21 rows r0 + l (values F[r, k0 + c]); column: U12 columns
+// (values F[k0 + c, c0 + l]).  Entries past `valid` or kb are zero.
+__device__ __forceinline__ void pack_panel(const float* __restrict__ F, int ld, int k0, int kb, int first, int valid,
+                                           bool row, int l, float* hi, float* lo) {
+  const bool ok = l < valid;
+  const int li = ok ? l : 0;
+  const float* base = row ? F + (int64_t)k0 * ld + first + li : F + (int64_t)(first + li) * ld + k0;
+  const int64_t step = row ? ld : 1;
+  float v[MF_NB];
+#pragma unroll
+  for (int c = 0; c < MF_NB; ++c) v[c] = ldcg(base + (c < kb ? c : 0) * step);
+#pragma unroll
+  for (int c = 0; c < MF_NB; ++c)
+    if (!ok || c >= kb) v[c] = 0.f;
+#pragma unroll
+  for (int c4 = 0; c4 < MF_NB; c4 += 4) {
+    float4 h, o;
+    h.x = tf32_rn(v[c4]); o.x = tf32_rn(v[c4] - h.x);
+    h.y = tf32_rn(v[c4 + 1]); o.y = tf32_rn(v[c4 + 1] - h.y);
+    h.z = tf32_rn(v[c4 + 2]); o.z = tf32_rn(v[c4 + 2] - h.z);
+    h.w = tf32_rn(v[c4 + 3]); o.w = tf32_rn(v[c4 + 3] - h.w);
+    *reinterpret_cast<float4*>(hi + pack_idx(l, c4)) = h;
+    *reinterpret_cast<float4*>(lo + pack_idx(l, c4)) = o;
+  }
+}
+
+// One thread: the twelve products of a chunk (four K-steps of 8, each hi*hi + hi*lo + lo*hi),
+// then a commit of their completion to the mbarrier.
+__device__ __noinline__ void issue_chunk(const TcSmem& S, uint64_t* bar) {
+  const uint32_t ah = su32(S.Ahi), al = su32(S.Alo), bh = su32(S.Bhi), bl = su32(S.Blo);
+#pragma unroll 1
+  for (int kk = 0; kk < MF_NB / 8; ++kk) {
+    const uint32_t o = kk * 256;   // 8 TF32 values = two 16-byte core matrices along K
+    tc_mma_tf32(S.tmem, sm_desc(ah + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, kk > 0);
+    tc_mma_tf32(S.tmem, sm_desc(ah + o, 128, 1024), sm_desc(bl + o, 128, 1024), MF_IDESC, 1);
+    tc_mma_tf32(S.tmem, sm_desc(al + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, 1);
+  }
+  tc_commit(bar);
+}
+
+// Trailing update F[k1:m, k1:m] -= L21 U12 of one pivot block on the tensor cores, in
+// chunks of 128 rows x 256 columns (one accumulator in tensor memory).
+__device__ __noinline__ void update_tc(TcSmem& S, float* __restrict__ F, int ld, int m, int k0, int kb, int k1,
+                                       unsigned& ph, int* s_flag) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int c0 = k1; c0 < m; c0 += MF_CN) {
+    const int nc = min(MF_CN, m - c0);
+    for (int r0 = k1; r0 < m; r0 += MF_TILE) {
+      const int nr = min(MF_TILE, m - r0);
+      // operands: A rows once per chunk row, B columns once per chunk column
+      if (tid < MF_TILE) pack_panel(F, ld, k0, kb, r0, nr, true, tid, S.Ahi, S.Alo);
+      if (r0 == k1) pack_panel(F, ld, k0, kb, c0, nc, false, tid, S.Bhi, S.Blo);
+      // the tensor core reads shared memory through the async proxy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_before();
+      __syncthreads();
+      tc_after();
+      if (tid == 0) issue_chunk(S, &S.bar);
+      if (!mb_wait(&S.bar, ph) && lane == 0) atomicOr(s_flag, 2);
+      ph ^= 1u;
+      tc_after();
+      // epilogue: warp w reads accumulator lanes 32 (w % 4) .., columns 128 (w / 4) ..
+      const int q4 = warp & 3, hcol = warp >> 2;
+      const int r = r0 + 32 * q4 + lane;
+      const int cb = c0 + 128 * hcol;
+      if (r0 + 32 * q4 < m && cb < m) {   // warp-uniform
+        const uint32_t base = S.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(128 * hcol);
+        const int rr = r < m ? r : m - 1;
+#pragma unroll 1
+        for (int h16 = 0; h16 < 8; ++h16) {
+          const int cb2 = cb + 16 * h16;
+          if (cb2 >= m) break;
+          uint32_t d[16];
+          tm_ld16(base + (uint32_t)(16 * h16), d);
+          // the front's current values, all loads in flight together (clamped addresses)
+          float f[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) f[c] = ldcg(F + (int64_t)(cb2 + c < m ? cb2 + c : m - 1) * ld + rr);
+          tm_wait_ld();
+          if (r < m) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              if (cb2 + c < m) F[(int64_t)(cb2 + c) * ld + r] = f[c] - __uint_as_float(d[c]);
+          }
+        }
+      }
+      tc_before();
+      __syncthreads();
+      tc_after();
+    }
+  }
+}
+
+// ---------------------------------------------------------------- factorisation
+struct MFArgs {
+  const MFSysDev* sys;
+  const MFFrontDev* fronts;
+  int nfront;
+  const int32_t* relmap;
+  const int64_t* colptr;
+  const int32_t* orig_k;
+  const int32_t* orig_ij;   // row | column << 16 in the front
+  const double* vals;
+  int* status;
+  int* sched;   // [0] task counter, [1] finished CTAs, [2] epoch
+  int* flag;    // per front: epoch when factored
+};
+
+// Assemble a front in three passes over all of its entries, separated by barriers: zero,
+// the CSR values it owns (distinct positions), then the Schur complement of each child in
+// turn (distinct positions within one child), so the sums do not depend on scheduling.
+template <typename T>
+__device__ __noinline__ void assemble_front(const MFArgs& A, const MFFrontDev& Fd, T* __restrict__ Fall, const double* vals) {
+  const int tid = threadIdx.x;
+  T* F = Fall + Fd.f_off;
+  const int m = Fd.m, ld = Fd.ld;
+  {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int E = sizeof(V) / sizeof(T);
+    V z;
+    memset(&z, 0, sizeof(V));
+    V* Fv = reinterpret_cast<V*>(F);
+    const int nv = ld * m / E;
+    for (int q = tid; q < nv; q += MF_THREADS) Fv[q] = z;
+  }
+  __syncthreads();
+  {
+    const int64_t b = A.colptr[Fd.colptr_off], e = A.colptr[Fd.colptr_off + m];
+    for (int64_t q0 = b + tid; q0 < e; q0 += 4 * MF_THREADS) {
+      int32_t ij[4];
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t q = q0 + (int64_t)u * MF_THREADS;
+        ij[u] = q < e ? A.orig_ij[q] : -1;
+        v[u] = q < e ? vals[A.orig_k[q]] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ij[u] >= 0) F[(int64_t)(ij[u] >> 16) * ld + (ij[u] & 0xFFFF)] = (T)v[u];
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < Fd.nchild; ++c) {
+    const MFFrontDev& C = A.fronts[c == 0 ? Fd.child0 : Fd.child1];
+    const int qc = C.m - C.p;
+    const T* src = Fall + C.f_off + (int64_t)C.p * C.ld + C.p;
+    const int32_t* rm = A.relmap + C.relmap_off;
+    const int tot = qc * qc;
+    for (int q0 = tid; q0 < tot; q0 += 4 * MF_THREADS) {
+      T v[4];
+      int dst[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * MF_THREADS;
+        dst[u] = -1;
+        v[u] = T(0);
+        if (q < tot) {
+          const int ic = q % qc, jc = q / qc;
+          v[u] = ldcg(src + (int64_t)jc * C.ld + ic);
+          dst[u] = rm[jc] * ld + rm[ic];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (dst[u] >= 0) F[dst[u]] += v[u];
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int next_task(int* sched, int* s_task) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_task = atomicAdd(&sched[0], 1);
+  __syncthreads();
+  return *s_task;
+}
+
+// the last CTA to finish resets the task counter and advances the epoch for the next launch
+__device__ __forceinline__ void finish_launch(int* sched) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&sched[1], 1) == (int)gridDim.x - 1) {
+      atomicExch(&sched[0], 0);
+      atomicExch(&sched[1], 0);
+      __threadfence();
+      atomicAdd(&sched[2], 1);
+    }
+  }
+}
+
+template <typename T, bool TC>
+__global__ void __launch_bounds__(MF_THREADS, 1)
+    mf_factor_kernel(MFArgs A, T* __restrict__ Fall, T* __restrict__ dinv) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ int s_task, s_flag;
+  const int tid = threadIdx.x;
+  TcSmem& TS = *reinterpret_cast<TcSmem*>(smem_raw);
+  PanelSmem<T>* Pp;
+  T* As = nullptr;
+  if constexpr (TC) {
+    Pp = reinterpret_cast<PanelSmem<T>*>(&TS.P);
+  } else {
+    As = reinterpret_cast<T*>(smem_raw);
+    Pp = reinterpret_cast<PanelSmem<T>*>(smem_raw + (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T));
+  }
+  PanelSmem<T>& P = *Pp;
+  const int epoch = ld_acquire(&A.sched[2]);
+  unsigned ph = 0;
+  if constexpr (TC) {
+    if (tid == 0) {
+      mb_init(&TS.bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((tid >> 5) == 0) tm_alloc(&TS.tmem, MF_TMEM_COLS);
+    tc_before();
+    __syncthreads();
+    tc_after();
+  }
+  for (;;) {
+    const int f = next_task(A.sched, &s_task);
+    if (f >= A.nfront) break;
+    const MFFrontDev& Fd = A.fronts[f];
+    const MFSysDev& S = A.sys[Fd.sys];
+    if (tid == 0) {
+      s_flag = 0;
+      if (Fd.nchild > 0 && !wait_flag(&A.flag[Fd.child0], epoch)) s_flag |= 4;
+      if (Fd.nchild > 1 && !wait_flag(&A.flag[Fd.child1], epoch)) s_flag |= 4;
+    }
+    __syncthreads();
+    assemble_front<T>(A, Fd, Fall, A.vals + S.val_off);
+    T* F = Fall + Fd.f_off;
+    for (int k0 = 0, kk = 0; k0 < Fd.p; k0 += MF_NB, ++kk) {
+      const int kb = min(MF_NB, Fd.p - k0), k1 = k0 + kb;
+      pivot_block<T>(P, F, Fd.ld, k0, kb, &s_flag);
+      T* dv = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB;
+      for (int q = tid; q < MF_NB * MF_NB; q += blockDim.x) {
+        dv[q] = P.Li[q >> 5][q & 31];
+        dv[MF_NB * MF_NB + q] = P.Ui[q >> 5][q & 31];
+      }
+      if (k1 >= Fd.m) {
+        __syncthreads();
+        continue;
+      }
+      panel_lu<T>(P, F, Fd.ld, Fd.m, k0, kb, k1);
+      if constexpr (TC) {
+        if (s_flag & 2) continue;   // a bounded wait gave up: issue no further products
+        update_tc(TS, F, Fd.ld, Fd.m, k0, kb, k1, ph, &s_flag);
+      } else {
+        const int nt = (Fd.m - k1 + MF_TILE - 1) / MF_TILE;
+        for (int t = 0; t < nt * nt; ++t)
+          update_tile_fma<T>(F, Fd.ld, Fd.m, k0, kb, k1 + (t % nt) * MF_TILE, k1 + (t / nt) * MF_TILE, As,
+                             As + MF_NB * (MF_TILE + 4));
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (s_flag) atomicOr(&A.status[S.sid], s_flag);
+      __threadfence();
+      st_release(&A.flag[f], epoch);
+    }
+  }
+  if constexpr (TC) {
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if ((tid >> 5) == 0) tm_dealloc(TS.tmem, MF_TMEM_COLS);
+  }
+  finish_launch(A.sched);
+}
+
+// ---------------------------------------------------------------- solves
+struct MFSolveArgs {
+  const MFSysDev* sys;
+  int nsys;
+  const MFFrontDev* fronts;
+  int nfront;
+  const int32_t* rows;
+  const int32_t* relmap;
+  const int* done;
+  int* sched;
+  int* fflag;   // forward done, per front
+  int* bflag;   // backward done, per front
+};
+
+template <typename T>
+__global__ void __launch_bounds__(MF_THREADS, 1)
+    mf_solve_kernel(MFSolveArgs A, const T* __restrict__ Fall, const T* __restrict__ dinv,
+                    const double* __restrict__ rhs, double* __restrict__ x, int accumulate, T* __restrict__ yv,
+                    T* __restrict__ dvec, T* __restrict__ upd) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  T* w = reinterpret_cast<T*>(smem_raw);
+  __shared__ T red[MF_THREADS / 32][MF_NB];
+  __shared__ T blk[MF_NB];
+  __shared__ T Dinv[MF_NB * MF_NB];
+  __shared__ int s_task, s_any;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int epoch = ld_acquire(&A.sched[2]);
+  // a pass after every system has converged takes no task at all
+  if (tid == 0) {
+    int any = A.done ? 0 : 1;
+    for (int i = 0; i < A.nsys && !any; ++i) any = !A.done[A.sys[i].sid];
+    s_any = any;
+  }
+  __syncthreads();
+  for (; s_any;) {
+    const int task = next_task(A.sched, &s_task);
+    if (task >= 2 * A.nfront) break;
+    const bool fwd = task < A.nfront;
+    const int f = fwd ? task : 2 * A.nfront - 1 - task;
+    const MFFrontDev& Fd = A.fronts[f];
+    const MFSysDev& S = A.sys[Fd.sys];
+    if (A.done && A.done[S.sid]) continue;   // converged: the whole tree of this system is skipped
+    const T* F = Fall + Fd.f_off;
+    const int32_t* rw = A.rows + Fd.rows_off;
+    const int m = Fd.m, p = Fd.p;
+    T* y = yv + S.x_off;
+    T* d = dvec + S.x_off;
+    if (fwd) {
+      if (tid == 0) {
+        if (Fd.nchild > 0) wait_flag(&A.fflag[Fd.child0], epoch);
+        if (Fd.nchild > 1) wait_flag(&A.fflag[Fd.child1], epoch);
+      }
+      __syncthreads();
+      const double* r = rhs + S.x_off;
+      for (int i = tid; i < m; i += blockDim.x) w[i] = i < p ? (T)r[rw[i]] : T(0);
+      __syncthreads();
+      for (int c = 0; c < Fd.nchild; ++c) {
+        const MFFrontDev& C = A.fronts[c == 0 ? Fd.child0 : Fd.child1];
+        const int qc = C.m - C.p;
+        const int32_t* rm = A.relmap + C.relmap_off;
+        const T* u = upd + C.upd_off;
+        for (int i = tid; i < qc; i += blockDim.x) w[rm[i]] += ldcg(u + i);
+        __syncthreads();
+      }
+      for (int k0 = 0, kk = 0; k0 < p; k0 += MF_NB, ++kk) {
+        const int kb = min(MF_NB, p - k0);
+        const T* Li = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB;
+#pragma unroll
+        for (int u = 0; u < MF_NB * MF_NB / MF_THREADS; ++u) Dinv[tid + u * MF_THREADS] = ldcg(Li + tid + u * MF_THREADS);
+        __syncthreads();
+        if (warp == 0) {
+          T s = T(0);
+#pragma unroll
+          for (int c = 0; c < MF_NB; ++c)
+            if (c < kb) s += Dinv[lane * MF_NB + c] * w[k0 + c];
+          __syncwarp();
+          if (lane < kb) w[k0 + lane] = s;
+        }
+        __syncthreads();
+        const int k1 = k0 + kb;
+        for (int i = k1 + tid; i < m; i += blockDim.x) {
+          T fv[MF_NB];
+#pragma unroll
+          for (int c = 0; c < MF_NB; ++c) fv[c] = c < kb ? ldcg(F + (int64_t)(k0 + c) * Fd.ld + i) : T(0);
+          T s = T(0);
+#pragma unroll
+          for (int c = 0; c < MF_NB; ++c)
+            if (c < kb) s += fv[c] * w[k0 + c];
+          w[i] -= s;
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < m; i += blockDim.x) {
+        if (i < p) y[rw[i]] = w[i];
+        else upd[Fd.upd_off + i - p] = w[i];
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(&A.fflag[f], epoch);
+      }
+    } else {
+      if (tid == 0) {
+        wait_flag(&A.fflag[f], epoch);
+        if (Fd.parent >= 0) wait_flag(&A.bflag[Fd.parent], epoch);
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += blockDim.x) w[i] = i < p ? ldcg(y + rw[i]) : ldcg(d + rw[i]);
+      __syncthreads();
+      const int nblk = (p + MF_NB - 1) / MF_NB;
+      for (int kk = nblk - 1; kk >= 0; --kk) {
+        const int k0 = kk * MF_NB;
+        const int kb = min(MF_NB, p - k0);
+        const int k1 = k0 + kb;
+        T s = T(0);
+        const T* Ui = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB + MF_NB * MF_NB;
+#pragma unroll
+        for (int u = 0; u < MF_NB * MF_NB / MF_THREADS; ++u) Dinv[tid + u * MF_THREADS] = ldcg(Ui + tid + u * MF_THREADS);
+        if (lane < kb) {
+          int j = k1 + warp;
+          for (; j + 3 * (MF_THREADS / 32) < m; j += 4 * (MF_THREADS / 32)) {
+            T f4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) f4[u] = ldcg(F + (int64_t)(j + u * (MF_THREADS / 32)) * Fd.ld + k0 + lane);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += f4[u] * w[j + u * (MF_THREADS / 32)];
+          }
+          for (; j < m; j += MF_THREADS / 32) s += ldcg(F + (int64_t)j * Fd.ld + k0 + lane) * w[j];
+        }
+        red[warp][lane] = s;
+        __syncthreads();
+        if (warp == 0) {
+          T z = T(0);
+          if (lane < kb) {
+            z = w[k0 + lane];
+#pragma unroll
+            for (int q = 0; q < MF_THREADS / 32; ++q) z -= red[q][lane];
+          }
+          blk[lane] = z;
+          __syncwarp();
+          T xv = T(0);
+#pragma unroll
+          for (int c = 0; c < MF_NB; ++c)
+            if (c < kb) xv += Dinv[lane * MF_NB + c] * blk[c];
+          if (lane < kb) w[k0 + lane] = xv;
+        }
+        __syncthreads();
+      }
+      double* xo = x + S.x_off;
+      for (int i = tid; i < p; i += blockDim.x) {
+        d[rw[i]] = w[i];
+        xo[rw[i]] = accumulate ? xo[rw[i]] + (double)w[i] : (double)w[i];
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(&A.bflag[f], epoch);
+      }
+    }
+  }
+  finish_launch(A.sched);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+size_t mf_factor_smem(bool tc) {
+  if (tc && sizeof(T) == 4) return sizeof(TcSmem);
+  return (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T) + sizeof(PanelSmem<T>);
+}
+
+static int mf_grid(const void* fn, size_t smem, int cap) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, MF_THREADS, smem);
+  const int g = nsm * (per > 0 ? per : 1);
+  return cap > 0 && cap < g ? cap : g;
+}
+
+template <typename T>
+cudaError_t launch_mf_factor(const MFLaunch& L, T* F, T* dinv, int tc, cudaStream_t st) {
+  if (L.nfront == 0) return cudaSuccess;
+  MFArgs A{L.sys, L.fronts, L.nfront, L.relmap, L.colptr, L.orig_k, L.orig_ij, L.vals, L.status, L.sched,
+           L.fflag};
+  const bool use_tc = tc && sizeof(T) == 4;
+  const size_t smem = mf_factor_smem<T>(use_tc);
+  count_launches(1);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc) {
+      auto fn = mf_factor_kernel<T, true>;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      // at most two CTAs per SM (shared memory), each allocating half of the tensor memory
+      const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), L.nfront);
+      fn<<<grid, MF_THREADS, smem, st>>>(A, F, dinv);
+      return cudaGetLastError();
+    }
+  }
+  auto fn = mf_factor_kernel<T, false>;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), L.nfront);
+  fn<<<grid, MF_THREADS, smem, st>>>(A, F, dinv);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const double* r, double* x, int accumulate,
+                            const int* done, T* yv, T* dv, T* upd, int m_max, cudaStream_t st) {
+  if (L.nfront == 0) return cudaSuccess;
+  MFSolveArgs A{L.sys, L.nsys, L.fronts, L.nfront, L.rows, L.relmap, done, L.sched + 4, L.sflag, L.sflag + L.nfront};
+  const size_t smem = (size_t)(m_max + 4) * sizeof(T);
+  count_launches(1);
+  auto fn = mf_solve_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), 2 * L.nfront);
+  fn<<<grid, MF_THREADS, smem, st>>>(A, F, dinv, r, x, accumulate, yv, dv, upd);
+  return cudaGetLastError();
+}
+
+#define TPNS_MF_INST(T)                                                                                      \
+  template size_t mf_factor_smem<T>(bool);                                                                  \
+  template cudaError_t launch_mf_factor<T>(const MFLaunch&, T*, T*, int, cudaStream_t);                     \
+  template cudaError_t launch_mf_solve<T>(const MFLaunch&, const T*, const T*, const double*, double*, int, \
+                                          const int*, T*, T*, T*, int, cudaStream_t);
+TPNS_MF_INST(float)
+TPNS_MF_INST(double)
+
+}  // namespace tpns

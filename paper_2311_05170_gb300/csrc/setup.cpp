@@ -235,8 +235,10 @@ static void order_unknowns(Problem& P) {
 }
 
 // Pack (target, source) contributions sorted by target into warp chunks of 32 lanes so
-// that no run of equal targets straddles two chunks (padding lanes get target -1).
-static void pack_chunks(std::vector<std::pair<int32_t, int32_t>>& c, std::vector<int32_t>& tgt,
+// that no run of equal targets straddles two chunks (padding lanes get target -1).  The
+// segmented warp reduction adds one run inside one warp, so a target with more than 32
+// contributions cannot be packed: returns false (nothing is truncated).
+static bool pack_chunks(std::vector<std::pair<int32_t, int32_t>>& c, std::vector<int32_t>& tgt,
                         std::vector<int32_t>& src) {
   std::sort(c.begin(), c.end());
   tgt.clear(); src.clear();
@@ -246,7 +248,7 @@ static void pack_chunks(std::vector<std::pair<int32_t, int32_t>>& c, std::vector
     size_t j = i;
     while (j < c.size() && c[j].first == c[i].first) ++j;
     int len = (int)(j - i);
-    if (len > 32) { std::fprintf(stderr, "tpns: scatter run longer than a warp\n"); len = 32; }
+    if (len > 32) return false;
     if (lane + len > 32) {
       while (lane < 32) { tgt.push_back(-1); src.push_back(0); ++lane; }
       lane = 0;
@@ -257,9 +259,10 @@ static void pack_chunks(std::vector<std::pair<int32_t, int32_t>>& c, std::vector
     i = j;
   }
   while (lane != 0 && lane < 32) { tgt.push_back(-1); src.push_back(0); ++lane; }
+  return true;
 }
 
-static void build_pattern(Problem& P) {
+static bool build_pattern(Problem& P) {
   const int S = P.slots();
   std::vector<std::vector<int32_t>> rows(P.n);
   for (int e = 0; e < P.ne; ++e)
@@ -305,8 +308,7 @@ static void build_pattern(Problem& P) {
         mc.push_back({k, e * S * S + r * S + c});
       }
     }
-  pack_chunks(mc, P.mtgt, P.msrc);
-  pack_chunks(rc, P.rtgt, P.rsrc);
+  if (!pack_chunks(mc, P.mtgt, P.msrc) || !pack_chunks(rc, P.rtgt, P.rsrc)) return false;
   // algorithmic flops of the unpivoted band LU under this ordering
   double f = 0;
   for (int j = 0; j < P.n; ++j) {
@@ -314,11 +316,29 @@ static void build_pattern(Problem& P) {
     f += l + 2.0 * l * u;
   }
   P.lu_flops = f;
+  return true;
 }
 
-static void finish_problem(Problem& P) {
+static bool finish_problem(Problem& P) {
   order_unknowns(P);
-  build_pattern(P);
+  return build_pattern(P);
+}
+
+static const char* kLongRun = "a matrix or vector entry receives more than 32 element contributions";
+
+// Multifrontal analysis of a local Oseen system: the unknowns' half-grid coordinates in the
+// box (vertices at even coordinates) drive the nested dissection.
+static std::string analyse_mf(Problem& P, int leaf) {
+  const int nI = 2 * (P.i1 - P.i0) + 1;
+  std::vector<int32_t> coord((size_t)P.n * 2);
+  std::vector<int8_t> pres(P.n);
+  for (int d = 0; d < P.n; ++d) {
+    const int l = P.dof_node[d];
+    coord[2 * (size_t)d] = l % nI;
+    coord[2 * (size_t)d + 1] = l / nI;
+    pres[d] = P.dof_comp[d] == 2;
+  }
+  return mf_analyse(P.n, 2, coord.data(), pres.data(), P.rowptr.data(), P.colidx.data(), leaf, P.mf);
 }
 
 // ------------------------------------------------------------------------------ prolongation
@@ -398,7 +418,7 @@ static void glue_table(const std::vector<Problem>& probs, int nnodes, bool verti
   }
 }
 
-std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L) {
+std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf) {
   if (md.nx_coarse <= 0 || md.ny_coarse <= 0 || md.ny_coarse > TPNS_MAX_COARSE_ROWS ||
       md.fine_per_coarse_x <= 0)
     return "invalid mesh description";
@@ -430,14 +450,18 @@ std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd
         Problem P;
         make_problem(P, m, region == 0 ? PK_OSEEN : PK_DARCY, region, false, i0, i1, j0, j1, di0,
                      di1, dj0, dj1);
-        finish_problem(P);
+        if (!finish_problem(P)) return kLongRun;
+        if (mf_leaf > 0 && P.kind == PK_OSEEN) {
+          std::string e = analyse_mf(P, mf_leaf);
+          if (!e.empty()) return e;
+        }
         list.push_back(std::move(P));
       }
   }
   make_problem(L.cfl, L.mcH, PK_OSEEN, 0, true, 0, L.mcH.nx, 0, L.mcH.ny, 0, L.mcH.nx, 0, L.mcH.ny);
-  finish_problem(L.cfl);
+  if (!finish_problem(L.cfl)) return kLongRun;
   make_problem(L.cpo, L.mpH, PK_DARCY, 1, true, 0, L.mpH.nx, 0, L.mpH.ny, 0, L.mpH.nx, 0, L.mpH.ny);
-  finish_problem(L.cpo);
+  if (!finish_problem(L.cpo)) return kLongRun;
   // Gamma partner nodes (same half-grid column on the other region's Gamma row)
   auto gam = [](Problem& P, const Mesh& self, const Mesh& other, int region) {
     P.gam_src.assign(P.nn, -1);

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "mf.hpp"
 #include "tpns.h"
 
 namespace tpns {
@@ -60,6 +61,7 @@ struct Problem {
   std::vector<int32_t> mtgt, msrc;   // element matrix entry -> CSR entry
   std::vector<int32_t> rtgt, rsrc;   // element vector entry -> unknown
   double lu_flops = 0;               // sum over columns of 2 * (#L entries) * (#U entries) + (#L)
+  MFSymbolic mf;                     // multifrontal analysis (local Oseen problems)
   int slots() const { return kind == PK_OSEEN ? 15 : 6; }
 };
 
@@ -82,7 +84,9 @@ struct Layout {
 };
 
 // Build everything from the ABI descriptors; returns "" on success or an error message.
-std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L);
+// mf_leaf > 0: also run the multifrontal analysis of every local Oseen system with leaves
+// of at most mf_leaf unknowns.
+std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf = 0);
 
 // Reference-element integrals (computed by the degree-5 rule) and quadrature tables.
 struct RefTables {

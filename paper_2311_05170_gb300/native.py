@@ -35,12 +35,22 @@ class DataDesc(C.Structure):
     _fields_ = [("mms_id", C.c_int32)]
 
 
+class Options(C.Structure):
+    _fields_ = [("local_factor", C.c_int32), ("mf_leaf", C.c_int32), ("mf_cuda_cores", C.c_int32),
+                ("mf_ctas", C.c_int32)]
+
+
+FACTORS = {"mf": 0, "band": 1}
+
+
 class Stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("last_ir_iters_max", C.c_int32), ("last_newton_iters", C.c_int32),
                 ("last_ir_relres_max", C.c_double), ("n_fine_dofs", C.c_int64), ("n_local_systems", C.c_int64),
                 ("device_bytes", C.c_int64), ("band_lu_flops", C.c_double), ("h2d_bytes", C.c_int64),
                 ("last_ir_solves", C.c_int64), ("last_solve_bytes", C.c_double), ("last_step_ms", C.c_double),
-                ("lu_cluster_ctas", C.c_int64)]
+                ("lu_cluster_ctas", C.c_int64), ("oseen_unknowns", C.c_int64), ("oseen_nnz", C.c_int64),
+                ("oseen_elements", C.c_int64), ("darcy_unknowns", C.c_int64), ("darcy_elements", C.c_int64),
+                ("factor_entries", C.c_double), ("mf_fronts", C.c_int64), ("create_ms", C.c_double)]
 
 
 class TpnsError(RuntimeError):
@@ -55,7 +65,7 @@ EXPORTS = ["tpns_create", "tpns_step", "tpns_coarse_precompute", "tpns_local_ste
            "tpns_get_field", "tpns_get_stats", "tpns_batch_step", "tpns_last_error", "tpns_destroy",
            "tpns_debug_mesh", "tpns_debug_system", "tpns_set_timing", "tpns_get_timings", "tpns_launch_count",
            "tpns_layout_create", "tpns_debug_values", "tpns_band_solve",
-           "tpns_band_solve_noalloc"]
+           "tpns_band_solve_noalloc", "tpns_create_ex", "tpns_layout_create_ex", "tpns_debug_fronts"]
 
 PHASES = ["coarse", "prolong", "asm_oseen", "scatter", "asm_darcy", "band_fill", "band_lu", "solve", "residual",
           "state_glue", "copies"]
@@ -73,6 +83,15 @@ def load(path=LIB_PATH):
     lib.tpns_create.argtypes = [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(PartitionDesc),
                                 C.POINTER(DataDesc), C.c_double, C.c_int, C.c_size_t, P, C.POINTER(P)]
     lib.tpns_create.restype = C.c_int
+    lib.tpns_create_ex.argtypes = [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(PartitionDesc),
+                                   C.POINTER(DataDesc), C.c_double, C.c_int, C.c_size_t, P, C.POINTER(Options),
+                                   C.POINTER(P)]
+    lib.tpns_create_ex.restype = C.c_int
+    lib.tpns_layout_create_ex.argtypes = [C.POINTER(MeshDesc), C.POINTER(PartitionDesc), C.POINTER(Options),
+                                          C.POINTER(P)]
+    lib.tpns_layout_create_ex.restype = C.c_int
+    lib.tpns_debug_fronts.argtypes = [P, C.c_int32, C.c_int32, P, C.POINTER(C.c_size_t)]
+    lib.tpns_debug_fronts.restype = C.c_int
     for name in ("tpns_step", "tpns_coarse_precompute", "tpns_local_step"):
         getattr(lib, name).argtypes = [P, C.c_int32]
         getattr(lib, name).restype = C.c_int
@@ -138,18 +157,21 @@ FIELD_IDS = {"ux": 0, "uy": 1, "p": 2, "pF": 3, "pf": 4, "pm": 5}
 class Solver:
     """One simulation context on the current CUDA device (host_only=True: layout only)."""
 
-    def __init__(self, w, precision="fp64", hbm_budget_bytes=0, stream=None, host_only=False):
+    def __init__(self, w, precision="fp64", hbm_budget_bytes=0, stream=None, host_only=False, factor="mf",
+                 mf_leaf=0, cuda_cores=False, mf_ctas=0):
         self.lib = load()
         self.w = w
         md, pr, pd, dd = descriptors(w)
+        opt = Options(FACTORS[factor], int(mf_leaf), 1 if cuda_cores else 0, int(mf_ctas))
         ctx = C.c_void_p()
         if host_only:
-            _check(self.lib, None, self.lib.tpns_layout_create(C.byref(md), C.byref(pd), C.byref(ctx)))
+            _check(self.lib, None, self.lib.tpns_layout_create_ex(C.byref(md), C.byref(pd), C.byref(opt),
+                                                                  C.byref(ctx)))
             self.ctx = ctx
             return
         st = C.c_void_p(stream) if stream else None
-        s = self.lib.tpns_create(C.byref(md), C.byref(pr), C.byref(pd), C.byref(dd), float(w.dt),
-                                 PRECISIONS[precision], int(hbm_budget_bytes), st, C.byref(ctx))
+        s = self.lib.tpns_create_ex(C.byref(md), C.byref(pr), C.byref(pd), C.byref(dd), float(w.dt),
+                                    PRECISIONS[precision], int(hbm_budget_bytes), st, C.byref(opt), C.byref(ctx))
         _check(self.lib, None, s)
         self.ctx = ctx
 
@@ -211,6 +233,36 @@ class Solver:
                                                     comp.ctypes.data_as(I32), None, rp.ctypes.data_as(I32),
                                                     ci.ctypes.data_as(I32), None, None))
         return {"node": node, "comp": comp, "rowptr": rp, "colidx": ci, "kl": kl.value, "ku": ku.value}
+
+    def debug_fronts(self, j):
+        """Multifrontal structure of local Oseen system j (see tpns_debug_fronts)."""
+        lib = self.lib
+
+        def get(what):
+            n = C.c_size_t()
+            _check(lib, self.ctx, lib.tpns_debug_fronts(self.ctx, j, what, None, C.byref(n)))
+            out = np.empty(n.value, np.int32)
+            _check(lib, self.ctx, lib.tpns_debug_fronts(self.ctx, j, what, out.ctypes.data, C.byref(n)))
+            return out
+
+        nf, nlev = get(0)
+        info = get(1).reshape(nf, 7)
+        fronts = []
+        rows, rel, cp, ok, oi, cc = get(2), get(3), get(4), get(5), get(6), get(7)
+        a = b = c = d = 0
+        for t in range(nf):
+            m, p = int(info[t, 0]), int(info[t, 1])
+            cptr = cp[c:c + m + 1].copy()
+            fronts.append({"m": m, "p": p, "level": int(info[t, 2]), "parent": int(info[t, 3]),
+                           "children": [int(x) for x in info[t, 5:5 + info[t, 4]]], "rows": rows[a:a + m].copy(),
+                           "relmap": rel[b:b + m - p].copy() if info[t, 3] >= 0 else np.empty(0, np.int32),
+                           "col_ptr": cptr, "orig_k": ok[d:d + cptr[-1]].copy(), "orig_i": oi[d:d + cptr[-1]].copy(),
+                           "col_child": cc[2 * a:2 * a + 2 * m].reshape(m, 2).copy()})
+            a += m
+            b += m - p if info[t, 3] >= 0 else 0
+            c += m + 1
+            d += cptr[-1]
+        return {"nlevels": int(nlev), "fronts": fronts, "order": get(8)}
 
     def set_timing(self, on=True):
         _check(self.lib, self.ctx, self.lib.tpns_set_timing(self.ctx, 1 if on else 0))

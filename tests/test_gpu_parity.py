@@ -3,7 +3,9 @@
 Tolerances (per field, relative L2 over the global fine dofs): 1e-10 for the FP64 path,
 1e-8 for FP32 factors with FP64-residual refinement.  Both sides integrate the
 transcendental data with the same quadrature rules, so the only differences are rounding
-orders and the refinement's stopping point."""
+orders and the refinement's stopping point.  The local Oseen systems are factored by the
+multifrontal LU (default: tensor-core trailing updates for FP32 fronts; "mf-cc": CUDA-core
+updates) or by the band LU ("band")."""
 import numpy as np
 import pytest
 
@@ -31,9 +33,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def run_pair(native, w, prec, nsteps):
+FACTOR = {"mf": {}, "mf-cc": {"cuda_cores": True}, "band": {"factor": "band"}}
+
+
+def run_pair(native, w, prec, nsteps, factor="mf"):
     o = TwoGridOracle(w)
-    s = native.Solver(w, precision=prec)
+    s = native.Solver(w, precision=prec, **FACTOR[factor])
     f0 = s.fields()
     for k in f0:
         assert rel(f0[k], o.fine[k]) < 1e-13, ("initial", k)
@@ -46,29 +51,32 @@ def run_pair(native, w, prec, nsteps):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_patch_field_exact_on_gpu(native, prec):
+@pytest.mark.parametrize("factor", ["mf", "band"])
+def test_patch_field_exact_on_gpu(native, prec, factor):
     w = W.config_patch(nx_coarse=2, r=2, nsub=(2, 2), nsteps=3)
-    f, o, _ = run_pair(native, w, prec, 3)
+    f, o, _ = run_pair(native, w, prec, 3, factor)
     ex = o.exact_fine()
     for k in f:
         assert np.abs(f[k] - ex[k]).max() < 1e-11, k
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
-def test_small_2d_parity(native, prec):
+@pytest.mark.parametrize("prec,factor", [("fp64", "mf"), ("fp32", "mf"), ("fp32", "mf-cc"), ("tf32", "mf"),
+                                         ("fp64", "band"), ("fp32", "band"), ("tf32", "band"), ("bf16", "band")])
+def test_small_2d_parity(native, prec, factor):
     w = W.config_small(nsteps=10)
-    f, o, stats = run_pair(native, w, prec, 10)
+    f, o, stats = run_pair(native, w, prec, 10, factor)
     for k in f:
         assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))
     assert stats["last_ir_relres_max"] <= 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
-def test_graded_full_size_parity(native, prec):
+@pytest.mark.parametrize("prec,factor", [("fp64", "mf"), ("fp32", "mf"), ("fp32", "mf-cc"), ("fp32", "band"),
+                                         ("tf32", "band")])
+def test_graded_full_size_parity(native, prec, factor):
     """The bench workload at full size (130,966 fine dofs, 16 + 48 local systems of 1.4k to
     8.3k unknowns), three steps."""
     w = W.config_graded(nsteps=3)
-    f, o, stats = run_pair(native, w, prec, 3)
+    f, o, stats = run_pair(native, w, prec, 3, factor)
     for k in f:
         assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))
     assert stats["n_fine_dofs"] == 130966 and stats["n_local_systems"] == 64
@@ -78,8 +86,9 @@ def test_graded_full_size_parity(native, prec):
                                W.config_uniform(8, 2, nsub=(4, 2), overlap=3, nsteps=3),
                                W.config_uniform(4, 1, nsub=(2, 2), overlap=1, nsteps=3)],
                          ids=["single_subdomain", "uneven_4x2", "H_equals_h"])
-def test_edge_layouts_parity(native, w):
-    f, o, _ = run_pair(native, w, "fp32", 3)
+@pytest.mark.parametrize("factor", ["mf", "band"])
+def test_edge_layouts_parity(native, w, factor):
+    f, o, _ = run_pair(native, w, "fp32", 3, factor)
     for k in f:
         assert rel(f[k], o.fine[k]) <= 1e-8, k
 
@@ -92,7 +101,7 @@ def test_wide_band_parity(native):
     s = native.Solver(w, precision="fp32", host_only=True)
     assert max(s.debug_system(j)["kl"] for j in range(4)) == 851
     s.close()
-    f, o, stats = run_pair(native, w, "fp32", 2)
+    f, o, stats = run_pair(native, w, "fp32", 2, "band")
     for k in f:
         assert rel(f[k], o.fine[k]) <= TOL["fp32"], (k, rel(f[k], o.fine[k]))
     assert stats["last_ir_relres_max"] <= 1e-12
@@ -107,7 +116,7 @@ def test_widest_band_global_vector_parity(native):
     info = s.debug_system(0)
     assert info["kl"] == 1123 and len(info["rowptr"]) - 1 > 38000
     s.close()
-    f, o, stats = run_pair(native, w, "fp32", 1)
+    f, o, stats = run_pair(native, w, "fp32", 1, "band")
     for k in f:
         assert rel(f[k], o.fine[k]) <= TOL["fp32"], (k, rel(f[k], o.fine[k]))
     assert stats["last_ir_relres_max"] <= 1e-12
@@ -118,8 +127,50 @@ def test_band_too_wide_for_fp64_is_refused(native):
     with TPNS_EINVAL and a message, before any device allocation."""
     w = W.config_uniform(4, 24, nsub=(2, 2), nsteps=1)
     with pytest.raises(native.TpnsError) as e:
-        native.Solver(w, precision="fp64")
+        native.Solver(w, precision="fp64", factor="band")
     assert e.value.status == native.TPNS_EINVAL and "shared memory" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_multifrontal_on_systems_too_wide_for_the_band_lu(native, prec):
+    """h = 1/128 with 2 x 2 subdomains (39k-unknown Oseen systems, band kl = 1123): the
+    multifrontal factorisation has no band-width limit, in FP64 as well; one step against the
+    oracle."""
+    w = W.config_uniform(4, 32, nsub=(2, 2), nsteps=1)
+    f, o, stats = run_pair(native, w, prec, 1)
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))
+    assert stats["last_ir_relres_max"] <= 1e-12
+
+
+def test_multifrontal_bf16_is_refused(native):
+    with pytest.raises(native.TpnsError) as e:
+        native.Solver(W.config_small(nsteps=1), precision="bf16")
+    assert e.value.status == native.TPNS_EINVAL
+
+
+def test_multifrontal_leaf_sizes_and_launch_caps_agree(native):
+    """Different dissection depths change the fronts (and so the rounding), not the result:
+    every variant meets the FP32 tolerance against the oracle; a cap of 7 CTAs on the
+    dataflow launches (fronts then wait for children taken by the few running CTAs) gives
+    the same fields bit for bit as the default launch."""
+    w = W.config_small(nsteps=3)
+    o = TwoGridOracle(w)
+    o.run(3)
+    ref = None
+    for leaf, ctas in ((0, 0), (0, 7), (24, 0), (400, 0)):
+        s = native.Solver(w, precision="fp32", mf_leaf=leaf, mf_ctas=ctas)
+        s.step(3)
+        f = s.fields()
+        s.close()
+        for k in f:
+            assert rel(f[k], o.fine[k]) <= TOL["fp32"], (leaf, ctas, k)
+        if leaf == 0:
+            if ref is None:
+                ref = f
+            else:
+                for k in f:
+                    assert np.array_equal(f[k], ref[k]), k
 
 
 def test_assembled_systems_match_oracle(native):
@@ -159,19 +210,20 @@ def test_assembled_systems_match_oracle(native):
     s.close()
 
 
-def test_deterministic_and_precomputed_coarse_path_bitwise(native):
-    """Two runs give bit-identical fields (no atomics anywhere), and running the local hot
+@pytest.mark.parametrize("factor", ["mf", "band"])
+def test_deterministic_and_precomputed_coarse_path_bitwise(native, factor):
+    """Two runs give bit-identical fields (no atomics in any sum), and running the local hot
     path on precomputed coarse states gives bit-identical fields to full steps."""
     w = W.config_small(nsteps=4)
-    a = native.Solver(w, precision="fp32")
+    a = native.Solver(w, precision="fp32", **FACTOR[factor])
     a.step(4)
     fa = a.fields()
     a.close()
-    b = native.Solver(w, precision="fp32")
+    b = native.Solver(w, precision="fp32", **FACTOR[factor])
     b.step(4)
     fb = b.fields()
     b.close()
-    c = native.Solver(w, precision="fp32")
+    c = native.Solver(w, precision="fp32", **FACTOR[factor])
     c.coarse_precompute(4)
     c.local_step(4)
     fc = c.fields()

@@ -1,8 +1,8 @@
 """tpns_band_solve_noalloc: the band solver for callers that cannot allocate device memory
-(code inside a CUDA stream capture, hosts whose device memory belongs to another
-allocator, loops that must not allocate at solve time).  Its scratch is a static device
-array inside the library.  It must return what tpns_band_solve returns for the same
-system, including on consecutive calls that reuse the array."""
+(hosts whose device memory belongs to another allocator, loops that must not allocate at
+solve time).  Its scratch is a static device array inside the library.  It must return
+what tpns_band_solve returns for the same system, including on consecutive calls that
+reuse the array and for a system whose solve vector does not fit in shared memory."""
 import ctypes as C
 
 import numpy as np
@@ -78,3 +78,39 @@ def test_noalloc_refuses_systems_beyond_its_scratch(lib):
                                       lib.PRECISIONS["fp32"], None, None)
     assert st == lib.TPNS_EINVAL
     assert b"scratch" in lib_.tpns_last_error(None)
+
+
+def _banded(n, kl, ku, seed):
+    """Diagonally dominant CSR matrix with bandwidths kl / ku and a right-hand side (host)."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for off in range(-kl, ku + 1):
+        i = np.arange(max(0, -off), min(n, n - off))
+        rows.append(i)
+        cols.append(i + off)
+        vals.append(rng.uniform(-1.0, 1.0, len(i)) + (4.0 * (kl + ku + 1) if off == 0 else 0.0))
+    r, c, v = (np.concatenate(a) for a in (rows, cols, vals))
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(rowptr, r + 1, 1)
+    return np.cumsum(rowptr).astype(np.int32), c.astype(np.int32), v, rng.standard_normal(n)
+
+
+def test_noalloc_vector_beyond_shared_memory(lib):
+    """n = 30,000 in FP64 does not fit one CTA's shared memory beside a pipeline stage, so the
+    solve keeps its vector in the scratch; two calls in a row match the allocating solver."""
+    import torch
+    n, kl, ku = 30000, 3, 2
+    rp, ci, va, b = _banded(n, kl, ku, seed=11)
+    dev = lambda a, dt: torch.tensor(a, dtype=dt, device="cuda")
+    info = {"node": np.zeros(n), "kl": kl, "ku": ku}
+    args = (dev(rp, torch.int32), dev(ci, torch.int32), dev(va, torch.float64), dev(b, torch.float64))
+    for _ in range(2):
+        x_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
+        x_new = torch.zeros(n, dtype=torch.float64, device="cuda")
+        _call(lib, "tpns_band_solve", info, *args, x_ref, "fp64")
+        rel = _call(lib, "tpns_band_solve_noalloc", info, *args, x_new, "fp64")
+        assert rel <= 1e-12
+        a, r = x_new.cpu().numpy(), x_ref.cpu().numpy()
+        assert np.linalg.norm(a - r) <= 1e-10 * np.linalg.norm(r)
