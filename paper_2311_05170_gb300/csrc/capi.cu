@@ -70,7 +70,7 @@ struct tpns_ctx {
   int lu_cl = 0;                                   // CTAs per cluster of the Oseen LU, picked at create
   // multifrontal factorisation of the local Oseen systems
   bool mf = false;
-  int mf_leaf = 96, mf_tc = 1, mf_m_max = 1;
+  int mf_leaf = 96, mf_tc = 1, mf_m_max = 1, mf_oseen_fronts = 0;
   double mf_flops = 0, mf_factor_entries = 0, mf_dinv_entries = 0;
   MFLaunch mfl{};
   std::vector<MFSysDev> h_mfsys;
@@ -311,7 +311,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
         C.band_off = ctx->band_chol_coarse_len; ctx->band_chol_coarse_len += (int64_t)S.n * C.ldab;
         S.lslab_off = ctx->lslab_coarse_len; ctx->lslab_coarse_len += round32(llen);
         S.uslab_off = ctx->uslab_coarse_len; ctx->uslab_coarse_len += round32(ulen);
-      } else if (ctx->mf && P.kind == PK_OSEEN) {
+      } else if (ctx->mf) {
         // factored by the multifrontal LU: no band storage
         S.band_off = 0; S.dinv_off = 0; S.lslab_off = 0; S.uslab_off = 0; C.band_off = 0;
       } else {
@@ -339,7 +339,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   ctx->list_cp = {ctx->sys_first[CP], ctx->sys_first[CP] + 1, ctx->sys_first[CP] + 2};
   ctx->list_local = ctx->list_osl;
   ctx->list_local.insert(ctx->list_local.end(), ctx->list_dl.begin(), ctx->list_dl.end());
-  ctx->list_band = ctx->mf ? ctx->list_dl : ctx->list_local;
+  if (ctx->mf) ctx->list_band.clear();
+  else ctx->list_band = ctx->list_local;
   for (int s : ctx->list_band) {
     ctx->n_max_band = std::max(ctx->n_max_band, ctx->hsys[s].n);
     ctx->kmax_band = std::max(ctx->kmax_band, std::max(ctx->hsys[s].kl, ctx->hsys[s].ku));
@@ -359,32 +360,48 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   ctx->kl_max_cf = ctx->hsys[ctx->list_cf[0]].kl;
   ctx->n_max_cf = ctx->hsys[ctx->list_cf[0]].n;
   for (int s : ctx->list_cp) ctx->n_max_cp = std::max(ctx->n_max_cp, ctx->hsys[s].n);
-  // multifrontal layout of the local Oseen systems: the fronts of all systems in level
-  // order (leaves first), so that a front's children always precede it
+  // multifrontal layout of the local systems: the fronts of all systems in level order
+  // (leaves first) within each group, so that a front's children always precede it
   std::vector<MFFrontDev> h_fronts;
   std::vector<int32_t> h_mrows, h_relmap, h_origk, h_origi;
   std::vector<int64_t> h_colptr;
   if (ctx->mf) {
     ctx->h_mfsys.clear();
     ctx->mf_flops = ctx->mf_factor_entries = ctx->mf_dinv_entries = 0;
-    struct Key { int level, q, t; };
+    // multifrontal systems: the Oseen systems (factored every step), then the three fields
+    // of every porous subdomain (factored once); each group's fronts in level order
+    struct MSys { int prob, sid; };
+    std::vector<MSys> msys;
+    for (int q = 0; q < ctx->nf; ++q) msys.push_back({q, ctx->sys_first[q]});
+    for (int q = ctx->nf + 1; q < ctx->nf + 1 + ctx->np; ++q)
+      for (int f = 0; f < 3; ++f) msys.push_back({q, ctx->sys_first[q] + f});
+    struct Key { int group, level, q, t; };
     std::vector<Key> keys;
-    std::vector<std::vector<int>> newid(ctx->nf);
-    for (int q = 0; q < ctx->nf; ++q) {
-      const MFSymbolic& M = ctx->probs[q]->mf;
+    std::vector<std::vector<int>> newid(msys.size());
+    for (int q = 0; q < (int)msys.size(); ++q) {
+      const MFSymbolic& M = ctx->probs[msys[q].prob]->mf;
+      const bool oseen = msys[q].prob < ctx->nf;
       newid[q].assign(M.fronts.size(), -1);
-      for (int t = 0; t < (int)M.fronts.size(); ++t) keys.push_back({M.fronts[t].level, q, t});
-      const SysDev& Sd = ctx->hsys[ctx->sys_first[q]];
+      for (int t = 0; t < (int)M.fronts.size(); ++t) keys.push_back({oseen ? 0 : 1, M.fronts[t].level, q, t});
+      const SysDev& Sd = ctx->hsys[msys[q].sid];
       MFSysDev D{};
-      D.sid = ctx->sys_first[q]; D.n = ctx->probs[q]->n; D.x_off = Sd.x_off; D.val_off = Sd.val_off;
+      D.sid = msys[q].sid; D.n = ctx->probs[msys[q].prob]->n; D.x_off = Sd.x_off; D.val_off = Sd.val_off;
       ctx->h_mfsys.push_back(D);
-      ctx->mf_flops += M.flops;
-      ctx->mf_factor_entries += M.factor_entries;
+      if (oseen) {
+        ctx->mf_flops += M.flops;
+        ctx->mf_factor_entries += M.factor_entries;
+      }
     }
-    std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) { return a.level < b.level; });
-    for (size_t i = 0; i < keys.size(); ++i) newid[keys[i].q][keys[i].t] = (int)i;
+    std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+      return a.group != b.group ? a.group < b.group : a.level < b.level;
+    });
+    ctx->mf_oseen_fronts = 0;
+    for (size_t i = 0; i < keys.size(); ++i) {
+      newid[keys[i].q][keys[i].t] = (int)i;
+      if (keys[i].group == 0) ctx->mf_oseen_fronts = (int)i + 1;
+    }
     for (const Key& k : keys) {
-      const MFFront& F = ctx->probs[k.q]->mf.fronts[k.t];
+      const MFFront& F = ctx->probs[msys[k.q].prob]->mf.fronts[k.t];
       if (F.m >= 32768) {
         ctx->err = "a multifrontal front of order " + std::to_string(F.m) + " exceeds 32767";
         return TPNS_EINVAL;
@@ -410,7 +427,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       for (int j = 0; j < F.m; ++j)
         for (int q = F.col_ptr[j]; q < F.col_ptr[j + 1]; ++q) h_origi.push_back(F.orig_i[q] | (j << 16));
       ctx->mf_m_max = std::max(ctx->mf_m_max, F.m);
-      ctx->mf_dinv_entries += (double)nb * 2 * MF_NB * MF_NB;
+      if (k.group == 0) ctx->mf_dinv_entries += (double)nb * 2 * MF_NB * MF_NB;
       h_fronts.push_back(FD);
     }
   }
@@ -984,7 +1001,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   T* mfD = reinterpret_cast<T*>(ctx->d_mf_dinv);
   if (ctx->mf) {
     ph_begin(ctx, PH_BAND_LU);
-    CK(launch_mf_factor<T>(ctx->mfl, mfF, mfD, ctx->mf_tc, st));
+    CK(launch_mf_factor<T>(ctx->mfl, 0, ctx->mf_oseen_fronts, mfF, mfD, ctx->mf_tc, st));
     ph_end(ctx, PH_BAND_LU);
   } else {
     ph_begin(ctx, PH_BAND_FILL);
@@ -1114,17 +1131,21 @@ static tpns_status read_stats(tpns_ctx* ctx) {
     // each residual after a solve counts one iteration, so iters = solve passes this step
     const SysDev& S = ctx->hsys[s];
     passes += it[s];
-    if (!(ctx->mf && s < ctx->nf))
+    if (!ctx->mf)
       bytes += (double)it[s] * ((double)S.n * (S.kl + S.ku) * tsz + (double)((S.n + 31) / 32) * 2048.0 * tsz +
                                 24.0 * S.n);
   }
   if (ctx->mf)
-    for (int q = 0; q < ctx->nf; ++q) {
-      const MFSymbolic& M = ctx->probs[q]->mf;
-      const int s = ctx->sys_first[q];
+    for (int q = 0; q < ctx->nprob; ++q) {
+      const Problem& P = *ctx->probs[q];
+      if (P.coarse) continue;
+      const MFSymbolic& M = P.mf;
       double dv = 0;
       for (const MFFront& F : M.fronts) dv += (double)((F.p + MF_NB - 1) / MF_NB) * 2 * MF_NB * MF_NB;
-      bytes += (double)it[s] * ((M.factor_entries + dv) * tsz + 24.0 * ctx->hsys[s].n);
+      for (int f = 0; f < (P.kind == PK_OSEEN ? 1 : 3); ++f) {
+        const int s = ctx->sys_first[q] + f;
+        bytes += (double)it[s] * ((M.factor_entries + dv) * tsz + 24.0 * ctx->hsys[s].n);
+      }
     }
   ctx->stats.last_ir_solves = passes;
   ctx->stats.last_solve_bytes = bytes;
@@ -1268,7 +1289,16 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
     CK(launch_band_dinv<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->nblk_max_cp, ctx->d_band_coarse,
                                 ctx->d_dinv_coarse, st, nullptr));
   }
-  if (ctx->prec == TPNS_FP64) {
+  if (ctx->mf) {
+    // the local Darcy systems: multifrontal LU once (their matrices do not change)
+    const int nd = ctx->mfl.nfront - ctx->mf_oseen_fronts;
+    if (ctx->prec == TPNS_FP64)
+      CK(launch_mf_factor<double>(ctx->mfl, ctx->mf_oseen_fronts, nd, reinterpret_cast<double*>(ctx->d_mf_F),
+                                  reinterpret_cast<double*>(ctx->d_mf_dinv), 0, st));
+    else
+      CK(launch_mf_factor<float>(ctx->mfl, ctx->mf_oseen_fronts, nd, reinterpret_cast<float*>(ctx->d_mf_F),
+                                 reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->mf_tc, st));
+  } else if (ctx->prec == TPNS_FP64) {
     double* band = reinterpret_cast<double*>(ctx->d_band_local);
     double* dinv = reinterpret_cast<double*>(ctx->d_dinv_local);
     double* cband;

@@ -67,11 +67,11 @@ cudaError_t launch_residual(const SysDev* sys, const int* sys_list, int nsys, co
                             cudaStream_t st, const int* skip);
 
 // ---- multifrontal LU of the local Oseen systems (kernels_mf.cu); `T` = float or double
-// Factor every front of every system of L in one persistent launch (dataflow over the
-// elimination trees).  tc (float fronts): trailing updates on the tensor cores (tcgen05,
-// split TF32).
+// Factor fronts task0 .. task0 + ntask - 1 of L (all children of a front in the range lie in
+// it) in one persistent launch (dataflow over the elimination trees).  tc (float fronts):
+// trailing updates on the tensor cores (tcgen05, split TF32).
 template <typename T>
-cudaError_t launch_mf_factor(const MFLaunch& L, T* F, T* dinv, int tc, cudaStream_t st);
+cudaError_t launch_mf_factor(const MFLaunch& L, int task0, int ntask, T* F, T* dinv, int tc, cudaStream_t st);
 // One refinement pass: x (+)= (LU)^{-1} r for every system of L whose done flag is clear.
 // yv, dv: vectors of T at the systems' x offsets; upd: update vectors of the fronts.
 template <typename T>

@@ -41,10 +41,12 @@
 namespace tpns {
 namespace {
 
-constexpr int MF_THREADS = 256;
+constexpr int MF_THREADS = 256;           // factorisation CTA
+constexpr int MF_STHREADS = 128;          // solve CTA: fronts are small, more of them in flight per SM
 constexpr int MF_WAIT_LIMIT = 1 << 22;
-constexpr int MF_CN = 2 * MF_TILE;         // columns of one tensor-core update chunk (rows: MF_TILE)
-constexpr int MF_TMEM_COLS = MF_CN;        // one 128 x 256 FP32 accumulator
+constexpr int MF_CN = MF_TILE;             // columns of one tensor-core update chunk (rows: MF_TILE)
+constexpr int MF_TMEM_COLS = MF_CN;        // one 128 x 128 FP32 accumulator
+constexpr int MF_SMEM = 226 * 1024;        // dynamic shared memory of the factorisation (near the opt-in maximum)
 constexpr int DS = MF_NB + 1;              // padded stride of the 32 x 32 shared tiles
 
 // ---------------------------------------------------------------- PTX helpers
@@ -127,7 +129,7 @@ __device__ __forceinline__ uint64_t sm_desc(uint32_t saddr, uint32_t lbo, uint32
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
          (1ull << 46);
 }
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 256.
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128.
 constexpr uint32_t MF_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(MF_CN >> 3) << 17) |
                               ((uint32_t)(MF_TILE >> 4) << 24);
 
@@ -136,6 +138,9 @@ __device__ __forceinline__ float tf32_rn(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
+// Loads of data written by other CTAs in the same launch (a child's Schur complement, the
+// solves' vectors) bypass L1; a front's own entries, written and read by one CTA (in global
+// or in shared memory), use plain loads.
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) {
   return __ldcg(p);
@@ -145,6 +150,8 @@ __device__ __forceinline__ T ldcg(const T* p) {
 // each other (1024 bytes apart)
 __device__ __forceinline__ int pack_idx(int r, int k) { return ((r >> 3) * 8 + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
 
+__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
 __device__ __forceinline__ bool bad_val(float v) { return !(fabsf(v) > 0.0f) || !(fabsf(v) < INFINITY); }
 __device__ __forceinline__ bool bad_val(double v) { return !(fabs(v) > 0.0) || !(fabs(v) < (double)INFINITY); }
 
@@ -172,7 +179,7 @@ __device__ __noinline__ void pivot_block(PanelSmem<T>& S, const T* __restrict__ 
     T a[MF_NB];   // lane j holds column j
     const T* col = F + (int64_t)(k0 + (lane < kb ? lane : 0)) * ld + k0;
 #pragma unroll
-    for (int i = 0; i < MF_NB; ++i) a[i] = ldcg(col + (i < kb ? i : 0));
+    for (int i = 0; i < MF_NB; ++i) a[i] = col[i < kb ? i : 0];
 #pragma unroll
     for (int i = 0; i < MF_NB; ++i)
       if (i >= kb || lane >= kb) a[i] = (i == lane) ? T(1) : T(0);
@@ -181,7 +188,7 @@ __device__ __noinline__ void pivot_block(PanelSmem<T>& S, const T* __restrict__ 
     for (int k = 0; k < MF_NB; ++k) {
       const T piv = __shfl_sync(0xffffffffu, a[k], k);
       if (k < kb) bad |= bad_val(piv);
-      const T rp = T(1) / piv;
+      const T rp = recip(piv);
       if (lane == 0) S.R[k] = rp;
       // lane k turns its column into the multipliers l_i; lanes right of it apply them
 #pragma unroll
@@ -225,10 +232,28 @@ __device__ __noinline__ void pivot_block(PanelSmem<T>& S, const T* __restrict__ 
   __syncthreads();
 }
 
+__device__ __forceinline__ void put_split(float* hi, float* lo, int l, const float (&o)[MF_NB]) {
+#pragma unroll
+  for (int c4 = 0; c4 < MF_NB; c4 += 4) {
+    float4 h, q;
+    h.x = tf32_rn(o[c4]); q.x = tf32_rn(o[c4] - h.x);
+    h.y = tf32_rn(o[c4 + 1]); q.y = tf32_rn(o[c4 + 1] - h.y);
+    h.z = tf32_rn(o[c4 + 2]); q.z = tf32_rn(o[c4 + 2] - h.z);
+    h.w = tf32_rn(o[c4 + 3]); q.w = tf32_rn(o[c4 + 3] - h.w);
+    *reinterpret_cast<float4*>(hi + pack_idx(l, c4)) = h;
+    *reinterpret_cast<float4*>(lo + pack_idx(l, c4)) = q;
+  }
+}
+__device__ __forceinline__ void put_split(float*, float*, int, const double (&)[MF_NB]) {}
+
 // L rows r in [k1, m): F[r, k0:k0+kb] <- F[r, k0:k0+kb] U11^{-1}; U columns c in [k1, m):
-// F[k0:k0+kb, c] <- L11^{-1} F[k0:k0+kb, c].  One thread per row or column.
+// F[k0:k0+kb, c] <- L11^{-1} F[k0:k0+kb, c].  One thread per row or column.  With `pk`
+// (FP32 tensor-core path) the first 128 rows and 256 columns also go straight into the
+// packed operand tiles of the first update chunk.
 template <typename T>
-__device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, int ld, int m, int k0, int kb, int k1) {
+__device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, int ld, int m, int k0, int kb, int k1,
+                                      float* pAh = nullptr, float* pAl = nullptr, float* pBh = nullptr,
+                                      float* pBl = nullptr) {
   const int rest = m - k1;
   for (int q = threadIdx.x; q < 2 * rest; q += blockDim.x) {
     const bool row = q < rest;
@@ -238,7 +263,7 @@ __device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, 
     const T* base = row ? F + (int64_t)k0 * ld + idx : F + (int64_t)idx * ld + k0;
     const int64_t step = row ? ld : 1;
 #pragma unroll
-    for (int c = 0; c < MF_NB; ++c) a[c] = ldcg(base + (c < kb ? c : 0) * step);
+    for (int c = 0; c < MF_NB; ++c) a[c] = base[(c < kb ? c : 0) * step];
 #pragma unroll
     for (int c = 0; c < MF_NB; ++c)
       if (c >= kb) a[c] = T(0);
@@ -259,10 +284,12 @@ __device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, 
 #pragma unroll
       for (int c2 = 0; c2 < MF_NB; ++c2)
         if (c2 < kb) F[(int64_t)(k0 + c2) * ld + idx] = o[c2];
+      if (pAh && idx - k1 < MF_TILE) put_split(pAh, pAl, idx - k1, o);
     } else {
 #pragma unroll
       for (int c2 = 0; c2 < MF_NB; ++c2)
         if (c2 < kb) F[(int64_t)idx * ld + k0 + c2] = o[c2];
+      if (pBh && idx - k1 < MF_CN) put_split(pBh, pBl, idx - k1, o);
     }
   }
   __syncthreads();
@@ -278,9 +305,9 @@ __device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, i
   for (int u = 0; u < MF_NB * MF_TILE / MF_THREADS; ++u) {
     const int q = tid + u * MF_THREADS;
     const int k = q / MF_TILE, r = q % MF_TILE;
-    As[k * W + r] = (k < kb && r0 + r < m) ? ldcg(F + (int64_t)(k0 + k) * ld + r0 + r) : T(0);
+    As[k * W + r] = (k < kb && r0 + r < m) ? F[(int64_t)(k0 + k) * ld + r0 + r] : T(0);
     const int c = q / MF_NB, kk = q % MF_NB;
-    Bs[kk * W + c] = (kk < kb && c0 + c < m) ? ldcg(F + (int64_t)(c0 + c) * ld + k0 + kk) : T(0);
+    Bs[kk * W + c] = (kk < kb && c0 + c < m) ? F[(int64_t)(c0 + c) * ld + k0 + kk] : T(0);
   }
   __syncthreads();
   T acc[8][8];
@@ -308,16 +335,16 @@ __device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, i
       const int r = r0 + tx + 16 * a;
       if (r < m) {
         T* p = F + (int64_t)c * ld + r;
-        *p = ldcg(p) - acc[a][b];
+        *p = *p - acc[a][b];
       }
     }
   }
   __syncthreads();
 }
 
-// Shared memory of the FP32 tensor-core path: operand chunks (A = 128 rows of L21, B = 256
+// Shared memory of the FP32 tensor-core path: operand chunks (A = 128 rows of L21, B = 128
 // columns of U12, 32 values each, TF32 hi and lo parts), the pivot block, barrier, TMEM
-// address.  About 110 KB: two CTAs per SM, each with half of the SM's tensor memory.
+// address (77 KB); the rest of the CTA's shared memory holds the front when it fits.
 struct TcSmem {
   float Ahi[MF_TILE * MF_NB], Alo[MF_TILE * MF_NB], Bhi[MF_CN * MF_NB], Blo[MF_CN * MF_NB];
   PanelSmem<float> P;
@@ -336,7 +363,7 @@ __device__ __forceinline__ void pack_panel(const float* __restrict__ F, int ld, 
   const int64_t step = row ? ld : 1;
   float v[MF_NB];
 #pragma unroll
-  for (int c = 0; c < MF_NB; ++c) v[c] = ldcg(base + (c < kb ? c : 0) * step);
+  for (int c = 0; c < MF_NB; ++c) v[c] = base[(c < kb ? c : 0) * step];
 #pragma unroll
   for (int c = 0; c < MF_NB; ++c)
     if (!ok || c >= kb) v[c] = 0.f;
@@ -367,7 +394,7 @@ __device__ __noinline__ void issue_chunk(const TcSmem& S, uint64_t* bar) {
 }
 
 // Trailing update F[k1:m, k1:m] -= L21 U12 of one pivot block on the tensor cores, in
-// chunks of 128 rows x 256 columns (one accumulator in tensor memory).
+// chunks of 128 rows x 128 columns (one accumulator in tensor memory).
 __device__ __noinline__ void update_tc(TcSmem& S, float* __restrict__ F, int ld, int m, int k0, int kb, int k1,
                                        unsigned& ph, int* s_flag) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -375,9 +402,11 @@ __device__ __noinline__ void update_tc(TcSmem& S, float* __restrict__ F, int ld,
     const int nc = min(MF_CN, m - c0);
     for (int r0 = k1; r0 < m; r0 += MF_TILE) {
       const int nr = min(MF_TILE, m - r0);
-      // operands: A rows once per chunk row, B columns once per chunk column
-      if (tid < MF_TILE) pack_panel(F, ld, k0, kb, r0, nr, true, tid, S.Ahi, S.Alo);
-      if (r0 == k1) pack_panel(F, ld, k0, kb, c0, nc, false, tid, S.Bhi, S.Blo);
+      // operands: A rows once per chunk row, B columns once per chunk column; the panel
+      // pass already packed those of the first chunk
+      const bool first = r0 == k1 && c0 == k1;
+      if (!first && tid < MF_TILE) pack_panel(F, ld, k0, kb, r0, nr, true, tid, S.Ahi, S.Alo);
+      if (!first && r0 == k1 && tid < MF_CN) pack_panel(F, ld, k0, kb, c0, nc, false, tid, S.Bhi, S.Blo);
       // the tensor core reads shared memory through the async proxy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_before();
@@ -387,15 +416,15 @@ __device__ __noinline__ void update_tc(TcSmem& S, float* __restrict__ F, int ld,
       if (!mb_wait(&S.bar, ph) && lane == 0) atomicOr(s_flag, 2);
       ph ^= 1u;
       tc_after();
-      // epilogue: warp w reads accumulator lanes 32 (w % 4) .., columns 128 (w / 4) ..
+      // epilogue: warp w reads accumulator lanes 32 (w % 4) .., columns 64 (w / 4) ..
       const int q4 = warp & 3, hcol = warp >> 2;
       const int r = r0 + 32 * q4 + lane;
-      const int cb = c0 + 128 * hcol;
+      const int cb = c0 + 64 * hcol;
       if (r0 + 32 * q4 < m && cb < m) {   // warp-uniform
-        const uint32_t base = S.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(128 * hcol);
+        const uint32_t base = S.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(64 * hcol);
         const int rr = r < m ? r : m - 1;
 #pragma unroll 1
-        for (int h16 = 0; h16 < 8; ++h16) {
+        for (int h16 = 0; h16 < 4; ++h16) {
           const int cb2 = cb + 16 * h16;
           if (cb2 >= m) break;
           uint32_t d[16];
@@ -403,7 +432,7 @@ __device__ __noinline__ void update_tc(TcSmem& S, float* __restrict__ F, int ld,
           // the front's current values, all loads in flight together (clamped addresses)
           float f[16];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) f[c] = ldcg(F + (int64_t)(cb2 + c < m ? cb2 + c : m - 1) * ld + rr);
+          for (int c = 0; c < 16; ++c) f[c] = F[(int64_t)(cb2 + c < m ? cb2 + c : m - 1) * ld + rr];
           tm_wait_ld();
           if (r < m) {
 #pragma unroll
@@ -423,7 +452,7 @@ __device__ __noinline__ void update_tc(TcSmem& S, float* __restrict__ F, int ld,
 struct MFArgs {
   const MFSysDev* sys;
   const MFFrontDev* fronts;
-  int nfront;
+  int task0, ntask;   // fronts task0 .. task0 + ntask - 1 are factored
   const int32_t* relmap;
   const int64_t* colptr;
   const int32_t* orig_k;
@@ -438,19 +467,11 @@ struct MFArgs {
 // the CSR values it owns (distinct positions), then the Schur complement of each child in
 // turn (distinct positions within one child), so the sums do not depend on scheduling.
 template <typename T>
-__device__ __noinline__ void assemble_front(const MFArgs& A, const MFFrontDev& Fd, T* __restrict__ Fall, const double* vals) {
+__device__ __noinline__ void assemble_front(const MFArgs& A, const MFFrontDev& Fd, T* __restrict__ F, int ld,
+                                           const T* __restrict__ Fall, const double* vals) {
   const int tid = threadIdx.x;
-  T* F = Fall + Fd.f_off;
-  const int m = Fd.m, ld = Fd.ld;
-  {
-    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-    constexpr int E = sizeof(V) / sizeof(T);
-    V z;
-    memset(&z, 0, sizeof(V));
-    V* Fv = reinterpret_cast<V*>(F);
-    const int nv = ld * m / E;
-    for (int q = tid; q < nv; q += MF_THREADS) Fv[q] = z;
-  }
+  const int m = Fd.m;
+  for (int q = tid; q < ld * m; q += MF_THREADS) F[q] = T(0);
   __syncthreads();
   {
     const int64_t b = A.colptr[Fd.colptr_off], e = A.colptr[Fd.colptr_off + m];
@@ -534,6 +555,11 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
     Pp = reinterpret_cast<PanelSmem<T>*>(smem_raw + (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T));
   }
   PanelSmem<T>& P = *Pp;
+  // the front itself goes to the shared memory left after the fixed part when it fits
+  constexpr size_t fixed = TC ? sizeof(TcSmem) : (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T) + sizeof(PanelSmem<T>);
+  constexpr size_t fs_off = (fixed + 127) & ~(size_t)127;
+  T* Fs = reinterpret_cast<T*>(smem_raw + fs_off);
+  const int64_t fs_cap = (int64_t)(MF_SMEM - fs_off) / (int64_t)sizeof(T);
   const int epoch = ld_acquire(&A.sched[2]);
   unsigned ph = 0;
   if constexpr (TC) {
@@ -547,8 +573,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
     tc_after();
   }
   for (;;) {
-    const int f = next_task(A.sched, &s_task);
-    if (f >= A.nfront) break;
+    const int t = next_task(A.sched, &s_task);
+    if (t >= A.ntask) break;
+    const int f = A.task0 + t;
     const MFFrontDev& Fd = A.fronts[f];
     const MFSysDev& S = A.sys[Fd.sys];
     if (tid == 0) {
@@ -557,11 +584,15 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
       if (Fd.nchild > 1 && !wait_flag(&A.flag[Fd.child1], epoch)) s_flag |= 4;
     }
     __syncthreads();
-    assemble_front<T>(A, Fd, Fall, A.vals + S.val_off);
-    T* F = Fall + Fd.f_off;
+    T* Fg = Fall + Fd.f_off;
+    const int lds = Fd.m | 1;   // odd stride: row-wise accesses in shared memory are conflict free
+    const bool sh = (int64_t)Fd.m * lds <= fs_cap;
+    T* F = sh ? Fs : Fg;
+    const int ld = sh ? lds : Fd.ld;
+    assemble_front<T>(A, Fd, F, ld, Fall, A.vals + S.val_off);
     for (int k0 = 0, kk = 0; k0 < Fd.p; k0 += MF_NB, ++kk) {
       const int kb = min(MF_NB, Fd.p - k0), k1 = k0 + kb;
-      pivot_block<T>(P, F, Fd.ld, k0, kb, &s_flag);
+      pivot_block<T>(P, F, ld, k0, kb, &s_flag);
       T* dv = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB;
       for (int q = tid; q < MF_NB * MF_NB; q += blockDim.x) {
         dv[q] = P.Li[q >> 5][q & 31];
@@ -571,18 +602,28 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
         __syncthreads();
         continue;
       }
-      panel_lu<T>(P, F, Fd.ld, Fd.m, k0, kb, k1);
+      if constexpr (TC) panel_lu<T>(P, F, ld, Fd.m, k0, kb, k1, TS.Ahi, TS.Alo, TS.Bhi, TS.Blo);
+      else panel_lu<T>(P, F, ld, Fd.m, k0, kb, k1);
       if constexpr (TC) {
         if (s_flag & 2) continue;   // a bounded wait gave up: issue no further products
-        update_tc(TS, F, Fd.ld, Fd.m, k0, kb, k1, ph, &s_flag);
+        update_tc(TS, F, ld, Fd.m, k0, kb, k1, ph, &s_flag);
       } else {
         const int nt = (Fd.m - k1 + MF_TILE - 1) / MF_TILE;
         for (int t = 0; t < nt * nt; ++t)
-          update_tile_fma<T>(F, Fd.ld, Fd.m, k0, kb, k1 + (t % nt) * MF_TILE, k1 + (t / nt) * MF_TILE, As,
+          update_tile_fma<T>(F, ld, Fd.m, k0, kb, k1 + (t % nt) * MF_TILE, k1 + (t / nt) * MF_TILE, As,
                              As + MF_NB * (MF_TILE + 4));
       }
     }
     __syncthreads();
+    if (sh) {
+      // factors and Schur complement to the front's place in global memory
+      const int m = Fd.m;
+      for (int q = tid; q < m * m; q += MF_THREADS) {
+        const int j = q / m, i = q - j * m;
+        Fg[(int64_t)j * Fd.ld + i] = Fs[j * lds + i];
+      }
+      __syncthreads();
+    }
     if (tid == 0) {
       if (s_flag) atomicOr(&A.status[S.sid], s_flag);
       __threadfence();
@@ -613,13 +654,13 @@ struct MFSolveArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(MF_THREADS, 1)
+__global__ void __launch_bounds__(MF_STHREADS, 4)
     mf_solve_kernel(MFSolveArgs A, const T* __restrict__ Fall, const T* __restrict__ dinv,
                     const double* __restrict__ rhs, double* __restrict__ x, int accumulate, T* __restrict__ yv,
                     T* __restrict__ dvec, T* __restrict__ upd) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   T* w = reinterpret_cast<T*>(smem_raw);
-  __shared__ T red[MF_THREADS / 32][MF_NB];
+  __shared__ T red[MF_STHREADS / 32][MF_NB];
   __shared__ T blk[MF_NB];
   __shared__ T Dinv[MF_NB * MF_NB];
   __shared__ int s_task, s_any;
@@ -666,7 +707,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
         const int kb = min(MF_NB, p - k0);
         const T* Li = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB;
 #pragma unroll
-        for (int u = 0; u < MF_NB * MF_NB / MF_THREADS; ++u) Dinv[tid + u * MF_THREADS] = ldcg(Li + tid + u * MF_THREADS);
+        for (int u = 0; u < MF_NB * MF_NB / MF_STHREADS; ++u) Dinv[tid + u * MF_STHREADS] = ldcg(Li + tid + u * MF_STHREADS);
         __syncthreads();
         if (warp == 0) {
           T s = T(0);
@@ -715,17 +756,17 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
         T s = T(0);
         const T* Ui = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB + MF_NB * MF_NB;
 #pragma unroll
-        for (int u = 0; u < MF_NB * MF_NB / MF_THREADS; ++u) Dinv[tid + u * MF_THREADS] = ldcg(Ui + tid + u * MF_THREADS);
+        for (int u = 0; u < MF_NB * MF_NB / MF_STHREADS; ++u) Dinv[tid + u * MF_STHREADS] = ldcg(Ui + tid + u * MF_STHREADS);
         if (lane < kb) {
           int j = k1 + warp;
-          for (; j + 3 * (MF_THREADS / 32) < m; j += 4 * (MF_THREADS / 32)) {
+          for (; j + 3 * (MF_STHREADS / 32) < m; j += 4 * (MF_STHREADS / 32)) {
             T f4[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) f4[u] = ldcg(F + (int64_t)(j + u * (MF_THREADS / 32)) * Fd.ld + k0 + lane);
+            for (int u = 0; u < 4; ++u) f4[u] = ldcg(F + (int64_t)(j + u * (MF_STHREADS / 32)) * Fd.ld + k0 + lane);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s += f4[u] * w[j + u * (MF_THREADS / 32)];
+            for (int u = 0; u < 4; ++u) s += f4[u] * w[j + u * (MF_STHREADS / 32)];
           }
-          for (; j < m; j += MF_THREADS / 32) s += ldcg(F + (int64_t)j * Fd.ld + k0 + lane) * w[j];
+          for (; j < m; j += MF_STHREADS / 32) s += ldcg(F + (int64_t)j * Fd.ld + k0 + lane) * w[j];
         }
         red[warp][lane] = s;
         __syncthreads();
@@ -734,7 +775,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
           if (lane < kb) {
             z = w[k0 + lane];
 #pragma unroll
-            for (int q = 0; q < MF_THREADS / 32; ++q) z -= red[q][lane];
+            for (int q = 0; q < MF_STHREADS / 32; ++q) z -= red[q][lane];
           }
           blk[lane] = z;
           __syncwarp();
@@ -765,24 +806,23 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
 
 // ---------------------------------------------------------------- launchers
 template <typename T>
-size_t mf_factor_smem(bool tc) {
-  if (tc && sizeof(T) == 4) return sizeof(TcSmem);
-  return (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T) + sizeof(PanelSmem<T>);
+size_t mf_factor_smem(bool) {
+  return MF_SMEM;   // fixed part + the front when it fits (one CTA per SM)
 }
 
-static int mf_grid(const void* fn, size_t smem, int cap) {
+static int mf_grid(const void* fn, size_t smem, int cap, int threads = MF_THREADS) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, MF_THREADS, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   const int g = nsm * (per > 0 ? per : 1);
   return cap > 0 && cap < g ? cap : g;
 }
 
 template <typename T>
-cudaError_t launch_mf_factor(const MFLaunch& L, T* F, T* dinv, int tc, cudaStream_t st) {
-  if (L.nfront == 0) return cudaSuccess;
-  MFArgs A{L.sys, L.fronts, L.nfront, L.relmap, L.colptr, L.orig_k, L.orig_ij, L.vals, L.status, L.sched,
+cudaError_t launch_mf_factor(const MFLaunch& L, int task0, int ntask, T* F, T* dinv, int tc, cudaStream_t st) {
+  if (ntask <= 0) return cudaSuccess;
+  MFArgs A{L.sys, L.fronts, task0, ntask, L.relmap, L.colptr, L.orig_k, L.orig_ij, L.vals, L.status, L.sched,
            L.fflag};
   const bool use_tc = tc && sizeof(T) == 4;
   const size_t smem = mf_factor_smem<T>(use_tc);
@@ -794,7 +834,7 @@ cudaError_t launch_mf_factor(const MFLaunch& L, T* F, T* dinv, int tc, cudaStrea
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       // at most two CTAs per SM (shared memory), each allocating half of the tensor memory
-      const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), L.nfront);
+      const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), ntask);
       fn<<<grid, MF_THREADS, smem, st>>>(A, F, dinv);
       return cudaGetLastError();
     }
@@ -802,7 +842,7 @@ cudaError_t launch_mf_factor(const MFLaunch& L, T* F, T* dinv, int tc, cudaStrea
   auto fn = mf_factor_kernel<T, false>;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), L.nfront);
+  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), ntask);
   fn<<<grid, MF_THREADS, smem, st>>>(A, F, dinv);
   return cudaGetLastError();
 }
@@ -817,14 +857,14 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
   auto fn = mf_solve_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap), 2 * L.nfront);
-  fn<<<grid, MF_THREADS, smem, st>>>(A, F, dinv, r, x, accumulate, yv, dv, upd);
+  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap, MF_STHREADS), 2 * L.nfront);
+  fn<<<grid, MF_STHREADS, smem, st>>>(A, F, dinv, r, x, accumulate, yv, dv, upd);
   return cudaGetLastError();
 }
 
 #define TPNS_MF_INST(T)                                                                                      \
   template size_t mf_factor_smem<T>(bool);                                                                  \
-  template cudaError_t launch_mf_factor<T>(const MFLaunch&, T*, T*, int, cudaStream_t);                     \
+  template cudaError_t launch_mf_factor<T>(const MFLaunch&, int, int, T*, T*, int, cudaStream_t);          \
   template cudaError_t launch_mf_solve<T>(const MFLaunch&, const T*, const T*, const double*, double*, int, \
                                           const int*, T*, T*, T*, int, cudaStream_t);
 TPNS_MF_INST(float)

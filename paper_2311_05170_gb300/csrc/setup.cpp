@@ -326,8 +326,9 @@ static bool finish_problem(Problem& P) {
 
 static const char* kLongRun = "a matrix or vector entry receives more than 32 element contributions";
 
-// Multifrontal analysis of a local Oseen system: the unknowns' half-grid coordinates in the
-// box (vertices at even coordinates) drive the nested dissection.
+// Multifrontal analysis of a local system (Oseen, or the pattern shared by the three Darcy
+// fields): the unknowns' half-grid coordinates in the box (vertices at even coordinates) drive
+// the nested dissection.
 static std::string analyse_mf(Problem& P, int leaf) {
   const int nI = 2 * (P.i1 - P.i0) + 1;
   std::vector<int32_t> coord((size_t)P.n * 2);
@@ -451,7 +452,7 @@ std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd
         make_problem(P, m, region == 0 ? PK_OSEEN : PK_DARCY, region, false, i0, i1, j0, j1, di0,
                      di1, dj0, dj1);
         if (!finish_problem(P)) return kLongRun;
-        if (mf_leaf > 0 && P.kind == PK_OSEEN) {
+        if (mf_leaf > 0) {
           std::string e = analyse_mf(P, mf_leaf);
           if (!e.empty()) return e;
         }

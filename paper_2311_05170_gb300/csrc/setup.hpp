@@ -61,7 +61,7 @@ struct Problem {
   std::vector<int32_t> mtgt, msrc;   // element matrix entry -> CSR entry
   std::vector<int32_t> rtgt, rsrc;   // element vector entry -> unknown
   double lu_flops = 0;               // sum over columns of 2 * (#L entries) * (#U entries) + (#L)
-  MFSymbolic mf;                     // multifrontal analysis (local Oseen problems)
+  MFSymbolic mf;                     // multifrontal analysis (local problems)
   int slots() const { return kind == PK_OSEEN ? 15 : 6; }
 };
 
@@ -84,8 +84,8 @@ struct Layout {
 };
 
 // Build everything from the ABI descriptors; returns "" on success or an error message.
-// mf_leaf > 0: also run the multifrontal analysis of every local Oseen system with leaves
-// of at most mf_leaf unknowns.
+// mf_leaf > 0: also run the multifrontal analysis of every local system with leaves of at
+// most mf_leaf unknowns.
 std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf = 0);
 
 // Reference-element integrals (computed by the degree-5 rule) and quadrature tables.
