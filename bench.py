@@ -76,6 +76,114 @@ def oracle_sample(nsteps, warmup=1):
     return d["dofs"] * d["steps"] / d["secs"], d
 
 
+POOL_SNIPPET = r"""
+import json, multiprocessing as mp, os, sys, time
+sys.path.insert(0, %r)
+import workloads as W
+from oracle.scheme import TwoGridOracle
+
+def worker(conn, mine, nsteps):
+    # one rank of the paper's layout: the coarse solve (replicated) plus its own subdomains
+    w = W.config_graded(nsteps=nsteps)
+    o = TwoGridOracle(w)
+    conn.send("ready")
+    while conn.recv() == "step":
+        d = o.step_inputs()
+        out = {}
+        for kind, j in mine:
+            if kind == 0:
+                out[(0, j)] = o.local_fluid(j, d["t"], d["uH1h"], d["uH0h"], d["pH1h"], d["pFn_c"])
+            else:
+                out[(1, j)] = o.local_porous(j, d["t"], d["pdH1h"], d["pdH0h"], d["ucn_p"])
+        for (kind, j), v in out.items():
+            if kind == 0:
+                o.ec[j], o.dc[j] = v
+            else:
+                o.ep[j] = v
+        o.uH, o.pH, o.pdH = d["u1"], d["p1"], d["pd1"]
+        o.n += 1
+        conn.send(out)
+
+if __name__ == "__main__":
+    nsteps, warm, nwork = %d, %d, %d
+    w = W.config_graded(nsteps=nsteps + warm)
+    o = TwoGridOracle(w)
+    tasks = [(0, j) for j in range(len(o.sub_c))] + [(1, j) for j in range(len(o.sub_p))]
+    nwork = max(1, min(nwork, len(tasks)))
+    ctx = mp.get_context("spawn")
+    pipes, procs = [], []
+    for r in range(nwork):
+        a, b = ctx.Pipe()
+        pr = ctx.Process(target=worker, args=(b, tasks[r::nwork], nsteps + warm))
+        pr.start()
+        pipes.append(a)
+        procs.append(pr)
+    for a in pipes:
+        a.recv()
+    def step():
+        for a in pipes:
+            a.send("step")
+        d = o.step_inputs()
+        for a in pipes:
+            for (kind, j), v in a.recv().items():
+                if kind == 0:
+                    o.ec[j], o.dc[j] = v
+                else:
+                    o.ep[j] = v
+        o.uH, o.pH, o.pdH = d["u1"], d["p1"], d["pd1"]
+        o.n += 1
+        o.glue()
+    for _ in range(warm):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        step()
+    dt = time.perf_counter() - t0
+    for a in pipes:
+        a.send("stop")
+    for pr in procs:
+        pr.join()
+    nd = 2 * o.mch.nn + o.mch.nv + 3 * o.mph.nn
+    print(json.dumps({"secs": dt, "steps": nsteps, "dofs": int(nd), "workers": nwork}))
+"""
+
+
+def oracle_pool_sample(nsteps, warmup=1):
+    """Time the oracle with a pool of min(#subdomains, nproc) worker processes, one per rank of
+    the paper's layout (coarse solve replicated, subdomains split over the workers, glue in the
+    parent), in a fresh process that starts them with spawn."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = POOL_SNIPPET % (ROOT, nsteps, warmup, os.cpu_count() or 1)
+    import tempfile
+    # spawned workers re-import the main module, so it has to be a file
+    with tempfile.NamedTemporaryFile("w", suffix="_oracle_pool.py", delete=False) as fh:
+        fh.write(code)
+        path = fh.name
+    try:
+        r = subprocess.run([sys.executable, path], capture_output=True, text=True, env=env, timeout=1800)
+    finally:
+        os.unlink(path)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["dofs"] * d["steps"] / d["secs"], d
+
+
+def host_cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def cpu_baseline_obj(value, d):
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{d['steps']} full time steps (coarse + all local solves + glue) of the same workload, "
@@ -338,6 +446,17 @@ def main():
             cpu = cpu_baseline_obj(v, d)
         except Exception as ex:  # the line still reports the GPU numbers
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+        cpu["nproc"] = os.cpu_count()
+        cpu["cpu_model"] = host_cpu_model()
+        try:
+            vp, dp = oracle_pool_sample(args.cpu_sample_steps)
+            cpu["pool"] = {"value": vp, "unit": UNIT, "cores": dp["workers"],
+                           "sample": f"{dp['steps']} full time steps, {dp['workers']} worker processes (spawned): "
+                                     "the coarse solve replicated in every worker, the 32 subdomain problems "
+                                     "split over the workers, the glue in the parent; "
+                                     f"{dp['secs']:.1f} s"}
+        except Exception as ex:
+            cpu["pool"] = {"value": None, "sample": f"failed: {str(ex)[:200]}"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value if valid else None, "unit": UNIT, "n_gpus": world, "steps": K,

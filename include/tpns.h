@@ -152,6 +152,22 @@ typedef struct {
   int32_t mf_ctas;          /* multifrontal: CTAs of the factorisation and solve launches
                                (0 = as many as are resident at once: one per SM for the
                                tensor-core factorisation) */
+  int32_t rank, nranks;     /* split of one simulation over nranks contexts (one per GPU;
+                               0 / 0 = whole simulation): the subdomains of each region are
+                               assigned to ranks by estimated per-step work, largest first, each
+                               to the least loaded rank (the same on every rank, no
+                               communication); a context solves only its own subdomains and
+                               replicates the coarse solve (Algorithm 3 Steps 1 and 3), and
+                               tpns_get_field returns its part of the glued field: the sum over
+                               ranks of the returned fields is the glued field of Step 4 (rank 0
+                               adds the coarse interpolant).  nranks must not exceed the number
+                               of subdomains per region. */
+  int32_t algorithm;        /* 0 or 3: Algorithm 3 (two-grid, local parallel); 1: Algorithm 1
+                               (Sec. 3.3: the decoupled partitioned time stepping on the fine
+                               grid itself), run on the same kernels as Step 1 with the coarse
+                               mesh set to the fine mesh (uniform fine rows only; the partition
+                               is ignored; the whole fine problem must fit the coarse-solve
+                               limits: Oseen system below about 25,000 unknowns in FP64) */
 } tpns_options;
 
 /* Build meshes, subdomains, sparsity, scatter maps and band orderings on the host, upload

@@ -71,6 +71,8 @@ struct tpns_ctx {
   // multifrontal factorisation of the local Oseen systems
   bool mf = false;
   int mf_leaf = 96, mf_tc = 1, mf_m_max = 1, mf_oseen_fronts = 0;
+  int rank = 0, nranks = 1;   // split of one simulation over contexts (see tpns_options)
+  bool alg1 = false;          // Algorithm 1: the coarse mesh is the fine mesh, no local phase
   double mf_flops = 0, mf_factor_entries = 0, mf_dinv_entries = 0;
   MFLaunch mfl{};
   std::vector<MFSysDev> h_mfsys;
@@ -239,7 +241,7 @@ static std::vector<int32_t> inverse_map(const std::vector<int32_t>& g, int n) {
 static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns_partition_desc& pd,
                              size_t budget) {
   Layout& L = ctx->L;
-  std::string msg = build_layout(md, pd, L, ctx->mf ? ctx->mf_leaf : 0);
+  std::string msg = build_layout(md, pd, L, ctx->mf ? ctx->mf_leaf : 0, ctx->rank, ctx->nranks);
   if (!msg.empty()) {
     ctx->err = msg;
     return TPNS_EINVAL;
@@ -560,6 +562,9 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(dalloc(ctx, &ctx->d_relprev, ctx->nsys));
   TRY(dalloc(ctx, &ctx->d_done, ctx->nsys));
   TRY(dalloc(ctx, &ctx->d_iters, ctx->nsys));
+  CK(cudaMemset(ctx->d_rel, 0, ctx->nsys * sizeof(double)));
+  CK(cudaMemset(ctx->d_iters, 0, ctx->nsys * sizeof(int)));
+  CK(cudaMemset(ctx->d_done, 0, ctx->nsys * sizeof(int)));
   TRY(dalloc(ctx, &ctx->d_status, ctx->nsys));
   CK(cudaMemset(ctx->d_status, 0, ctx->nsys * sizeof(int)));
   TRY(dalloc(ctx, &ctx->d_ticket, ctx->nsys));
@@ -847,6 +852,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   G.FW1 = ctx->d_FW1; G.FP1 = ctx->d_FP1; G.FPD1 = ctx->d_FPD1;
   G.out_u = ctx->d_out_u; G.out_p = ctx->d_out_p; G.out_pd = ctx->d_out_pd;
   G.nnc = nnc; G.nvc = nvc; G.nnp = nnp;
+  G.add_coarse = ctx->rank == 0 ? 1 : 0;
   ctx->mfl.vals = ctx->d_vals;
   ctx->mfl.status = ctx->d_status;
   return TPNS_OK;
@@ -1080,8 +1086,17 @@ static tpns_status enqueue_step(tpns_ctx* ctx, bool coarse) {
     TRY(coarse_step(ctx));
     ph_end(ctx, PH_COARSE);
   }
-  if (ctx->prec == TPNS_FP64) TRY(local_step<double>(ctx));
-  else TRY(local_step<float>(ctx));
+  if (ctx->alg1) {
+    // Algorithm 1: the coarse (= fine) solution is the result; the corrections stay zero
+    ph_begin(ctx, PH_STATE_GLUE);
+    TRY(prolong_and_glue(ctx));
+    CK(launch_glue(ctx->glue, ctx->stream));
+    ph_end(ctx, PH_STATE_GLUE);
+  } else if (ctx->prec == TPNS_FP64) {
+    TRY(local_step<double>(ctx));
+  } else {
+    TRY(local_step<float>(ctx));
+  }
   return end_step_device(ctx);
 }
 
@@ -1483,6 +1498,10 @@ static bool read_options(const tpns_options* o, tpns_options& opt) {
   if (o) opt = *o;
   if (opt.local_factor != TPNS_FACTOR_MULTIFRONTAL && opt.local_factor != TPNS_FACTOR_BAND) return false;
   if (opt.mf_leaf < 0 || opt.mf_ctas < 0) return false;
+  if (opt.nranks < 0 || (opt.nranks > 0 && (opt.rank < 0 || opt.rank >= opt.nranks))) return false;
+  if (opt.nranks == 0) opt.nranks = 1;
+  if (opt.algorithm == 0) opt.algorithm = 3;
+  if (opt.algorithm != 1 && opt.algorithm != 3) return false;
   if (opt.mf_leaf == 0) opt.mf_leaf = 96;
   if (opt.mf_leaf < 8) return false;
   return true;
@@ -1515,8 +1534,29 @@ tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params
     return TPNS_EINVAL;
   }
   if (data->mms_id != 0 && data->mms_id != 1 && data->mms_id != 3) { g_err = "unknown mms_id"; return TPNS_EINVAL; }
+  tpns_mesh_desc md1 = *mesh;
+  tpns_partition_desc pd1 = *part;
+  if (opt.algorithm == 1) {
+    // Algorithm 1: the same decoupled steps on the fine grid itself (H = h, no subdomains)
+    const int r = mesh->fine_rows_from_gamma[0];
+    for (int c = 0; c < mesh->ny_coarse && c < TPNS_MAX_COARSE_ROWS; ++c)
+      if (mesh->fine_rows_from_gamma[c] != r) { g_err = "Algorithm 1 needs uniform fine rows"; return TPNS_EINVAL; }
+    if ((int64_t)mesh->ny_coarse * r > TPNS_MAX_COARSE_ROWS || opt.nranks > 1) {
+      g_err = "Algorithm 1: more fine rows than TPNS_MAX_COARSE_ROWS, or a rank split";
+      return TPNS_EINVAL;
+    }
+    md1.nx_coarse = mesh->nx_coarse * mesh->fine_per_coarse_x;
+    md1.fine_per_coarse_x = 1;
+    md1.ny_coarse = mesh->ny_coarse * r;
+    for (int c = 0; c < md1.ny_coarse; ++c) md1.fine_rows_from_gamma[c] = 1;
+    pd1.nsub_x = pd1.nsub_y = 1;
+    pd1.overlap = 0;
+    mesh = &md1;
+    part = &pd1;
+  }
   tpns_ctx* ctx = new (std::nothrow) tpns_ctx();
   if (!ctx) { g_err = "host allocation failed"; return TPNS_ENOMEM; }
+  ctx->alg1 = opt.algorithm == 1;
   cudaGetDevice(&ctx->device);
   ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   if (!ctx->stream) {
@@ -1529,6 +1569,8 @@ tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params
   ctx->mf = opt.local_factor == TPNS_FACTOR_MULTIFRONTAL;
   ctx->mf_leaf = opt.mf_leaf;
   ctx->mf_tc = precision != TPNS_FP64 && !opt.mf_cuda_cores;
+  ctx->rank = opt.rank;
+  ctx->nranks = opt.nranks;
   ctx->mfl.grid_cap = opt.mf_ctas;
   Phys& P = ctx->phys;
   P.nu = params->nu; P.eta = params->eta; P.rho = params->rho; P.mu = params->mu; P.alpha = params->alpha;
@@ -1590,7 +1632,9 @@ tpns_status tpns_layout_create_ex(const tpns_mesh_desc* mesh, const tpns_partiti
   ctx->host_only = true;
   ctx->mf = opt.local_factor == TPNS_FACTOR_MULTIFRONTAL;
   ctx->mf_leaf = opt.mf_leaf;
-  std::string msg = build_layout(*mesh, *part, ctx->L, ctx->mf ? ctx->mf_leaf : 0);
+  ctx->rank = opt.rank;
+  ctx->nranks = opt.nranks;
+  std::string msg = build_layout(*mesh, *part, ctx->L, ctx->mf ? ctx->mf_leaf : 0, ctx->rank, ctx->nranks);
   if (!msg.empty()) {
     g_err = msg;
     delete ctx;

@@ -123,6 +123,7 @@ struct GlueArgs {
   const double *FW1, *FP1, *FPD1;
   double *out_u, *out_p, *out_pd;
   int nnc, nvc, nnp;
+  int add_coarse;   // 1: add the coarse interpolant (one rank of a split simulation, or the whole)
 };
 cudaError_t launch_glue(const GlueArgs& g, cudaStream_t st);
 // coarse Newton: u += delta (all coarse nodes), p += delta_p; convergence flag

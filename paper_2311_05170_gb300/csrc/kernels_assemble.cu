@@ -512,7 +512,7 @@ cudaError_t launch_prolong(int n2c, int n1c, int n2p, const int32_t* pc2i, const
 __global__ void glue_kernel(GlueArgs G) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < G.nnc) {
-    double u0 = G.FW1[2 * i], u1 = G.FW1[2 * i + 1];
+    double u0 = G.add_coarse ? G.FW1[2 * i] : 0.0, u1 = G.add_coarse ? G.FW1[2 * i + 1] : 0.0;
     for (int k = G.gc_ptr[i]; k < G.gc_ptr[i + 1]; ++k) {
       const ProbDev& P = G.fluid[G.gc_prob[k]];
       const int l = G.gc_node[k];
@@ -523,7 +523,7 @@ __global__ void glue_kernel(GlueArgs G) {
     G.out_u[2 * i + 1] = u1;
   }
   if (i < G.nvc) {
-    double p = G.FP1[i];
+    double p = G.add_coarse ? G.FP1[i] : 0.0;
     for (int k = G.gv_ptr[i]; k < G.gv_ptr[i + 1]; ++k) {
       const ProbDev& P = G.fluid[G.gv_prob[k]];
       p += G.gv_w[k] * P.EN[2 * P.nn + G.gv_vert[k]];
@@ -532,7 +532,7 @@ __global__ void glue_kernel(GlueArgs G) {
   }
   if (i < G.nnp) {
     for (int f = 0; f < 3; ++f) {
-      double v = G.FPD1[(int64_t)f * G.nnp + i];
+      double v = G.add_coarse ? G.FPD1[(int64_t)f * G.nnp + i] : 0.0;
       for (int k = G.gp_ptr[i]; k < G.gp_ptr[i + 1]; ++k) {
         const ProbDev& P = G.porous[G.gp_prob[k]];
         v += G.gp_w[k] * P.EN[(int64_t)f * P.nn + G.gp_node[k]];

@@ -419,7 +419,53 @@ static void glue_table(const std::vector<Problem>& probs, int nnodes, bool verti
   }
 }
 
-std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf) {
+// Indices of the problems a rank keeps: estimated per-step work of each problem, largest
+// first, each to the least loaded rank (ties to the lower rank).
+static std::vector<int> owned(const std::vector<Problem>& list, int rank, int nranks) {
+  std::vector<std::pair<double, int>> w;
+  for (int i = 0; i < (int)list.size(); ++i) {
+    const Problem& P = list[i];
+    double entries = P.mf.fronts.empty() ? (double)P.n * (P.kl + P.ku + 1) : P.mf.factor_entries;
+    double work = P.kind == PK_OSEEN ? (P.mf.fronts.empty() ? P.lu_flops : P.mf.flops) + 6.0 * entries
+                                     : 18.0 * entries;   // three fields, about three solve passes
+    w.push_back({-work, i});
+  }
+  std::sort(w.begin(), w.end());
+  std::vector<double> load(nranks, 0.0);
+  std::vector<int> mine;
+  for (auto& e : w) {
+    int r = 0;
+    for (int k = 1; k < nranks; ++k)
+      if (load[k] < load[r]) r = k;
+    load[r] += -e.first;
+    if (r == rank) mine.push_back(e.second);
+  }
+  std::sort(mine.begin(), mine.end());
+  return mine;
+}
+
+// Keep the glue entries of the kept problems (renumbered), with their weights unchanged.
+static void filter_glue(std::vector<int32_t>& ptr, std::vector<int32_t>& prob, std::vector<int32_t>& loc,
+                        std::vector<double>& w, const std::vector<int>& remap) {
+  std::vector<int32_t> p2(ptr.size(), 0), pr2, lo2;
+  std::vector<double> w2;
+  for (size_t i = 0; i + 1 < ptr.size(); ++i) {
+    for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+      if (remap[prob[k]] >= 0) {
+        pr2.push_back(remap[prob[k]]);
+        lo2.push_back(loc[k]);
+        w2.push_back(w[k]);
+      }
+    p2[i + 1] = (int32_t)pr2.size();
+  }
+  ptr.swap(p2);
+  prob.swap(pr2);
+  loc.swap(lo2);
+  w.swap(w2);
+}
+
+std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf,
+                         int rank, int nranks) {
   if (md.nx_coarse <= 0 || md.ny_coarse <= 0 || md.ny_coarse > TPNS_MAX_COARSE_ROWS ||
       md.fine_per_coarse_x <= 0)
     return "invalid mesh description";
@@ -490,6 +536,27 @@ std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd
     if (L.gc_ptr[i + 1] == L.gc_ptr[i]) return "a conduit node is in no D_j";
   for (int i = 0; i < L.mph.nn; ++i)
     if (L.gp_ptr[i + 1] == L.gp_ptr[i]) return "a porous node is in no D_j";
+  if (nranks > 1) {
+    if (rank < 0 || rank >= nranks || nranks > (int)L.fluid.size() || nranks > (int)L.porous.size())
+      return "invalid rank split: nranks must not exceed the subdomains per region";
+    for (int region = 0; region < 2; ++region) {
+      std::vector<Problem>& list = region == 0 ? L.fluid : L.porous;
+      const std::vector<int> mine = owned(list, rank, nranks);
+      std::vector<int> remap(list.size(), -1);
+      std::vector<Problem> kept;
+      for (int i : mine) {
+        remap[i] = (int)kept.size();
+        kept.push_back(std::move(list[i]));
+      }
+      list.swap(kept);
+      if (region == 0) {
+        filter_glue(L.gc_ptr, L.gc_prob, L.gc_node, L.gc_w, remap);
+        filter_glue(L.gv_ptr, L.gv_prob, L.gv_vert, L.gv_w, remap);
+      } else {
+        filter_glue(L.gp_ptr, L.gp_prob, L.gp_node, L.gp_w, remap);
+      }
+    }
+  }
   return "";
 }
 

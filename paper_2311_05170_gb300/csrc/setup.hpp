@@ -86,7 +86,11 @@ struct Layout {
 // Build everything from the ABI descriptors; returns "" on success or an error message.
 // mf_leaf > 0: also run the multifrontal analysis of every local system with leaves of at
 // most mf_leaf unknowns.
-std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf = 0);
+// rank / nranks > 1: keep only this rank's local problems (estimated per-step work, largest
+// first to the least loaded rank, per region); the glue tables keep the weights of the
+// whole partition but only the entries of the kept problems.
+std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf = 0,
+                         int rank = 0, int nranks = 1);
 
 // Reference-element integrals (computed by the degree-5 rule) and quadrature tables.
 struct RefTables {

@@ -1,12 +1,17 @@
-"""Multi-GPU layout: independent simulations per rank, no data-path collective.
+"""Multi-GPU layouts.
 
 Within one time step the local problems of the two-grid method (Algorithm 3) are coupled
-only through the coarse solve that precedes them and the glue that follows, and one
-simulation's local problems fit one GPU, so a simulation is never split across GPUs.  GPUs
-run independent simulations instead: replicas of one workload, or different requests of a
-serving workload.  Ranks exchange nothing while they compute; the collectives here run after
-a timed region, to reduce timings and statistics (max of the per-rank times, sums of the
-units processed, the pooled list of per-step latencies).
+only through the coarse solve that precedes them and the glue that follows.  Two layouts:
+
+* independent simulations per rank (replicas of one workload, or the requests of a serving
+  workload), with no data-path collective; the collectives run after a timed region, to
+  reduce timings and statistics (max of the per-rank times, sums of the units processed, the
+  pooled list of per-step latencies);
+* one simulation split over ranks (tpns_options.rank / nranks): every rank repeats the
+  coarse solve, solves its own subdomains (assigned by estimated work inside the library, the
+  same on every rank) and returns its part of the glued field; the glued field of Step 4 is
+  the sum of the parts, so the only exchange is one sum (all-reduce) of the fields, and only
+  when a global field is wanted.
 
 Every function takes the process group explicitly (None = a single process), so the same
 code runs on NCCL with CUDA tensors and on gloo with CPU tensors.
@@ -71,3 +76,19 @@ def gather_lists(values, dist_on, group=None):
     out = [None] * dist.get_world_size(group)
     dist.all_gather_object(out, list(values), group=group)
     return [x for part in out for x in part]
+
+
+def reduce_fields(parts, dist_on, device="cpu", group=None):
+    """Glued fields of a simulation split over ranks: the sum over ranks of each rank's part
+    (dict field -> 1D float64 array); every rank gets the whole field."""
+    if not dist_on:
+        return {k: v.copy() for k, v in parts.items()}
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    out = {}
+    for k in sorted(parts):
+        t = torch.from_numpy(np.ascontiguousarray(parts[k])).to(device)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        out[k] = t.cpu().numpy()
+    return out

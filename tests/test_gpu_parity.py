@@ -298,3 +298,19 @@ def test_standalone_band_solve_matches_sparse_lu(native, prec, j):
     ref = spla.splu(A.tocsc()).solve(rhs)
     got = x.cpu().numpy()
     assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_algorithm1_on_the_same_kernels(native, prec):
+    """Algorithm 1 (the partitioned time stepping on the fine grid itself) is Step 1 with the
+    coarse mesh set to the fine mesh; it matches the oracle's scheme on that mesh, where the
+    local corrections vanish (H = h)."""
+    w = W.config_small(nsteps=3)
+    o = TwoGridOracle(W.as_algorithm1(w))
+    o.run(3)
+    s = native.Solver(w, precision=prec, algorithm=1)
+    s.step(3)
+    f = s.fields()
+    s.close()
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))

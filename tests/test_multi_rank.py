@@ -75,3 +75,78 @@ def test_single_process_helpers_need_no_group():
     assert gather_lists([1, 2], False) == [1, 2]
     with pytest.raises(ValueError):
         shard_requests(reqs, 2, 2)
+
+
+def _split_worker(rank, world, port, q):
+    """One rank of a simulation split over two ranks, on CPU: the layout this rank's context
+    would own (host-only), and the all-reduce of field parts."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import numpy as np
+        from paper_2311_05170_gb300 import native
+        from paper_2311_05170_gb300.shard import reduce_fields
+        w = W.config_graded(nsteps=1)
+        s = native.Solver(w, host_only=True, rank=rank, nranks=world)
+        mine = []
+        j = 0
+        while True:
+            try:
+                info = s.debug_system(j)
+            except native.TpnsError:
+                break
+            mine.append((int(info["node"].min()), len(info["node"]), int(info["comp"].max())))
+            j += 1
+        s.close()
+        sig = gather_lists(mine, True)
+        parts = {"a": np.arange(5, dtype=np.float64) * (rank + 1), "b": np.full(3, float(rank))}
+        tot = reduce_fields(parts, True)
+        q.put((rank, mine, sig, {k: v.tolist() for k, v in tot.items()}))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_one_simulation_split_over_two_gloo_ranks():
+    """The two ranks' subdomain sets are disjoint and together are the whole partition (as the
+    library builds it on each rank without communicating), the Oseen / Darcy split is even, and
+    the field parts sum to the whole field on every rank."""
+    from paper_2311_05170_gb300 import native, build
+    build.build()
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_split_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    s = native.Solver(W.config_graded(nsteps=1), host_only=True)
+    full = []
+    j = 0
+    while True:
+        try:
+            info = s.debug_system(j)
+        except native.TpnsError:
+            break
+        full.append((int(info["node"].min()), len(info["node"]), int(info["comp"].max())))
+        j += 1
+    s.close()
+    a, b = res[0][1], res[1][1]
+    assert sorted(a + b) == sorted(full) and not set(a) & set(b)
+    for r in res:
+        assert sorted(r[2]) == sorted(full)        # the all-gathered view is the same on both ranks
+        assert r[3]["a"] == [0.0, 3.0, 6.0, 9.0, 12.0] and r[3]["b"] == [1.0, 1.0, 1.0]
+    # 16 Oseen systems (comp max 2) and 16 porous problems, split 8 / 8 each
+    for part in (a, b):
+        assert sum(1 for x in part if x[2] == 2) == 8 and sum(1 for x in part if x[2] == 0) == 8
+
+
+def test_split_refuses_more_ranks_than_subdomains():
+    from paper_2311_05170_gb300 import native, build
+    build.build()
+    with pytest.raises(native.TpnsError):
+        native.Solver(W.config_small(nsteps=1), host_only=True, rank=0, nranks=5)

@@ -453,3 +453,27 @@ def test_convergence_rates_theorem_5_4():
     assert rate("u_H1") >= gold["min_velocity_H1_rate"]
     for k in ("pF_L2", "pf_L2", "pm_L2"):
         assert rate(k) >= gold["min_darcy_L2_rate"]
+
+
+@pytest.mark.slow
+def test_algorithm3_approaches_algorithm1_as_H_shrinks():
+    """Algorithms 3 and 1 differ by the two-grid error c (dt + H^{r+1}) (Sec. 5 vs Sec. 3.3;
+    compare Tables 1 and 2 of Sec. 6): halving H (h = H/4, dt fixed) shrinks the difference by
+    more than 3 in every field, and at H = 1/8 the difference is below the larger of the two
+    schemes' own errors against the exact solution (the schemes agree to their accuracy)."""
+    import numpy as np
+    diffs = []
+    for nx in (4, 8):
+        w = W.config_uniform(nx, 4, nsub=(2, 2), overlap=2, dt=0.01, nsteps=5)
+        o3 = TwoGridOracle(w)
+        o3.run(5)
+        o1 = TwoGridOracle(W.as_algorithm1(w))
+        o1.run(5)
+        ex = o3.exact_fine()
+        d = {k: np.linalg.norm(o3.fine[k] - o1.fine[k]) / np.linalg.norm(ex[k]) for k in ex}
+        e1 = {k: np.linalg.norm(o1.fine[k] - ex[k]) / np.linalg.norm(ex[k]) for k in ex}
+        e3 = {k: np.linalg.norm(o3.fine[k] - ex[k]) / np.linalg.norm(ex[k]) for k in ex}
+        diffs.append(d)
+    for k in diffs[0]:
+        assert diffs[0][k] > 3.0 * diffs[1][k], k
+        assert diffs[1][k] < max(e1[k], e3[k]), k

@@ -106,6 +106,18 @@ def config_uniform(nx_coarse, r, nsub=(2, 2), overlap=2, dt=0.01, nsteps=10, mms
                     [r] * nx_coarse, nsub, overlap, dt, nsteps, mms, params or Params())
 
 
+def as_algorithm1(w: Workload) -> Workload:
+    """The same run with the coarse mesh equal to the fine mesh (H = h) and one subdomain per
+    region: the two-grid scheme then reduces to the global fine-grid partitioned time stepping
+    of Algorithm 1 (the local corrections vanish).  Uniform fine rows only."""
+    rows = w.fine_rows_from_gamma[: w.ny_coarse]
+    if len(set(rows)) != 1:
+        raise ValueError("Algorithm 1 workloads need uniform fine rows")
+    r = rows[0]
+    return Workload(w.name + "_alg1", w.nx_coarse * w.fine_per_coarse_x, w.ny_coarse * r, 1,
+                    [1] * (w.ny_coarse * r), (1, 1), 0, w.dt, w.nsteps, w.mms, w.params)
+
+
 def serving_requests(n=512, seed_arrivals=3, rate=20.0):
     """Serving workload: Poisson arrivals (exponential gaps, rate per second); per request a
     seeded h in {1/32, 1/64, 1/128}, H = sqrt(h) rounded (up, finer) to a power of 1/2, a
