@@ -321,7 +321,9 @@ def main():
     for name, vp, opts in (("mf_fp32_cuda_cores", "fp32", {"cuda_cores": True}),
                            ("band_fp32", "fp32", {"factor": "band"}),
                            ("band_tf32_mma_sync", "tf32", {"factor": "band"}),
-                           ("band_bf16_mma_sync", "bf16", {"factor": "band"})):
+                           ("band_bf16_mma_sync", "bf16", {"factor": "band"}),
+                           ("band_bf16_mma_sync_gmres_ir", "bf16", {"factor": "band", "gmres": True,
+                                                                    "ir_classic_max": 1})):
         try:
             sv, msv, _, _, phv, fv = timed_hot(vp, with_phases=True, **opts)
             stv = sv.stats()
@@ -330,7 +332,8 @@ def main():
                               "factor_ms_per_step": phv["band_lu"][0] / K,
                               "relL2_vs_fp64_gpu_max": max(float(np.linalg.norm(fv[k] - f64[k]) / np.linalg.norm(f64[k]))
                                                            for k in fv),
-                              "ir_iters_max": stv["last_ir_iters_max"], "ir_relres_max": stv["last_ir_relres_max"]}
+                              "ir_iters_max": stv["last_ir_iters_max"], "ir_relres_max": stv["last_ir_relres_max"],
+                              "gmres_cycles_last_step": stv["last_gmres_outer"], "gmres_steps": stv["gmres_steps"]}
         except Exception as ex:
             variants[name] = {"error": str(ex)[:160]}
     solve_bytes_step = phases.pop("_solve_bytes") / K
@@ -476,7 +479,8 @@ def main():
             "factorisation_variants": {
                 "what": "other factorisations of the local Oseen systems on the same steps: the multifrontal "
                         "LU with CUDA-core trailing updates, and the band LU (FP32 FMA; mma.sync TF32 with "
-                        "split operands; mma.sync plain BF16); FP64-residual refinement throughout",
+                        "split operands; mma.sync plain BF16, with classic refinement and with one classic "
+                        "pass followed by GMRES-based refinement); FP64-residual refinement throughout",
                 **variants},
             "speedup_vs_fp64_gpu": value / value64,
             "roofline": roof, "kernels": kernels,

@@ -129,6 +129,9 @@ typedef struct {
   double factor_entries;          /* stored entries of one step's Oseen factors (L and U) */
   int64_t mf_fronts;              /* multifrontal: fronts per step (0 with the band LU) */
   double create_ms;               /* host wall time of tpns_create for this context */
+  int32_t last_gmres_outer;       /* GMRES-based refinement cycles run in the last step (0: none
+                                     needed) */
+  int32_t gmres_steps;            /* steps so far that needed them */
 } tpns_stats;
 
 typedef struct tpns_ctx tpns_ctx;
@@ -168,6 +171,15 @@ typedef struct {
                                mesh set to the fine mesh (uniform fine rows only; the partition
                                is ignored; the whole fine problem must fit the coarse-solve
                                limits: Oseen system below about 25,000 unknowns in FP64) */
+  int32_t refinement;       /* 0: classic iterative refinement x += (LU)^{-1} (b - A x), FP64
+                               residuals, stop at the tolerance or on stagnation; 1: the same,
+                               and when a local system is still above the tolerance after a
+                               step's classic passes, restarted GMRES preconditioned by the
+                               factors (FP64 Krylov vectors and Hessenberg problem; GMRES-based
+                               refinement) corrects it before the corrections are glued; the
+                               step then synchronises the stream to check */
+  int32_t ir_classic_max;   /* classic refinement passes per step (0 = 12 for low-precision
+                               factors, 2 for FP64) */
 } tpns_options;
 
 /* Build meshes, subdomains, sparsity, scatter maps and band orderings on the host, upload

@@ -73,6 +73,10 @@ struct tpns_ctx {
   int mf_leaf = 96, mf_tc = 1, mf_m_max = 1, mf_oseen_fronts = 0;
   int rank = 0, nranks = 1;   // split of one simulation over contexts (see tpns_options)
   bool alg1 = false;          // Algorithm 1: the coarse mesh is the fine mesh, no local phase
+  bool gmres = false;         // GMRES-based refinement when classic refinement stagnates
+  int ir_classic_max = 0;     // classic refinement passes per step (0: default)
+  double *gm_V = nullptr, *gm_W = nullptr, *gm_H = nullptr;
+  int* gm_skip = nullptr;
   double mf_flops = 0, mf_factor_entries = 0, mf_dinv_entries = 0;
   MFLaunch mfl{};
   std::vector<MFSysDev> h_mfsys;
@@ -1033,7 +1037,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   };
   // a8: solves with FP64-residual iterative refinement
   const bool fp64 = ctx->prec == TPNS_FP64;
-  const int maxit = fp64 ? 2 : 12;
+  const int maxit = ctx->ir_classic_max > 0 ? ctx->ir_classic_max : fp64 ? 2 : 12;
   const double tol = fp64 ? 1e-14 : 1e-13;
   // the refinement starts from a prediction of the local solutions from the last two steps
   // (2 x^n - x^{n-1}; x^n alone at the second step): the local problems change smoothly in
@@ -1097,6 +1101,8 @@ static tpns_status enqueue_step(tpns_ctx* ctx, bool coarse) {
   } else {
     TRY(local_step<float>(ctx));
   }
+  // with GMRES-based refinement the step ends after the host has checked the local systems
+  if (ctx->gmres && !ctx->alg1) return TPNS_OK;
   return end_step_device(ctx);
 }
 
@@ -1180,6 +1186,89 @@ static tpns_status read_stats(tpns_ctx* ctx) {
   return TPNS_OK;
 }
 
+// GMRES-based refinement of the local systems still above the tolerance after a step's
+// classic passes (restarted GMRES, preconditioned by the factors, FP64 vectors), then new
+// corrections and glue from the refined solutions.  Eager launches with host checks between
+// restart cycles; runs only when needed.
+constexpr int GM_KDIM = 10, GM_CYCLES = 4;
+
+template <typename T>
+static tpns_status gmres_refine(tpns_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const double tol = ctx->prec == TPNS_FP64 ? 1e-14 : 1e-13;
+  const int nloc = (int)ctx->list_local.size();
+  const int gstride = (GM_KDIM + 1) * GM_KDIM + (GM_KDIM + 1) + 2 * GM_KDIM;
+  std::vector<double> rel(ctx->nsys);
+  std::vector<int> skip(ctx->nsys, 1);
+  auto pending = [&]() -> int {
+    int any = 0;
+    std::fill(skip.begin(), skip.end(), 1);
+    for (int s : ctx->list_local)
+      if (!(rel[s] <= tol)) { skip[s] = 0; any = 1; }
+    return any;
+  };
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpy(rel.data(), ctx->d_rel, ctx->nsys * sizeof(double), cudaMemcpyDeviceToHost));
+  ctx->stats.last_gmres_outer = 0;
+  if (!pending()) return TPNS_OK;
+  if (!ctx->gm_V) {
+    TRY(dalloc(ctx, &ctx->gm_V, (size_t)(GM_KDIM + 1) * ctx->xvec_tot));
+    TRY(dalloc(ctx, &ctx->gm_W, (size_t)ctx->xvec_tot));
+    TRY(dalloc(ctx, &ctx->gm_H, (size_t)nloc * gstride));
+    TRY(dalloc(ctx, &ctx->gm_skip, (size_t)ctx->nsys));
+  }
+  T* mfF = reinterpret_cast<T*>(ctx->d_mf_F);
+  T* mfD = reinterpret_cast<T*>(ctx->d_mf_dinv);
+  T* lslab = reinterpret_cast<T*>(ctx->d_lslab_local);
+  T* uslab = reinterpret_cast<T*>(ctx->d_uslab_local);
+  T* dinv = reinterpret_cast<T*>(ctx->d_dinv_local);
+  T* vwork = reinterpret_cast<T*>(ctx->d_vwork);
+  const int nband = (int)ctx->list_band.size();
+  // z = M^{-1} w for the pending systems (the factorisation's own solve, overwriting z)
+  auto precond = [&](const double* w, double* z) -> tpns_status {
+    CK(launch_band_solve<T>(ctx->d_sys, ctx->d_list_band, nband, ctx->n_max_band, ctx->kmax_band, lslab, uslab, dinv,
+                            w, z, 0, ctx->gm_skip, ctx->d_status, st, nullptr, vwork));
+    if (ctx->mf)
+      CK(launch_mf_solve<T>(ctx->mfl, mfF, mfD, w, z, 0, ctx->gm_skip, reinterpret_cast<T*>(ctx->d_mf_y),
+                            reinterpret_cast<T*>(ctx->d_mf_d), reinterpret_cast<T*>(ctx->d_mf_upd), ctx->mf_m_max,
+                            st));
+    return TPNS_OK;
+  };
+  const int64_t vs = ctx->xvec_tot;
+  for (int cyc = 0; cyc < GM_CYCLES; ++cyc) {
+    CK(cudaMemcpyAsync(ctx->gm_skip, skip.data(), ctx->nsys * sizeof(int), cudaMemcpyHostToDevice, st));
+    // r = b - A x; V[0] = M^{-1} r, normalised
+    CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
+                       ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial,
+                       ctx->d_ticket, tol, 2, st, nullptr));
+    TRY(precond(ctx->d_r, ctx->gm_V));
+    CK(launch_gm_begin(ctx->d_sys, ctx->d_list_local, nloc, ctx->gm_V, vs, ctx->gm_H, gstride, GM_KDIM, ctx->gm_skip,
+                       st));
+    for (int j = 0; j < GM_KDIM; ++j) {
+      CK(launch_spmv(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals,
+                     ctx->gm_V + (int64_t)j * vs, ctx->gm_W, ctx->gm_skip, st));
+      TRY(precond(ctx->gm_W, ctx->gm_V + (int64_t)(j + 1) * vs));
+      CK(launch_gm_arnoldi(ctx->d_sys, ctx->d_list_local, nloc, ctx->gm_V, vs, ctx->gm_H, gstride, GM_KDIM, j,
+                           ctx->gm_skip, st));
+    }
+    CK(launch_gm_finish(ctx->d_sys, ctx->d_list_local, nloc, ctx->gm_V, vs, ctx->gm_H, gstride, GM_KDIM, ctx->d_x,
+                        ctx->gm_skip, st));
+    CK(launch_residual(ctx->d_sys, ctx->d_list_local, nloc, ctx->d_rowptr, ctx->d_colidx, ctx->d_vals, ctx->d_b,
+                       ctx->d_x, ctx->d_r, ctx->d_rel, ctx->d_relprev, ctx->d_done, ctx->d_iters, ctx->d_partial,
+                       ctx->d_ticket, tol, 2, st, nullptr));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(rel.data(), ctx->d_rel, ctx->nsys * sizeof(double), cudaMemcpyDeviceToHost));
+    ctx->stats.last_gmres_outer = cyc + 1;
+    if (!pending()) break;
+  }
+  ctx->stats.gmres_steps += 1;
+  // new corrections and glue from the refined local solutions
+  CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_fl, ctx->nn_fl, ctx->d_x, st, nullptr));
+  CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_pl, ctx->nn_pl, ctx->d_x, st, nullptr));
+  CK(launch_glue(ctx->glue, st));
+  return TPNS_OK;
+}
+
 static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
   for (int s = 0; s < nsteps; ++s) {
     if (from_traj) {
@@ -1210,6 +1299,10 @@ static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
       }
     }
     if (!graph) TRY(enqueue_step(ctx, !from_traj));
+    if (ctx->gmres && !ctx->alg1) {
+      TRY(ctx->prec == TPNS_FP64 ? gmres_refine<double>(ctx) : gmres_refine<float>(ctx));
+      TRY(end_step_device(ctx));
+    }
     ctx->step += 1;
   }
   return read_stats(ctx);
@@ -1502,6 +1595,7 @@ static bool read_options(const tpns_options* o, tpns_options& opt) {
   if (opt.nranks == 0) opt.nranks = 1;
   if (opt.algorithm == 0) opt.algorithm = 3;
   if (opt.algorithm != 1 && opt.algorithm != 3) return false;
+  if (opt.refinement < 0 || opt.refinement > 1 || opt.ir_classic_max < 0 || opt.ir_classic_max > 64) return false;
   if (opt.mf_leaf == 0) opt.mf_leaf = 96;
   if (opt.mf_leaf < 8) return false;
   return true;
@@ -1557,6 +1651,8 @@ tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params
   tpns_ctx* ctx = new (std::nothrow) tpns_ctx();
   if (!ctx) { g_err = "host allocation failed"; return TPNS_ENOMEM; }
   ctx->alg1 = opt.algorithm == 1;
+  ctx->gmres = opt.refinement == 1;
+  ctx->ir_classic_max = opt.ir_classic_max;
   cudaGetDevice(&ctx->device);
   ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   if (!ctx->stream) {
@@ -1973,7 +2069,14 @@ tpns_status tpns_batch_step(tpns_ctx** ctxs, int32_t n) {
   }
   tpns_status worst = TPNS_OK;
   for (int i = 0; i < n; ++i) {
-    tpns_status s = read_stats(ctxs[i]);
+    tpns_ctx* ctx = ctxs[i];
+    tpns_status s = TPNS_OK;
+    if (ctx->gmres && !ctx->alg1) {
+      // the refinement check and the end of the step of a context with GMRES-based refinement
+      s = ctx->prec == TPNS_FP64 ? gmres_refine<double>(ctx) : gmres_refine<float>(ctx);
+      if (s == TPNS_OK) s = end_step_device(ctx);
+    }
+    if (s == TPNS_OK) s = read_stats(ctxs[i]);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctxs[i]->ev_s0, ctxs[i]->ev_s1) == cudaSuccess) ctxs[i]->stats.last_step_ms = ms;
     if (s != TPNS_OK && worst == TPNS_OK) {

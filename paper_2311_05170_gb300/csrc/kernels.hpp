@@ -80,6 +80,18 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
 template <typename T>
 size_t mf_factor_smem(bool tc);
 
+// ---- GMRES-based iterative refinement (kernels_krylov.cu); systems with skip[sid] != 0 are
+// left alone.  V: kdim + 1 vectors of stride vstride at the systems' x offsets; gm: per
+// system (list position) gstride doubles: H ((kdim+1) x kdim), g (kdim+1), cs, sn (kdim each)
+cudaError_t launch_spmv(const SysDev* sys, const int* list, int nsys, const int32_t* rowptr, const int32_t* colidx,
+                        const double* vals, const double* v, double* w, const int* skip, cudaStream_t st);
+cudaError_t launch_gm_begin(const SysDev* sys, const int* list, int nsys, double* V, int64_t vstride, double* gm,
+                            int gstride, int kdim, const int* skip, cudaStream_t st);
+cudaError_t launch_gm_arnoldi(const SysDev* sys, const int* list, int nsys, double* V, int64_t vstride, double* gm,
+                              int gstride, int kdim, int j, const int* skip, cudaStream_t st);
+cudaError_t launch_gm_finish(const SysDev* sys, const int* list, int nsys, const double* V, int64_t vstride,
+                             const double* gm, int gstride, int kdim, double* x, const int* skip, cudaStream_t st);
+
 // ---- assembly (kernels_assemble.cu)
 struct AsmArgs {
   const ProbDev* probs;

@@ -37,7 +37,8 @@ class DataDesc(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("local_factor", C.c_int32), ("mf_leaf", C.c_int32), ("mf_cuda_cores", C.c_int32),
-                ("mf_ctas", C.c_int32), ("rank", C.c_int32), ("nranks", C.c_int32), ("algorithm", C.c_int32)]
+                ("mf_ctas", C.c_int32), ("rank", C.c_int32), ("nranks", C.c_int32), ("algorithm", C.c_int32),
+                ("refinement", C.c_int32), ("ir_classic_max", C.c_int32)]
 
 
 FACTORS = {"mf": 0, "band": 1}
@@ -50,7 +51,8 @@ class Stats(C.Structure):
                 ("last_ir_solves", C.c_int64), ("last_solve_bytes", C.c_double), ("last_step_ms", C.c_double),
                 ("lu_cluster_ctas", C.c_int64), ("oseen_unknowns", C.c_int64), ("oseen_nnz", C.c_int64),
                 ("oseen_elements", C.c_int64), ("darcy_unknowns", C.c_int64), ("darcy_elements", C.c_int64),
-                ("factor_entries", C.c_double), ("mf_fronts", C.c_int64), ("create_ms", C.c_double)]
+                ("factor_entries", C.c_double), ("mf_fronts", C.c_int64), ("create_ms", C.c_double),
+                ("last_gmres_outer", C.c_int32), ("gmres_steps", C.c_int32)]
 
 
 class TpnsError(RuntimeError):
@@ -158,12 +160,13 @@ class Solver:
     """One simulation context on the current CUDA device (host_only=True: layout only)."""
 
     def __init__(self, w, precision="fp64", hbm_budget_bytes=0, stream=None, host_only=False, factor="mf",
-                 mf_leaf=0, cuda_cores=False, mf_ctas=0, rank=0, nranks=0, algorithm=3):
+                 mf_leaf=0, cuda_cores=False, mf_ctas=0, rank=0, nranks=0, algorithm=3, gmres=False,
+                 ir_classic_max=0):
         self.lib = load()
         self.w = w
         md, pr, pd, dd = descriptors(w)
         opt = Options(FACTORS[factor], int(mf_leaf), 1 if cuda_cores else 0, int(mf_ctas), int(rank), int(nranks),
-                      int(algorithm))
+                      int(algorithm), 1 if gmres else 0, int(ir_classic_max))
         ctx = C.c_void_p()
         if host_only:
             _check(self.lib, None, self.lib.tpns_layout_create_ex(C.byref(md), C.byref(pd), C.byref(opt),

@@ -314,3 +314,40 @@ def test_algorithm1_on_the_same_kernels(native, prec):
     s.close()
     for k in f:
         assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))
+
+
+@pytest.mark.parametrize("prec,factor", [("fp32", "mf"), ("bf16", "band")])
+def test_gmres_refinement_after_forced_stagnation(native, prec, factor):
+    """One classic refinement pass per step cannot reach the tolerance; the GMRES-based
+    refinement (preconditioned by the same factors, FP64 Krylov vectors) finishes every local
+    system to 1e-13 within three restart cycles, and the fields meet the mixed-precision
+    tolerance against the oracle."""
+    w = W.config_small(nsteps=3)
+    o = TwoGridOracle(w)
+    o.run(3)
+    s = native.Solver(w, precision=prec, gmres=True, ir_classic_max=1, **FACTOR[factor])
+    s.step(3)
+    f = s.fields()
+    st = s.stats()
+    s.close()
+    assert st["gmres_steps"] >= 1 and 1 <= st["last_gmres_outer"] <= 3
+    assert st["last_ir_relres_max"] <= 1e-13
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL[prec], (k, rel(f[k], o.fine[k]))
+
+
+def test_gmres_refinement_idle_when_classic_converges(native):
+    """With enough classic passes no GMRES cycle runs and the fields equal those of a context
+    without the fallback bit for bit."""
+    w = W.config_small(nsteps=2)
+    a = native.Solver(w, precision="fp32", gmres=True)
+    a.step(2)
+    fa, st = a.fields(), a.stats()
+    a.close()
+    b = native.Solver(w, precision="fp32")
+    b.step(2)
+    fb = b.fields()
+    b.close()
+    assert st["gmres_steps"] == 0
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
