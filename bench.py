@@ -425,6 +425,7 @@ def main():
         sstats, done = run_serving(mine, hbm_budget_bytes=64 << 30, precision=args.precision)
         on = dist is not None
         lat = np.array(gather_lists([x for r in done for x in r.latencies_ms], on))
+        obs = np.array(gather_lists([x for r in done for x in r.observed_ms], on))
         wall = max_over_ranks(sstats["wall_s"], on, device="cuda")
         serving = {
             "requests": int(sum_over_ranks(sstats["requests"], on, device="cuda")),
@@ -434,12 +435,17 @@ def main():
             "refused_for_budget": int(sum_over_ranks(sstats["refused_for_budget"], on, device="cuda")),
             "step_latency_ms_p50": float(np.percentile(lat, 50)) if lat.size else None,
             "step_latency_ms_p99": float(np.percentile(lat, 99)) if lat.size else None,
+            "observed_step_latency_ms_p50": float(np.percentile(obs, 50)) if obs.size else None,
+            "observed_step_latency_ms_p99": float(np.percentile(obs, 99)) if obs.size else None,
             "tick_ms_max_p50": max_over_ranks(sstats["tick_ms_p50"] or 0.0, on, device="cuda"),
             "dof_steps_per_s": sum_over_ranks(sum(r.dofs * r.done_steps for r in done), on, device="cuda") / wall,
             "sample": (f"first {args.serving_requests} of the 512 seeded requests (Poisson arrivals, 20/s), "
                        f"{args.serving_steps} steps each, sharded over {world} GPU(s) by estimated work, "
                        f"HBM budget 64 GiB per GPU; step latency = device time of a request's step within "
-                       f"its batched tick (other requests running beside it); wall includes context creation"),
+                       f"its batched tick (other requests running beside it); observed step latency = wall time "
+                       f"from the step's readiness (end of the request's previous step, or its admission) to "
+                       f"the end of its tick; contexts created by a background thread beside the ticks; wall "
+                       f"includes context creation"),
         }
     # ---------------------------------------------------------------- CPU baseline (oracle)
     cpu = None

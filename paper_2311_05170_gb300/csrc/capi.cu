@@ -1113,10 +1113,11 @@ static bool capture_step(tpns_ctx* ctx, bool coarse, cudaGraphExec_t* out) {
     cudaGetLastError();
     return false;
   }
-  const int64_t l0 = launch_counter();
+  const int64_t l0 = thread_launch_counter();
   tpns_status s = enqueue_step(ctx, coarse);
-  // kernels recorded in the graph run at every replay, not now
-  const int64_t recorded = launch_counter() - l0;
+  // kernels recorded in the graph run at every replay, not now (counted on this thread only:
+  // other threads may launch meanwhile)
+  const int64_t recorded = thread_launch_counter() - l0;
   count_launches((int)-recorded);
   (coarse ? ctx->kernels_full : ctx->kernels_local) = recorded;
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);

@@ -10,6 +10,7 @@ namespace tpns {
 
 // number of kernel launches issued by this library since it was loaded
 int64_t launch_counter();
+int64_t thread_launch_counter();   // launches issued by the calling host thread
 void count_launches(int n);
 
 constexpr int LU_NB = 32;        // panel width of the band LU and block size of the solves

@@ -14,8 +14,13 @@
 namespace tpns {
 
 static std::atomic<int64_t> g_launches{0};
+static thread_local int64_t t_launches = 0;   // this host thread's share (graph captures)
 int64_t launch_counter() { return g_launches.load(); }
-void count_launches(int n) { g_launches.fetch_add(n); }
+int64_t thread_launch_counter() { return t_launches; }
+void count_launches(int n) {
+  g_launches.fetch_add(n);
+  t_launches += n;
+}
 
 namespace {
 

@@ -76,3 +76,23 @@ def test_batch_step_matches_individual_steps(native):
         for k in ref:
             assert np.array_equal(f[k], ref[k]), k
         s.close()
+
+
+def test_served_results_match_the_oracle(native):
+    """A seeded sample of served requests (different mesh sizes and parameters, run in the mix)
+    meets the mixed-precision tolerance against the CPU oracle run alone."""
+    from oracle.scheme import TwoGridOracle
+    from paper_2311_05170_gb300.serve import run_serving
+    reqs = W.serving_requests_small(n=4, nsteps=3)
+    stats, done = run_serving(reqs, hbm_budget_bytes=8 << 30, keep_fields=True)
+    assert stats["requests"] == 4
+    for r in done[:2]:
+        o = TwoGridOracle(r.w)
+        o.run(r.nsteps)
+        for k in o.fine:
+            rel = np.linalg.norm(r.fields[k] - o.fine[k]) / np.linalg.norm(o.fine[k])
+            assert rel <= 1e-8, (r.rid, k, rel)
+    # the observed latency (from the step's readiness to the end of its tick) is at least the
+    # device time of the step
+    assert stats["observed_step_latency_ms_p50"] >= stats["step_latency_ms_p50"] * 0.5
+    assert all(len(r.observed_ms) == r.nsteps for r in done)

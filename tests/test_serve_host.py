@@ -16,7 +16,7 @@ class FakeSolver:
     live = []
     created = []
 
-    def __init__(self, w, precision="fp32", hbm_budget_bytes=0):
+    def __init__(self, w, precision="fp32", hbm_budget_bytes=0, stream=None):
         if w.nbytes > hbm_budget_bytes:
             raise TpnsError(TPNS_EBUDGET, "over budget")
         self.w, self.steps, self.closed = w, 0, False
@@ -57,7 +57,7 @@ def test_every_request_runs_its_steps_within_the_budget(fake):
     fake_batch_step.budget = budget
     reqs = [(0.0, FakeWorkload("a", 60, 10), 3), (0.0, FakeWorkload("b", 50, 20), 2),
             (0.0, FakeWorkload("c", 30, 5), 4)]
-    stats, done = serve.run_serving(reqs, budget, keep_fields=True, time_scale=0.0)
+    stats, done = serve.run_serving(reqs, budget, keep_fields=True, time_scale=0.0, background=False)
     assert stats["requests"] == 3 and not fake.live
     by = {r.w.name: r for r in done}
     for name, n in (("a", 3), ("b", 2), ("c", 4)):
@@ -74,7 +74,7 @@ def test_every_request_runs_its_steps_within_the_budget(fake):
 def test_max_live_caps_the_batch(fake):
     fake_batch_step.budget = 10 ** 9
     reqs = [(0.0, FakeWorkload(str(i), 1, 1), 2) for i in range(7)]
-    stats, done = serve.run_serving(reqs, 10 ** 9, max_live=3, time_scale=0.0)
+    stats, done = serve.run_serving(reqs, 10 ** 9, max_live=3, time_scale=0.0, background=False)
     assert stats["requests"] == 7 and fake_batch_step.max_live == 3
     assert all(r.done_steps == 2 for r in done)
     assert stats["dof_steps_per_s"] > 0
@@ -87,4 +87,6 @@ def test_other_errors_are_not_swallowed(fake, monkeypatch):
 
     monkeypatch.setattr(serve, "Solver", Broken)
     with pytest.raises(TpnsError):
-        serve.run_serving([(0.0, FakeWorkload("x", 1, 1), 1)], 10, time_scale=0.0)
+        serve.run_serving([(0.0, FakeWorkload("x", 1, 1), 1)], 10, time_scale=0.0, background=False)
+    with pytest.raises(TpnsError):
+        serve.run_serving([(0.0, FakeWorkload("x", 1, 1), 1)], 10, time_scale=0.0, background=True)
