@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=16)
     ap.add_argument("--serving-steps", type=int, default=10)
+    ap.add_argument("--profile", action="store_true",
+                    help="only create the mixed-precision context and run W + K hot-path steps (for ncu); "
+                         "prints no bench line")
     return ap.parse_args()
 
 
@@ -267,6 +270,16 @@ def main():
     w = W.config_graded(nsteps=Wm + K)
     stream = torch.cuda.Stream()
     handle = stream.cuda_stream
+    if args.profile:
+        s = Solver(w, precision=args.precision, stream=handle)
+        s.coarse_precompute(Wm + K)
+        s.local_step(Wm)
+        torch.cuda.synchronize()
+        s.local_step(K)
+        torch.cuda.synchronize()
+        s.close()
+        print("profile run: %d + %d hot-path steps of %s" % (Wm, K, WORKLOAD))
+        return
 
     def timed_hot(prec, with_phases=False, **opts):
         """K hot-path steps replayed from the captured CUDA graph (the timed region); then,

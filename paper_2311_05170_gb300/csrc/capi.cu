@@ -71,6 +71,8 @@ struct tpns_ctx {
   // multifrontal factorisation of the local Oseen systems
   bool mf = false;
   int mf_leaf = 96, mf_tc = 1, mf_m_max = 1, mf_oseen_fronts = 0;
+  int mf_oseen_blocks = 0, mf_blocks = 0;   // pivot blocks of the Oseen fronts / of all fronts
+  int64_t* d_mf_dblk = nullptr;
   int rank = 0, nranks = 1;   // split of one simulation over contexts (see tpns_options)
   bool alg1 = false;          // Algorithm 1: the coarse mesh is the fine mesh, no local phase
   bool gmres = false;         // GMRES-based refinement when classic refinement stagnates
@@ -366,9 +368,10 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   ctx->kl_max_cf = ctx->hsys[ctx->list_cf[0]].kl;
   ctx->n_max_cf = ctx->hsys[ctx->list_cf[0]].n;
   for (int s : ctx->list_cp) ctx->n_max_cp = std::max(ctx->n_max_cp, ctx->hsys[s].n);
-  // multifrontal layout of the local systems: the fronts of all systems in level order
-  // (leaves first) within each group, so that a front's children always precede it
+  // multifrontal layout of the local systems: the fronts of all systems in one task order
+  // per group, in which a front's children always precede it
   std::vector<MFFrontDev> h_fronts;
+  std::vector<int64_t> h_dblk;   // pivot-block slots: the Oseen fronts' first, then the Darcy fronts'
   std::vector<int32_t> h_mrows, h_relmap, h_origk, h_origi;
   std::vector<int64_t> h_colptr;
   if (ctx->mf) {
@@ -381,14 +384,26 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     for (int q = 0; q < ctx->nf; ++q) msys.push_back({q, ctx->sys_first[q]});
     for (int q = ctx->nf + 1; q < ctx->nf + 1 + ctx->np; ++q)
       for (int f = 0; f < 3; ++f) msys.push_back({q, ctx->sys_first[q] + f});
-    struct Key { int group, level, q, t; };
+    // Task order: a front's priority is the estimated time from its start to the end of its
+    // tree's root (its own cost plus its parent's priority), so children always rank before
+    // their parents (the order stays topological) and the fronts on the longest remaining
+    // chains are taken first.  Estimated cost of a front in microseconds: fixed work plus
+    // per-pivot-block work plus the assembly and update traffic.
+    struct Key { int group; double prio; int q, t; };
     std::vector<Key> keys;
     std::vector<std::vector<int>> newid(msys.size());
     for (int q = 0; q < (int)msys.size(); ++q) {
       const MFSymbolic& M = ctx->probs[msys[q].prob]->mf;
       const bool oseen = msys[q].prob < ctx->nf;
       newid[q].assign(M.fronts.size(), -1);
-      for (int t = 0; t < (int)M.fronts.size(); ++t) keys.push_back({oseen ? 0 : 1, M.fronts[t].level, q, t});
+      const int nf = (int)M.fronts.size();
+      std::vector<double> prio(nf, 0.0);
+      for (int t = nf - 1; t >= 0; --t) {   // postorder: parents after children
+        const MFFront& F = M.fronts[t];
+        const double cost = 10.0 + 15.0 * ((F.p + MF_NB - 1) / MF_NB) + 1e-3 * (double)F.m * F.m;
+        prio[t] = cost + (F.parent >= 0 ? prio[F.parent] : 0.0);
+      }
+      for (int t = 0; t < nf; ++t) keys.push_back({oseen ? 0 : 1, prio[t], q, t});
       const SysDev& Sd = ctx->hsys[msys[q].sid];
       MFSysDev D{};
       D.sid = msys[q].sid; D.n = ctx->probs[msys[q].prob]->n; D.x_off = Sd.x_off; D.val_off = Sd.val_off;
@@ -399,7 +414,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       }
     }
     std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
-      return a.group != b.group ? a.group < b.group : a.level < b.level;
+      return a.group != b.group ? a.group < b.group : a.prio > b.prio;
     });
     ctx->mf_oseen_fronts = 0;
     for (size_t i = 0; i < keys.size(); ++i) {
@@ -434,6 +449,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
         for (int q = F.col_ptr[j]; q < F.col_ptr[j + 1]; ++q) h_origi.push_back(F.orig_i[q] | (j << 16));
       ctx->mf_m_max = std::max(ctx->mf_m_max, F.m);
       if (k.group == 0) ctx->mf_dinv_entries += (double)nb * 2 * MF_NB * MF_NB;
+      for (int b = 0; b < nb; ++b) h_dblk.push_back(FD.dinv_off + (int64_t)b * 2 * MF_NB * MF_NB);
+      if (k.group == 0) ctx->mf_oseen_blocks = (int)h_dblk.size();
       h_fronts.push_back(FD);
     }
   }
@@ -612,6 +629,9 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     TRY(upload(ctx, &d_cp, h_colptr));
     TRY(upload(ctx, &d_ok, h_origk));
     TRY(upload(ctx, &d_oi, h_origi));
+    ctx->mf_blocks = (int)h_dblk.size();
+    if (h_dblk.empty()) h_dblk.push_back(0);
+    TRY(upload(ctx, &ctx->d_mf_dblk, h_dblk));
     // scheduling words: task counters and finished-CTA counts at 0, epochs from 1 (the flags
     // start at 0, so no flag of a launch is set before the launch sets it)
     const int nfr = (int)h_fronts.size();
@@ -1012,6 +1032,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
   if (ctx->mf) {
     ph_begin(ctx, PH_BAND_LU);
     CK(launch_mf_factor<T>(ctx->mfl, 0, ctx->mf_oseen_fronts, mfF, mfD, ctx->mf_tc, st));
+    CK(launch_mf_dinv<T>(mfD, ctx->d_mf_dblk, ctx->mf_oseen_blocks, st));
     ph_end(ctx, PH_BAND_LU);
   } else {
     ph_begin(ctx, PH_BAND_FILL);
@@ -1401,12 +1422,18 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
   if (ctx->mf) {
     // the local Darcy systems: multifrontal LU once (their matrices do not change)
     const int nd = ctx->mfl.nfront - ctx->mf_oseen_fronts;
-    if (ctx->prec == TPNS_FP64)
+    const int nb = ctx->mf_blocks - ctx->mf_oseen_blocks;
+    if (ctx->prec == TPNS_FP64) {
       CK(launch_mf_factor<double>(ctx->mfl, ctx->mf_oseen_fronts, nd, reinterpret_cast<double*>(ctx->d_mf_F),
                                   reinterpret_cast<double*>(ctx->d_mf_dinv), 0, st));
-    else
+      CK(launch_mf_dinv<double>(reinterpret_cast<double*>(ctx->d_mf_dinv), ctx->d_mf_dblk + ctx->mf_oseen_blocks, nb,
+                                st));
+    } else {
       CK(launch_mf_factor<float>(ctx->mfl, ctx->mf_oseen_fronts, nd, reinterpret_cast<float*>(ctx->d_mf_F),
                                  reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->mf_tc, st));
+      CK(launch_mf_dinv<float>(reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->d_mf_dblk + ctx->mf_oseen_blocks, nb,
+                               st));
+    }
   } else if (ctx->prec == TPNS_FP64) {
     double* band = reinterpret_cast<double*>(ctx->d_band_local);
     double* dinv = reinterpret_cast<double*>(ctx->d_dinv_local);

@@ -80,6 +80,10 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
                             const int* done, T* yv, T* dv, T* upd, int m_max, cudaStream_t st);
 template <typename T>
 size_t mf_factor_smem(bool tc);
+// Inverses of the factored pivot blocks (the solves' diagonal blocks): `blocks` lists the
+// offsets of the blocks' 2 x 32 x 32 slots in dinv.
+template <typename T>
+cudaError_t launch_mf_dinv(T* dinv, const int64_t* blocks, int nblk, cudaStream_t st);
 
 // ---- GMRES-based iterative refinement (kernels_krylov.cu); systems with skip[sid] != 0 are
 // left alone.  V: kdim + 1 vectors of stride vstride at the systems' x offsets; gm: per

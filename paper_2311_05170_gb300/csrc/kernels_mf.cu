@@ -1,8 +1,9 @@
 // Multifrontal LU and triangular solves of the local Oseen systems (Algorithm 3 Step 3(2),
 // eq. uclocalFully), scheduled as a dataflow over the elimination trees of all systems.
 //
-// One persistent launch factors every front of every system.  The fronts are numbered in
-// level order (all leaves first); each CTA takes the next front from an atomic counter,
+// One persistent launch factors every front of every system.  The fronts are numbered in a
+// topological order (children first) that puts the fronts with the longest estimated
+// remaining chain to their root first; each CTA takes the next front from an atomic counter,
 // waits until the front's children are finished (a flag per front, tagged with the
 // launch's epoch, bounded wait) and factors the whole front itself.  A CTA only waits for
 // fronts that CTAs which started before it have taken, so no launch geometry or
@@ -23,7 +24,7 @@
 // The Schur complement left in a front's trailing block is consumed by its parent.
 //
 // Solves (one pass of iterative refinement), one launch with the same scheduling: the
-// forward tasks in level order (a front waits for its children: right-hand side plus the
+// forward tasks in that order (a front waits for its children: right-hand side plus the
 // children's update vectors, the pivot blocks through the inverses of L11's diagonal
 // blocks, then the L columns below), then the backward tasks in reverse order (a front
 // waits for its own forward task and its parent: U12 against the ancestors' correction,
@@ -161,73 +162,52 @@ __device__ __forceinline__ bool bad_val(double v) { return !(fabs(v) > 0.0) || !
 // ---------------------------------------------------------------- pivot block
 template <typename T>
 struct alignas(16) PanelSmem {
-  T D[MF_NB][DS];      // pivot block, then its LU (unit L below, U on and above the diagonal)
-  T Li[MF_NB][DS];     // inverse of the unit-lower triangle
-  T Ui[MF_NB][DS];     // inverse of the upper triangle
+  T D[MF_NB][DS];      // the pivot block's LU (unit L below, U on and above the diagonal)
   T R[MF_NB];          // reciprocals of the pivots
+  T P[MF_NB];          // the pivot row being broadcast
 };
 
 // Factor the pivot block of rows / columns k0 .. k0 + kb - 1 (padded to 32 with the
-// identity) and form both triangular inverses.  All threads call; a zero or non-finite
-// pivot sets bit 0 of *s_flag.  Warp 0 holds one column per lane, eliminates with
-// shuffles and keeps the pivots' reciprocals, so the inverses need no division.
+// identity) in place: S.D holds unit L below and U on and above the diagonal, S.R the
+// pivots' reciprocals.  All threads call; a zero or non-finite pivot sets bit 0 of *s_flag.
+// Warp 0 holds one row per lane; at step k lane k publishes its (final) row in shared memory
+// and the lanes below eliminate against it.  The inverses of the block's triangles, which
+// only the solves need, are formed afterwards for all blocks at once (mf_dinv_kernel).
 template <typename T>
 __device__ __noinline__ void pivot_block(PanelSmem<T>& S, const T* __restrict__ F, int ld, int k0, int kb,
                                          int* s_flag) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (warp == 0) {
-    T a[MF_NB];   // lane j holds column j
-    const T* col = F + (int64_t)(k0 + (lane < kb ? lane : 0)) * ld + k0;
+    T a[MF_NB];   // lane i holds row i
+    const T* row = F + (int64_t)k0 * ld + k0 + (lane < kb ? lane : 0);
 #pragma unroll
-    for (int i = 0; i < MF_NB; ++i) a[i] = col[i < kb ? i : 0];
+    for (int c = 0; c < MF_NB; ++c) a[c] = row[(int64_t)(c < kb ? c : 0) * ld];
 #pragma unroll
-    for (int i = 0; i < MF_NB; ++i)
-      if (i >= kb || lane >= kb) a[i] = (i == lane) ? T(1) : T(0);
+    for (int c = 0; c < MF_NB; ++c)
+      if (c >= kb || lane >= kb) a[c] = (c == lane) ? T(1) : T(0);
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < MF_NB; ++k) {
-      const T piv = __shfl_sync(0xffffffffu, a[k], k);
+      if (lane == k) {
+#pragma unroll
+        for (int c = 0; c < MF_NB; ++c) S.P[c] = a[c];
+      }
+      __syncwarp();
+      const T piv = S.P[k];
       if (k < kb) bad |= bad_val(piv);
       const T rp = recip(piv);
       if (lane == 0) S.R[k] = rp;
-      // lane k turns its column into the multipliers l_i; lanes right of it apply them
+      if (lane > k) {
+        const T l = a[k] * rp;
+        a[k] = l;
 #pragma unroll
-      for (int i = k + 1; i < MF_NB; ++i) {
-        const T li = __shfl_sync(0xffffffffu, a[i], k) * rp;
-        const T upd = a[i] - li * a[k];
-        a[i] = lane == k ? li : (lane > k ? upd : a[i]);
+        for (int c = k + 1; c < MF_NB; ++c) a[c] -= l * S.P[c];
       }
+      __syncwarp();
     }
 #pragma unroll
-    for (int i = 0; i < MF_NB; ++i) S.D[i][lane] = a[i];
+    for (int c = 0; c < MF_NB; ++c) S.D[lane][c] = a[c];
     if (lane == 0 && bad) atomicOr(s_flag, 1);
-  }
-  __syncthreads();
-  if (warp == 0) {
-    // column `lane` of U^{-1}, right-looking: x_i = s_i / u_ii, then s_k -= u_ki x_i (k < i)
-    T s[MF_NB];
-#pragma unroll
-    for (int i = 0; i < MF_NB; ++i) s[i] = (i == lane) ? T(1) : T(0);
-#pragma unroll
-    for (int i = MF_NB - 1; i >= 0; --i) {
-      s[i] = s[i] * S.R[i];
-#pragma unroll
-      for (int k = 0; k < i; ++k) s[k] -= S.D[k][i] * s[i];
-    }
-#pragma unroll
-    for (int i = 0; i < MF_NB; ++i) S.Ui[i][lane] = s[i];
-  } else if (warp == 1) {
-    // column `lane` of L^{-1} (unit diagonal), right-looking
-    T s[MF_NB];
-#pragma unroll
-    for (int i = 0; i < MF_NB; ++i) s[i] = (i == lane) ? T(1) : T(0);
-#pragma unroll
-    for (int i = 0; i < MF_NB; ++i) {
-#pragma unroll
-      for (int k = i + 1; k < MF_NB; ++k) s[k] -= S.D[k][i] * s[i];
-    }
-#pragma unroll
-    for (int i = 0; i < MF_NB; ++i) S.Li[i][lane] = s[i];
   }
   __syncthreads();
 }
@@ -247,7 +227,8 @@ __device__ __forceinline__ void put_split(float* hi, float* lo, int l, const flo
 __device__ __forceinline__ void put_split(float*, float*, int, const double (&)[MF_NB]) {}
 
 // L rows r in [k1, m): F[r, k0:k0+kb] <- F[r, k0:k0+kb] U11^{-1}; U columns c in [k1, m):
-// F[k0:k0+kb, c] <- L11^{-1} F[k0:k0+kb, c].  One thread per row or column.  With `pk`
+// F[k0:k0+kb, c] <- L11^{-1} F[k0:k0+kb, c], by substitution with the factored pivot block.
+// One thread per row or column.  With `pk`
 // (FP32 tensor-core path) the first 128 rows and 256 columns also go straight into the
 // packed operand tiles of the first update chunk.
 template <typename T>
@@ -267,18 +248,15 @@ __device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, 
 #pragma unroll
     for (int c = 0; c < MF_NB; ++c)
       if (c >= kb) a[c] = T(0);
+    // row: solve l U11 = a (l_c = a_c / u_cc, then a_c' -= l_c u_cc' for c' > c);
+    // column: solve L11 u = a (unit diagonal: u_c = a_c, then a_c' -= l_c'c u_c)
     T o[MF_NB];
 #pragma unroll
-    for (int c2 = 0; c2 < MF_NB; ++c2) {
-      T s = T(0);
-      if (row) {
+    for (int c = 0; c < MF_NB; ++c) {
+      const T v = row ? a[c] * S.R[c] : a[c];
+      o[c] = v;
 #pragma unroll
-        for (int c = 0; c <= c2; ++c) s += a[c] * S.Ui[c][c2];
-      } else {
-#pragma unroll
-        for (int c = 0; c <= c2; ++c) s += S.Li[c2][c] * a[c];
-      }
-      o[c2] = s;
+      for (int c2 = c + 1; c2 < MF_NB; ++c2) a[c2] -= v * (row ? S.D[c][c2] : S.D[c2][c]);
     }
     if (row) {
 #pragma unroll
@@ -593,11 +571,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
     for (int k0 = 0, kk = 0; k0 < Fd.p; k0 += MF_NB, ++kk) {
       const int kb = min(MF_NB, Fd.p - k0), k1 = k0 + kb;
       pivot_block<T>(P, F, ld, k0, kb, &s_flag);
-      T* dv = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB;
-      for (int q = tid; q < MF_NB * MF_NB; q += blockDim.x) {
-        dv[q] = P.Li[q >> 5][q & 31];
-        dv[MF_NB * MF_NB + q] = P.Ui[q >> 5][q & 31];
-      }
+      // the factored pivot block (row-major) for mf_dinv_kernel
+      T* dv = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB + MF_NB * MF_NB;
+      for (int q = tid; q < MF_NB * MF_NB; q += blockDim.x) dv[q] = P.D[q >> 5][q & 31];
       if (k1 >= Fd.m) {
         __syncthreads();
         continue;
@@ -637,6 +613,48 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
     if ((tid >> 5) == 0) tm_dealloc(TS.tmem, MF_TMEM_COLS);
   }
   finish_launch(A.sched);
+}
+
+// ---------------------------------------------------------------- block inverses
+// For every pivot block in the list (offset of its 2 x 32 x 32 slot): read the factored block
+// (row-major, second half of the slot), write L11^{-1} (unit lower) to the first half and
+// U11^{-1} to the second.  One warp per block, lane j forms column j of each inverse.
+template <typename T>
+__global__ void __launch_bounds__(256) mf_dinv_kernel(T* __restrict__ dinv, const int64_t* __restrict__ blocks, int nblk) {
+  __shared__ T B[8][MF_NB][DS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = blockIdx.x * 8 + w;
+  if (b >= nblk) return;
+  T* slot = dinv + blocks[b];
+  T(&D)[MF_NB][DS] = B[w];
+#pragma unroll
+  for (int i = 0; i < MF_NB; ++i) D[i][lane] = slot[MF_NB * MF_NB + i * MF_NB + lane];
+  __syncwarp();
+  T u[MF_NB], l[MF_NB];
+#pragma unroll
+  for (int i = 0; i < MF_NB; ++i) {
+    u[i] = (i == lane) ? T(1) : T(0);
+    l[i] = u[i];
+  }
+  // U^{-1} e_lane, right-looking back substitution
+#pragma unroll
+  for (int i = MF_NB - 1; i >= 0; --i) {
+    u[i] = u[i] / D[i][i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) u[k] -= D[k][i] * u[i];
+  }
+  // L^{-1} e_lane (unit diagonal), right-looking forward substitution
+#pragma unroll
+  for (int i = 0; i < MF_NB; ++i) {
+#pragma unroll
+    for (int k = i + 1; k < MF_NB; ++k) l[k] -= D[k][i] * l[i];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < MF_NB; ++i) {
+    slot[i * MF_NB + lane] = l[i];
+    slot[MF_NB * MF_NB + i * MF_NB + lane] = u[i];
+  }
 }
 
 // ---------------------------------------------------------------- solves
@@ -848,6 +866,14 @@ cudaError_t launch_mf_factor(const MFLaunch& L, int task0, int ntask, T* F, T* d
 }
 
 template <typename T>
+cudaError_t launch_mf_dinv(T* dinv, const int64_t* blocks, int nblk, cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  count_launches(1);
+  mf_dinv_kernel<T><<<(nblk + 7) / 8, 256, 0, st>>>(dinv, blocks, nblk);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const double* r, double* x, int accumulate,
                             const int* done, T* yv, T* dv, T* upd, int m_max, cudaStream_t st) {
   if (L.nfront == 0) return cudaSuccess;
@@ -865,6 +891,7 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
 #define TPNS_MF_INST(T)                                                                                      \
   template size_t mf_factor_smem<T>(bool);                                                                  \
   template cudaError_t launch_mf_factor<T>(const MFLaunch&, int, int, T*, T*, int, cudaStream_t);          \
+  template cudaError_t launch_mf_dinv<T>(T*, const int64_t*, int, cudaStream_t);                            \
   template cudaError_t launch_mf_solve<T>(const MFLaunch&, const T*, const T*, const double*, double*, int, \
                                           const int*, T*, T*, T*, int, cudaStream_t);
 TPNS_MF_INST(float)

@@ -50,8 +50,8 @@ std::string mf_analyse(int n, int dim, const int32_t* coord, const int8_t* press
                        const int32_t* colidx, int leaf_max, MFSymbolic& out);
 
 // Device descriptor of one front (offsets in elements of the front's precision T unless
-// said otherwise).  The fronts of all systems are numbered in level order (leaves first), so
-// every child precedes its parent.
+// said otherwise).  The fronts of all systems are numbered in a topological order (every
+// child precedes its parent), longest estimated remaining chain to the root first.
 struct MFFrontDev {
   int64_t f_off;      // dense front, column-major, leading dimension ld
   int64_t dinv_off;   // per pivot block: L11^{-1} (32x32, row-major) then U11^{-1}

@@ -30,7 +30,7 @@ def _alone(native, w, nsteps):
 def test_results_equal_alone_and_in_the_mix(native):
     from paper_2311_05170_gb300.serve import run_serving
     reqs = W.serving_requests_small(n=6, nsteps=4)
-    stats, done = run_serving(reqs, hbm_budget_bytes=8 << 30, keep_fields=True)
+    stats, done = run_serving(reqs, hbm_budget_bytes=8 << 30, keep_fields=True, background=False)
     assert stats["requests"] == 6 and stats["max_concurrency"] >= 2
     assert stats["step_latency_ms_p50"] is not None and stats["step_latency_ms_p99"] >= stats["step_latency_ms_p50"]
     # a request's own step time is positive and within the tick that carried it
@@ -96,3 +96,17 @@ def test_served_results_match_the_oracle(native):
     # device time of the step
     assert stats["observed_step_latency_ms_p50"] >= stats["step_latency_ms_p50"] * 0.5
     assert all(len(r.observed_ms) == r.nsteps for r in done)
+
+
+def test_background_admission_results_equal_alone(native):
+    """Contexts created by the background thread while others step (all requests arrive at
+    once) give the same results as the same simulations run alone."""
+    from paper_2311_05170_gb300.serve import run_serving
+    reqs = W.serving_requests_small(n=4, nsteps=3)
+    stats, done = run_serving(reqs, hbm_budget_bytes=8 << 30, keep_fields=True, time_scale=0.0)
+    assert stats["requests"] == 4
+    for r in done:
+        ref = _alone(native, r.w, r.nsteps)
+        for k in ref:
+            rel = np.linalg.norm(r.fields[k] - ref[k]) / np.linalg.norm(ref[k])
+            assert rel <= 1e-12, (r.rid, k, rel)
