@@ -386,8 +386,9 @@ def main():
                       "note": "algorithmic flops of the nested-dissection partial factorisations; the "
                               "trailing updates issue 3 TF32 products per multiply-add (split operands)"},
         "solves": {**hbm(solve_bytes_step, ph["solve"]), "launches_per_step": phn["solve"] / K},
-        "oseen_assembly": hbm(asm_bytes, ph["asm_oseen"] + ph["scatter"]),
-        "darcy_rhs": hbm(darcy_bytes, ph["asm_darcy"]),
+        "oseen_assembly": {**hbm(asm_bytes, ph["asm_oseen"] + ph["scatter"]),
+                           "limiter": "FP64 pipe (ncu: 83 % active in the element kernel; DRAM 0.6 %)"},
+        "darcy_rhs": {**hbm(darcy_bytes, ph["asm_darcy"]), "limiter": "FP64 pipe (element right-hand sides in FP64)"},
         "state_glue": hbm(glue_bytes, ph["state_glue"]),
     }
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
