@@ -14,6 +14,9 @@ Modules
   mms     manufactured solutions and the data they induce (forcing, boundary, interface)
   scheme  Algorithm 3 (coarse step, local corrections, glue) and a global fine
           linearised solve used as a brute-force check
+  mesh3d, fe3d, mms3d, scheme3d
+          the same in 3D: Kuhn tetrahedral meshes, P2/P1 tetrahedra with a collapsed
+          Gauss-Jacobi rule, Gamma faces at z = 1, the 3D manufactured solutions, Algorithm 3
 
 Parity status: every routine is pinned by a CPU test (closed forms, invariants, exact
 polynomial reproduction, brute force, convergence rates) except the paper's printed

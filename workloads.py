@@ -168,3 +168,42 @@ def serving_requests_small(n=6, seed=7, rate=200.0, nsteps=4):
                      (ns, ns), 2, 0.01, nsteps, 1, p)
         out.append((float(t[r]), w, nsteps))
     return out
+
+
+# ---------------------------------------------------------------------------------- 3D
+@dataclass
+class Workload3D:
+    """One 3D run: fluid region [0,1]^2 x [1,2] over porous region [0,1]^3, Gamma at z=1,
+    uniform Kuhn tetrahedral meshes with H = 1/n_coarse and h = H / fine_per_coarse."""
+    name: str
+    n_coarse: int                  # coarse cells per axis and region
+    fine_per_coarse: int           # fine cells per coarse cell and axis
+    nsub: Tuple[int, int, int]     # subdomains per region (x, y, z)
+    overlap: int                   # overlap in fine layers beyond D_j
+    dt: float
+    nsteps: int
+    mms: int                       # 2: 3D trigonometric field, 4: steady polynomial patch field, 0: zero
+    params: Params = field(default_factory=Params)
+    dim: int = 3
+
+    def to_dict(self):
+        return asdict(self)
+
+
+def config_3d(nsteps=50) -> Workload3D:
+    """3D plain vs mixed precision: H=1/4, h=1/24, 2x2x2 subdomains per region, overlap 2h,
+    3D trigonometric manufactured solution, all parameters 1, dt=0.01, 50 steps."""
+    return Workload3D("3d_H4_h24_2x2x2sub_overlap2h_dt0.01", 4, 6, (2, 2, 2), 2, 0.01, nsteps, 2, Params())
+
+
+def config_3d_small(n_coarse=2, r=2, nsub=(2, 2, 1), overlap=1, nsteps=2, dt=0.01, mms=2, params=None) -> Workload3D:
+    """Small 3D runs for tests (H = 1/n_coarse, h = H/r)."""
+    return Workload3D(f"3d_H{n_coarse}_h{n_coarse * r}_{nsub[0]}x{nsub[1]}x{nsub[2]}sub", n_coarse, r, nsub, overlap,
+                      dt, nsteps, mms, params or Params())
+
+
+def config_3d_patch(n_coarse=2, r=2, nsub=(2, 1, 1), nsteps=2, dt=0.1) -> Workload3D:
+    """Steady polynomial patch field in 3D (P2 velocity, P1 pressure, P2 Darcy pressures)."""
+    p = Params(nu=0.7, eta=1.0, rho=1.3, mu=1.1, alpha=0.9, sigma=0.8, sigma_star=1.2,
+               phiC=(0.5, 0.7, 0.9), k=(1.5, 0.6, 0.25))
+    return Workload3D(f"3d_patch_H{n_coarse}_r{r}", n_coarse, r, nsub, 1, dt, nsteps, 4, p)
