@@ -70,12 +70,17 @@ typedef enum {
  * width 1/nx_coarse, ny_coarse rows of height 1/ny_coarse per region.  Fine mesh (nested
  * grid lines): every coarse column is split into fine_per_coarse_x equal columns; coarse
  * row c, counted from Gamma outwards in both regions, is split into
- * fine_rows_from_gamma[c] equal rows. */
+ * fine_rows_from_gamma[c] equal rows.
+ * dim = 3 (Sec. 6 Example 2 geometry: porous box [0,1]^3 below the fluid box
+ * [0,1]^2 x [1,2], Gamma at z = 1): uniform Kuhn tetrahedral meshes, coarse cells of edge
+ * H = 1/nx_coarse (ny_coarse must equal nx_coarse), fine cells of edge H / fine_per_coarse_x;
+ * fine_rows_from_gamma is not read.  dim = 0 or 2: the 2D meshes above. */
 typedef struct {
   int32_t nx_coarse;
   int32_t ny_coarse;
   int32_t fine_per_coarse_x;
   int32_t fine_rows_from_gamma[TPNS_MAX_COARSE_ROWS];
+  int32_t dim;
 } tpns_mesh_desc;
 
 /* Physical parameters of Sec. 2 (order of Darcy arrays: F, f, m). */
@@ -85,11 +90,12 @@ typedef struct {
   double k[3];         /* permeabilities */
 } tpns_params;
 
-/* Algorithm 3 Step 2: nsub_x x nsub_y boxes D_j per region aligned with coarse lines,
- * enlarged by `overlap` fine layers on sides inside the region. */
+/* Algorithm 3 Step 2: nsub_x x nsub_y (x nsub_z in 3D) boxes D_j per region aligned with
+ * coarse lines, enlarged by `overlap` fine layers on sides inside the region. */
 typedef struct {
   int32_t nsub_x, nsub_y;
   int32_t overlap;
+  int32_t nsub_z;      /* 3D only */
 } tpns_partition_desc;
 
 /* Data of the run: manufactured solution id (1 = 2D trigonometric field, 3 = steady

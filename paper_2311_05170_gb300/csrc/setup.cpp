@@ -181,23 +181,41 @@ static void make_problem(Problem& P, const Mesh& m, int kind, int region, bool c
 // unknown (col, 0, row, comp), of a vertex pressure (col + 1, 1, row, 0): each pressure
 // follows the velocities of the next half-grid column, so that every leading block of
 // the saddle-point matrix is invertible and the LU needs no pivoting.
+// 3D: the sweep runs along the longest side of the box; "column" is then a plane of the half
+// grid and every vertex pressure follows the velocities of the next plane.
 static void order_unknowns(Problem& P) {
-  const int nI = 2 * (P.i1 - P.i0) + 1;
-  const bool along_x = (P.i1 - P.i0) >= (P.j1 - P.j0);
+  const int D = P.dim;
+  const int nI = 2 * (P.i1 - P.i0) + 1, nJ = 2 * (P.j1 - P.j0) + 1, nK = 2 * (P.k1 - P.k0) + 1;
+  const int ext[3] = {P.i1 - P.i0, P.j1 - P.j0, P.k1 - P.k0};
+  int axis = 0;
+  if (D == 2) {
+    axis = ext[0] >= ext[1] ? 0 : 1;
+  } else {
+    for (int d = 1; d < 3; ++d)
+      if (ext[d] > ext[axis]) axis = d;
+  }
+  const int PC = D;   // component index of the pressure
   struct Key { int a, b, c, d, node, comp; };
   std::vector<Key> keys;
   for (int l = 0; l < P.nn; ++l) {
-    int a = l % nI, b = l / nI;
-    int col = along_x ? a : b, row = along_x ? b : a;
+    int crd[3] = {l % nI, (l / nI) % nJ, D == 3 ? l / (nI * nJ) : 0};
+    int col = crd[axis], row;
+    if (D == 2) {
+      row = axis == 0 ? crd[1] : crd[0];
+    } else {
+      const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+      const int n1 = o1 == 0 ? nI : nJ;
+      row = crd[o2] * n1 + crd[o1];
+    }
+    (void)nK;
     if (P.nkind[l] == 0) {
       if (P.kind == PK_OSEEN) {
-        keys.push_back({col, 0, row, 0, l, 0});
-        keys.push_back({col, 0, row, 1, l, 1});
+        for (int c = 0; c < D; ++c) keys.push_back({col, 0, row, c, l, c});
       } else {
         keys.push_back({col, 0, row, 0, l, 0});
       }
     }
-    if (P.kind == PK_OSEEN && P.vidx[l] >= 0 && !P.art[l]) keys.push_back({col + 1, 1, row, 0, l, 2});
+    if (P.kind == PK_OSEEN && P.vidx[l] >= 0 && !P.art[l]) keys.push_back({col + 1, 1, row, 0, l, PC});
   }
   std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
     return std::tie(x.a, x.b, x.c, x.d) < std::tie(y.a, y.b, y.c, y.d);
@@ -205,7 +223,7 @@ static void order_unknowns(Problem& P) {
   P.n = (int)keys.size();
   P.dof_node.resize(P.n); P.dof_comp.resize(P.n);
   if (P.kind == PK_OSEEN) {
-    P.node_dof.assign(2 * P.nn, -1);
+    P.node_dof.assign((size_t)D * P.nn, -1);
     P.vert_dof.assign(P.nvl, -1);
   } else {
     P.node_dof.assign(P.nn, -1);
@@ -215,21 +233,22 @@ static void order_unknowns(Problem& P) {
     P.dof_node[d] = keys[d].node;
     P.dof_comp[d] = keys[d].comp;
     if (P.kind == PK_OSEEN) {
-      if (keys[d].comp < 2) P.node_dof[2 * keys[d].node + keys[d].comp] = d;
+      if (keys[d].comp < D) P.node_dof[(size_t)D * keys[d].node + keys[d].comp] = d;
       else P.vert_dof[P.vidx[keys[d].node]] = d;
     } else {
       P.node_dof[keys[d].node] = d;
     }
   }
-  const int S = P.slots();
+  const int S = P.slots(), NPE = P.npe(), VPE = P.vpe(), VS = P.vslots();
   P.slot_dof.assign((size_t)P.ne * S, -1);
   for (int e = 0; e < P.ne; ++e) {
     if (P.kind == PK_OSEEN) {
-      for (int i = 0; i < 6; ++i)
-        for (int a = 0; a < 2; ++a) P.slot_dof[(size_t)e * S + 2 * i + a] = P.node_dof[2 * P.e6[6 * e + i] + a];
-      for (int k = 0; k < 3; ++k) P.slot_dof[(size_t)e * S + 12 + k] = P.vert_dof[P.e3[3 * e + k]];
+      for (int i = 0; i < NPE; ++i)
+        for (int a = 0; a < D; ++a)
+          P.slot_dof[(size_t)e * S + D * i + a] = P.node_dof[(size_t)D * P.e6[(size_t)NPE * e + i] + a];
+      for (int k = 0; k < VPE; ++k) P.slot_dof[(size_t)e * S + VS + k] = P.vert_dof[P.e3[(size_t)VPE * e + k]];
     } else {
-      for (int i = 0; i < 6; ++i) P.slot_dof[(size_t)e * S + i] = P.node_dof[P.e6[6 * e + i]];
+      for (int i = 0; i < NPE; ++i) P.slot_dof[(size_t)e * S + i] = P.node_dof[P.e6[(size_t)NPE * e + i]];
     }
   }
 }
@@ -263,7 +282,7 @@ static bool pack_chunks(std::vector<std::pair<int32_t, int32_t>>& c, std::vector
 }
 
 static bool build_pattern(Problem& P) {
-  const int S = P.slots();
+  const int S = P.slots(), VS = P.vslots();
   std::vector<std::vector<int32_t>> rows(P.n);
   for (int e = 0; e < P.ne; ++e)
     for (int r = 0; r < S; ++r) {
@@ -272,7 +291,7 @@ static bool build_pattern(Problem& P) {
       for (int c = 0; c < S; ++c) {
         int dc = P.slot_dof[(size_t)e * S + c];
         if (dc < 0) continue;
-        if (P.kind == PK_OSEEN && r >= 12 && c >= 12) continue;   // zero pressure block
+        if (P.kind == PK_OSEEN && r >= VS && c >= VS) continue;   // zero pressure block
         rows[dr].push_back(dc);
       }
     }
@@ -301,7 +320,7 @@ static bool build_pattern(Problem& P) {
       for (int c = 0; c < S; ++c) {
         int dc = P.slot_dof[(size_t)e * S + c];
         if (dc < 0) continue;
-        if (P.kind == PK_OSEEN && r >= 12 && c >= 12) continue;
+        if (P.kind == PK_OSEEN && r >= VS && c >= VS) continue;
         const int32_t* b = &P.colidx[P.rowptr[dr]];
         const int32_t* en = &P.colidx[P.rowptr[dr + 1]];
         int32_t k = P.rowptr[dr] + (int32_t)(std::lower_bound(b, en, dc) - b);
@@ -319,27 +338,33 @@ static bool build_pattern(Problem& P) {
   return true;
 }
 
-static bool finish_problem(Problem& P) {
+bool finish_problem(Problem& P) {
   order_unknowns(P);
   return build_pattern(P);
 }
 
-static const char* kLongRun = "a matrix or vector entry receives more than 32 element contributions";
+const char* kLongRun = "a matrix or vector entry receives more than 32 element contributions";
 
 // Multifrontal analysis of a local system (Oseen, or the pattern shared by the three Darcy
 // fields): the unknowns' half-grid coordinates in the box (vertices at even coordinates) drive
 // the nested dissection.
-static std::string analyse_mf(Problem& P, int leaf) {
-  const int nI = 2 * (P.i1 - P.i0) + 1;
-  std::vector<int32_t> coord((size_t)P.n * 2);
+std::string analyse_mf(Problem& P, int leaf) {
+  const int D = P.dim;
+  const int nI = 2 * (P.i1 - P.i0) + 1, nJ = 2 * (P.j1 - P.j0) + 1;
+  std::vector<int32_t> coord((size_t)P.n * D);
   std::vector<int8_t> pres(P.n);
   for (int d = 0; d < P.n; ++d) {
     const int l = P.dof_node[d];
-    coord[2 * (size_t)d] = l % nI;
-    coord[2 * (size_t)d + 1] = l / nI;
-    pres[d] = P.dof_comp[d] == 2;
+    coord[(size_t)D * d] = l % nI;
+    if (D == 2) {
+      coord[(size_t)D * d + 1] = l / nI;
+    } else {
+      coord[(size_t)D * d + 1] = (l / nI) % nJ;
+      coord[(size_t)D * d + 2] = l / (nI * nJ);
+    }
+    pres[d] = P.dof_comp[d] == D;
   }
-  return mf_analyse(P.n, 2, coord.data(), pres.data(), P.rowptr.data(), P.colidx.data(), leaf, P.mf);
+  return mf_analyse(P.n, D, coord.data(), pres.data(), P.rowptr.data(), P.colidx.data(), leaf, P.mf);
 }
 
 // ------------------------------------------------------------------------------ prolongation
@@ -391,9 +416,9 @@ static void prolong_table(const Mesh& H, const double* pts, int npts, int nb,
   }
 }
 
-static void glue_table(const std::vector<Problem>& probs, int nnodes, bool vertices,
-                       std::vector<int32_t>& ptr, std::vector<int32_t>& prob,
-                       std::vector<int32_t>& loc, std::vector<double>& w) {
+void glue_table(const std::vector<Problem>& probs, int nnodes, bool vertices,
+                std::vector<int32_t>& ptr, std::vector<int32_t>& prob,
+                std::vector<int32_t>& loc, std::vector<double>& w) {
   std::vector<std::vector<std::pair<int32_t, int32_t>>> lists(nnodes);
   for (size_t p = 0; p < probs.size(); ++p) {
     const Problem& P = probs[p];
@@ -466,6 +491,8 @@ static void filter_glue(std::vector<int32_t>& ptr, std::vector<int32_t>& prob, s
 
 std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd, Layout& L, int mf_leaf,
                          int rank, int nranks) {
+  if (md.dim == 3) return build_layout3(md, pd, L, mf_leaf, rank, nranks);
+  if (md.dim != 0 && md.dim != 2) return "invalid mesh dimension";
   if (md.nx_coarse <= 0 || md.ny_coarse <= 0 || md.ny_coarse > TPNS_MAX_COARSE_ROWS ||
       md.fine_per_coarse_x <= 0)
     return "invalid mesh description";
@@ -536,6 +563,11 @@ std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd
     if (L.gc_ptr[i + 1] == L.gc_ptr[i]) return "a conduit node is in no D_j";
   for (int i = 0; i < L.mph.nn; ++i)
     if (L.gp_ptr[i + 1] == L.gp_ptr[i]) return "a porous node is in no D_j";
+  return split_ranks(L, rank, nranks);
+}
+
+// Keep this rank's local problems and their glue entries (no-op for one rank).
+std::string split_ranks(Layout& L, int rank, int nranks) {
   if (nranks > 1) {
     if (rank < 0 || rank >= nranks || nranks > (int)L.fluid.size() || nranks > (int)L.porous.size())
       return "invalid rank split: nranks must not exceed the subdomains per region";

@@ -18,7 +18,7 @@ MAX_COARSE_ROWS = 64
 
 class MeshDesc(C.Structure):
     _fields_ = [("nx_coarse", C.c_int32), ("ny_coarse", C.c_int32), ("fine_per_coarse_x", C.c_int32),
-                ("fine_rows_from_gamma", C.c_int32 * MAX_COARSE_ROWS)]
+                ("fine_rows_from_gamma", C.c_int32 * MAX_COARSE_ROWS), ("dim", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -28,7 +28,7 @@ class Params(C.Structure):
 
 
 class PartitionDesc(C.Structure):
-    _fields_ = [("nsub_x", C.c_int32), ("nsub_y", C.c_int32), ("overlap", C.c_int32)]
+    _fields_ = [("nsub_x", C.c_int32), ("nsub_y", C.c_int32), ("overlap", C.c_int32), ("nsub_z", C.c_int32)]
 
 
 class DataDesc(C.Structure):
@@ -142,13 +142,20 @@ def _check(lib, ctx, status):
 def descriptors(w):
     """ABI descriptors of a workloads.Workload."""
     md = MeshDesc()
-    md.nx_coarse, md.ny_coarse, md.fine_per_coarse_x = w.nx_coarse, w.ny_coarse, w.fine_per_coarse_x
-    for c, m in enumerate(w.fine_rows_from_gamma):
-        md.fine_rows_from_gamma[c] = m
     p = w.params
     pr = Params(p.nu, p.eta, p.rho, p.mu, p.alpha, p.sigma, p.sigma_star, (C.c_double * 3)(*p.phiC),
                 (C.c_double * 3)(*p.k))
-    pd = PartitionDesc(w.nsub[0], w.nsub[1], w.overlap)
+    if getattr(w, "dim", 2) == 3:
+        md.nx_coarse = md.ny_coarse = w.n_coarse
+        md.fine_per_coarse_x = w.fine_per_coarse
+        md.dim = 3
+        pd = PartitionDesc(w.nsub[0], w.nsub[1], w.overlap, w.nsub[2])
+        return md, pr, pd, DataDesc(w.mms)
+    md.nx_coarse, md.ny_coarse, md.fine_per_coarse_x = w.nx_coarse, w.ny_coarse, w.fine_per_coarse_x
+    for c, m in enumerate(w.fine_rows_from_gamma):
+        md.fine_rows_from_gamma[c] = m
+    md.dim = 2
+    pd = PartitionDesc(w.nsub[0], w.nsub[1], w.overlap, 1)
     dd = DataDesc(w.mms)
     return md, pr, pd, dd
 
