@@ -28,6 +28,10 @@
  *     vertices), 3 = p_F (macro-fracture), 4 = p_f (micro-fracture), 5 = p_m (matrix), the
  *     last three on the P2 nodes of the porous mesh.  Global fine numbering: vertex
  *     (i, j) -> i + (nx+1) j, then one node per edge, edges sorted by (min, max) vertex id.
+ *     3D (tpns_mesh_desc.dim = 3): 0, 1, 2 = u_x, u_y, u_z, 3 = p, 4, 5, 6 = p_F, p_f, p_m;
+ *     vertex (i, j, k) -> i + (nx+1) (j + (ny+1) k), then the edges of the Kuhn
+ *     tetrahedra sorted by (min, max) vertex id.  Manufactured solutions: 1, 3 (2D), 2, 4
+ *     (3D), 0 (zero data).
  */
 #ifndef TPNS_H
 #define TPNS_H

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libtpns.so")
-UNITS = ["setup.cpp", "setup3d.cpp", "mf_symbolic.cpp", "kernels_band_f32.cu", "kernels_band_f64.cu", "kernels_assemble.cu",
+UNITS = ["setup.cpp", "setup3d.cpp", "mf_symbolic.cpp", "kernels_band_f32.cu", "kernels_band_f64.cu", "kernels_assemble.cu", "kernels_assemble3d.cu",
          "kernels_mf.cu", "kernels_krylov.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

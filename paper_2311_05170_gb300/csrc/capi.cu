@@ -33,6 +33,10 @@ struct tpns_ctx {
   Phys phys{};
   Layout L;
   RefTables ref{};
+  RefTables3 ref3{};
+  // element shape: dimension, Oseen / Darcy slots per element, P2 nodes and vertices per
+  // element, geometry doubles per element
+  int dim = 2, SO = 15, SD = 6, NPE = 6, VPE = 3, GEO = 11;
   std::string err;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -237,6 +241,48 @@ static double mms_pd_host(const Phys& P, int f, double x, double y, double t) {
   return 0.0;
 }
 
+// 3D manufactured fields (mms 2: trigonometric, 4: polynomial patch; see device.cuh)
+static void mms3_u_host(const Phys& P, const double* X, double t, double* u) {
+  const double pi = 3.141592653589793;
+  const double x = X[0], y = X[1], z = X[2];
+  if (P.mms == 2) {
+    const double E = std::exp(-t);
+    u[0] = std::sin(pi * x) * std::cos(pi * y) * std::cos(pi * z) * E;
+    u[1] = std::cos(pi * x) * std::sin(pi * y) * std::cos(pi * z) * E;
+    u[2] = -2.0 * std::cos(pi * x) * std::cos(pi * y) * std::sin(pi * z) * E;
+  } else if (P.mms == 4) {
+    u[0] = x * x; u[1] = y * y; u[2] = -2.0 * (x + y) * z;
+  } else {
+    u[0] = u[1] = u[2] = 0.0;
+  }
+}
+static double mms3_p_host(const Phys& P, const double* X, double t) {
+  const double pi = 3.141592653589793;
+  if (P.mms == 2) return std::cos(pi * X[0]) * std::cos(pi * X[1]) * std::cos(pi * X[2]) * std::exp(-t);
+  if (P.mms == 4) return X[0] + X[1] + X[2];
+  return 0.0;
+}
+static double mms3_pd_host(const Phys& P, int f, const double* X, double t) {
+  const double a = 3.0 - f;
+  const double pi = 3.141592653589793;
+  if (P.mms == 2) return a * std::cos(pi * X[0]) * std::cos(pi * X[1]) * std::cos(pi * X[2]) * std::exp(-t);
+  if (P.mms == 4) return a * (X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+  return 0.0;
+}
+// velocity / pressure / Darcy pressure of the manufactured solution at node i of a mesh
+static void mms_u_node(const tpns_ctx* ctx, const Mesh& m, int i, double t, double* u) {
+  if (ctx->dim == 3) mms3_u_host(ctx->phys, &m.node[3 * (size_t)i], t, u);
+  else mms_u_host(ctx->phys, m.node[2 * (size_t)i], m.node[2 * (size_t)i + 1], t, u);
+}
+static double mms_p_node(const tpns_ctx* ctx, const Mesh& m, int i, double t) {
+  if (ctx->dim == 3) return mms3_p_host(ctx->phys, &m.node[3 * (size_t)i], t);
+  return mms_p_host(ctx->phys, m.node[2 * (size_t)i], m.node[2 * (size_t)i + 1], t);
+}
+static double mms_pd_node(const tpns_ctx* ctx, int f, const Mesh& m, int i, double t) {
+  if (ctx->dim == 3) return mms3_pd_host(ctx->phys, f, &m.node[3 * (size_t)i], t);
+  return mms_pd_host(ctx->phys, f, m.node[2 * (size_t)i], m.node[2 * (size_t)i + 1], t);
+}
+
 static std::vector<int32_t> inverse_map(const std::vector<int32_t>& g, int n) {
   std::vector<int32_t> inv(n, -1);
   for (size_t l = 0; l < g.size(); ++l) inv[g[l]] = (int32_t)l;
@@ -252,7 +298,13 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     ctx->err = msg;
     return TPNS_EINVAL;
   }
-  build_ref_tables(ctx->ref);
+  ctx->dim = L.dim;
+  if (ctx->dim == 3) {
+    build_ref_tables3(ctx->ref3);
+    ctx->SO = 34; ctx->SD = 10; ctx->NPE = 10; ctx->VPE = 4; ctx->GEO = 22;
+  } else {
+    build_ref_tables(ctx->ref);
+  }
   ctx->nf = (int)L.fluid.size();
   ctx->np = (int)L.porous.size();
   ctx->probs.clear();
@@ -457,8 +509,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   // footprint check before any allocation
   const size_t Tsz = ctx->prec == TPNS_FP64 ? 8 : 4;
   size_t est = (size_t)ctx->band_local_len * Tsz + (size_t)ctx->band_coarse_len * 8 +
-               (size_t)(ctx->ne_osl + ctx->ne_cf) * (225 + 15) * 8 + (size_t)ctx->vals_tot * 8 +
-               (size_t)ctx->nnz_tot * 8 + (size_t)ctx->xvec_tot * 3 * 8 + (size_t)ctx->ne_tot * 11 * 8 +
+               (size_t)(ctx->ne_osl + ctx->ne_cf) * (ctx->SO * ctx->SO + ctx->SO) * 8 + (size_t)ctx->vals_tot * 8 +
+               (size_t)ctx->nnz_tot * 8 + (size_t)ctx->xvec_tot * 3 * 8 + (size_t)ctx->ne_tot * ctx->GEO * 8 +
                (size_t)(ctx->mf_F_len + ctx->mf_dinv_len + ctx->mf_upd_len + 2 * (ctx->mf ? ctx->xvec_tot : 0)) * Tsz;
   ctx->budget = budget;
   if (budget > 0 && est > budget) {
@@ -489,10 +541,11 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     }
   }
   // element arrays
-  std::vector<int32_t> h_eprob(ctx->ne_tot), h_e6((size_t)ctx->ne_tot * 6), h_e3((size_t)ctx->ne_tot * 3);
+  const int NPE = ctx->NPE, VPE = ctx->VPE, GEO = ctx->GEO, DIM = ctx->dim;
+  std::vector<int32_t> h_eprob(ctx->ne_tot), h_e6((size_t)ctx->ne_tot * NPE), h_e3((size_t)ctx->ne_tot * VPE);
   std::vector<int8_t> h_egam(ctx->ne_tot);
-  std::vector<double> h_geo((size_t)ctx->ne_tot * 11);
-  std::vector<int32_t> h_gnode(ctx->nn_tot), h_gam(ctx->nn_tot), h_ndof((size_t)ctx->nn_tot * 2, -1),
+  std::vector<double> h_geo((size_t)ctx->ne_tot * GEO);
+  std::vector<int32_t> h_gnode(ctx->nn_tot), h_gam(ctx->nn_tot), h_ndof((size_t)ctx->nn_tot * DIM, -1),
       h_nprob(ctx->nn_tot), h_nvidx(ctx->nn_tot);
   std::vector<int8_t> h_nkind(ctx->nn_tot);
   std::vector<int32_t> h_vloc(ctx->nv_tot), h_vdof(ctx->nv_tot, -1);
@@ -504,9 +557,34 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     for (int el = 0; el < P.ne; ++el) {
       int64_t ge = ctx->e_off[p] + el;
       h_eprob[ge] = p;
-      for (int k = 0; k < 6; ++k) h_e6[ge * 6 + k] = P.e6[6 * el + k];
-      for (int k = 0; k < 3; ++k) h_e3[ge * 3 + k] = P.e3[3 * el + k];
+      for (int k = 0; k < NPE; ++k) h_e6[ge * NPE + k] = P.e6[(size_t)NPE * el + k];
+      for (int k = 0; k < VPE; ++k) h_e3[ge * VPE + k] = P.e3[(size_t)VPE * el + k];
       h_egam[ge] = P.egam[el];
+      if (DIM == 3) {
+        // vertices, J^{-1} (row-major: d xi_r / d x_c), |det J|
+        const int32_t* tv = &m.tri[4 * (size_t)P.etri[el]];
+        double* g = &h_geo[ge * GEO];
+        double J[3][3];
+        for (int q = 0; q < 4; ++q)
+          for (int c = 0; c < 3; ++c) g[3 * q + c] = m.node[3 * (size_t)tv[q] + c];
+        for (int c = 0; c < 3; ++c)
+          for (int r = 0; r < 3; ++r) J[c][r] = g[3 * (r + 1) + c] - g[c];
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        double* Ji = g + 12;
+        Ji[0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+        Ji[1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        Ji[2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        Ji[3] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+        Ji[4] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        Ji[5] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        Ji[6] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+        Ji[7] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        Ji[8] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        g[21] = std::fabs(det);
+        continue;
+      }
       const int32_t* tv = &m.tri[3 * (size_t)P.etri[el]];
       double x0 = m.node[2 * tv[0]], y0 = m.node[2 * tv[0] + 1];
       double x1 = m.node[2 * tv[1]], y1 = m.node[2 * tv[1] + 1];
@@ -529,10 +607,9 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       h_nprob[gn] = p;
       h_nvidx[gn] = P.vidx[l];
       if (P.kind == PK_OSEEN) {
-        h_ndof[2 * gn] = P.node_dof[2 * l];
-        h_ndof[2 * gn + 1] = P.node_dof[2 * l + 1];
+        for (int c = 0; c < DIM; ++c) h_ndof[(size_t)DIM * gn + c] = P.node_dof[(size_t)DIM * l + c];
       } else {
-        h_ndof[2 * gn] = P.node_dof[l];
+        h_ndof[(size_t)DIM * gn] = P.node_dof[l];
       }
     }
     for (int vv = 0; vv < P.nvl; ++vv) {
@@ -553,8 +630,14 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   TRY(upload(ctx, &ctx->d_nvidx, h_nvidx));
   TRY(upload(ctx, &ctx->d_vloc, h_vloc));
   TRY(upload(ctx, &ctx->d_vert_dof, h_vdof));
-  std::vector<double> h_ref(sizeof(RefTables) / sizeof(double));
-  std::memcpy(h_ref.data(), &ctx->ref, sizeof(RefTables));
+  std::vector<double> h_ref;
+  if (DIM == 3) {
+    h_ref.resize(sizeof(RefTables3) / sizeof(double));
+    std::memcpy(h_ref.data(), &ctx->ref3, sizeof(RefTables3));
+  } else {
+    h_ref.resize(sizeof(RefTables) / sizeof(double));
+    std::memcpy(h_ref.data(), &ctx->ref, sizeof(RefTables));
+  }
   TRY(upload(ctx, &ctx->d_ref, h_ref));
   TRY(upload(ctx, &ctx->d_rowptr, h_rowptr));
   TRY(upload(ctx, &ctx->d_colidx, h_colidx));
@@ -679,9 +762,10 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       CK(cudaMemset(ctx->d_uslab_coarse_f, 0, (size_t)ctx->uslab_coarse_len * 4));
     }
   }
-  TRY(dalloc(ctx, &ctx->d_Ke, (size_t)(ctx->ne_osl + ctx->ne_cf) * 225));
-  TRY(dalloc(ctx, &ctx->d_Re, (size_t)(ctx->ne_osl + ctx->ne_cf) * 15));
-  TRY(dalloc(ctx, &ctx->d_ReD, (size_t)(ctx->ne_dl + ctx->ne_cp) * 18));
+  const int SO = ctx->SO, SD = ctx->SD;
+  TRY(dalloc(ctx, &ctx->d_Ke, (size_t)(ctx->ne_osl + ctx->ne_cf) * SO * SO));
+  TRY(dalloc(ctx, &ctx->d_Re, (size_t)(ctx->ne_osl + ctx->ne_cf) * SO));
+  TRY(dalloc(ctx, &ctx->d_ReD, (size_t)(ctx->ne_dl + ctx->ne_cp) * 3 * SD));
   // scatter maps with global offsets
   auto build_map = [&](int p, bool matrix, std::vector<int32_t>& T_, std::vector<int32_t>& S_) {
     const Problem& P = *ctx->probs[p];
@@ -692,13 +776,13 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       for (size_t k = 0; k < tg.size(); ++k) {
         if (tg[k] < 0) { T_.push_back(-1); S_.push_back(0); continue; }
         T_.push_back((int32_t)((matrix ? S.val_off : S.x_off) + tg[k]));
-        S_.push_back((int32_t)(ctx->e_off[p] * (matrix ? 225 : 15) + sr[k]));
+        S_.push_back((int32_t)(ctx->e_off[p] * (matrix ? SO * SO : SO) + sr[k]));
       }
     } else {
       const int64_t ebase = ctx->e_off[p] - (P.coarse ? ctx->e_off[p] : ctx->eD0);
       for (int f = 0; f < 3; ++f) {
         const SysDev& S = ctx->hsys[ctx->sys_first[p] + f];
-        const int per = matrix ? 36 : 6;
+        const int per = matrix ? SD * SD : SD;
         for (size_t k = 0; k < tg.size(); ++k) {
           if (tg[k] < 0) { T_.push_back(-1); S_.push_back(0); continue; }
           int el = sr[k] / per, rem = sr[k] % per;
@@ -728,21 +812,21 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   // fields
   const int nncH = L.mcH.nn, nvcH = L.mcH.nv, nnpH = L.mpH.nn;
   const int nnc = L.mch.nn, nvc = L.mch.nv, nnp = L.mph.nn;
-  TRY(dalloc(ctx, &ctx->d_uc_old, (size_t)nncH * 2));
-  TRY(dalloc(ctx, &ctx->d_uc_new, (size_t)nncH * 2));
+  TRY(dalloc(ctx, &ctx->d_uc_old, (size_t)nncH * DIM));
+  TRY(dalloc(ctx, &ctx->d_uc_new, (size_t)nncH * DIM));
   TRY(dalloc(ctx, &ctx->d_pc_new, (size_t)nvcH));
   TRY(dalloc(ctx, &ctx->d_pd_old, (size_t)nnpH * 3));
   TRY(dalloc(ctx, &ctx->d_pd_new, (size_t)nnpH * 3));
-  size_t zlen = std::max<size_t>((size_t)nnpH * 3, (size_t)(2 * L.cfl.nn + L.cfl.nvl));
+  size_t zlen = std::max<size_t>((size_t)nnpH * 3, (size_t)(DIM * L.cfl.nn + L.cfl.nvl));
   TRY(dalloc(ctx, &ctx->d_zero, zlen));
   CK(cudaMemset(ctx->d_zero, 0, zlen * sizeof(double)));
-  TRY(dalloc(ctx, &ctx->d_delta, (size_t)(2 * L.cfl.nn + L.cfl.nvl)));
-  TRY(dalloc(ctx, &ctx->d_FW1, (size_t)nnc * 2));
-  TRY(dalloc(ctx, &ctx->d_FW0, (size_t)nnc * 2));
+  TRY(dalloc(ctx, &ctx->d_delta, (size_t)(DIM * L.cfl.nn + L.cfl.nvl)));
+  TRY(dalloc(ctx, &ctx->d_FW1, (size_t)nnc * DIM));
+  TRY(dalloc(ctx, &ctx->d_FW0, (size_t)nnc * DIM));
   TRY(dalloc(ctx, &ctx->d_FP1, (size_t)nvc));
   TRY(dalloc(ctx, &ctx->d_FPD1, (size_t)nnp * 3));
   TRY(dalloc(ctx, &ctx->d_FPD0, (size_t)nnp * 3));
-  TRY(dalloc(ctx, &ctx->d_out_u, (size_t)nnc * 2));
+  TRY(dalloc(ctx, &ctx->d_out_u, (size_t)nnc * DIM));
   TRY(dalloc(ctx, &ctx->d_out_p, (size_t)nvc));
   TRY(dalloc(ctx, &ctx->d_out_pd, (size_t)nnp * 3));
   // prolongation tables; the porous coarse index is remapped to the coarse Darcy local order
@@ -768,7 +852,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   for (int p = 0; p < ctx->nprob; ++p) {
     const Problem& P = *ctx->probs[p];
     if (p == CF || p == CP) continue;
-    size_t len = P.kind == PK_OSEEN ? (size_t)(2 * P.nn + P.nvl) : (size_t)3 * P.nn;
+    size_t len = P.kind == PK_OSEEN ? (size_t)(DIM * P.nn + P.nvl) : (size_t)3 * P.nn;
     TRY(dalloc(ctx, &state[p], len));
   }
   // descriptors
@@ -776,7 +860,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   for (int p = 0; p < ctx->nprob; ++p) {
     const Problem& P = *ctx->probs[p];
     ProbDev& D = ctx->hprob[p];
-    D.kind = P.kind; D.coarse = P.coarse; D.ne = P.ne; D.nn = P.nn; D.nvl = P.nvl; D.n = P.n;
+    D.kind = P.kind; D.coarse = P.coarse; D.dim = DIM; D.ne = P.ne; D.nn = P.nn; D.nvl = P.nvl; D.n = P.n;
     D.e_off = ctx->e_off[p]; D.n_off = ctx->n_off[p]; D.v_off = ctx->v_off[p];
     D.x_off = ctx->hsys[ctx->sys_first[p]].x_off;
     D.fstride = 0;
@@ -804,13 +888,12 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   }
   TRY(upload(ctx, &ctx->d_probs, ctx->hprob));
   // initial data: coarse interpolants and e^0 = I_h u0 - I_h I_H u0 (0 on the artificial boundary)
-  const Phys& Ph = ctx->phys;
-  std::vector<double> uc((size_t)nncH * 2), pc(nvcH), pdl((size_t)nnpH * 3);
-  for (int i = 0; i < nncH; ++i) mms_u_host(Ph, L.mcH.node[2 * i], L.mcH.node[2 * i + 1], 0.0, &uc[2 * i]);
-  for (int i = 0; i < nvcH; ++i) pc[i] = mms_p_host(Ph, L.mcH.node[2 * i], L.mcH.node[2 * i + 1], 0.0);
+  std::vector<double> uc((size_t)nncH * DIM), pc(nvcH), pdl((size_t)nnpH * 3);
+  for (int i = 0; i < nncH; ++i) mms_u_node(ctx, L.mcH, i, 0.0, &uc[(size_t)DIM * i]);
+  for (int i = 0; i < nvcH; ++i) pc[i] = mms_p_node(ctx, L.mcH, i, 0.0);
   for (int l = 0; l < nnpH; ++l) {
     int g = L.cpo.gnode[l];
-    for (int f = 0; f < 3; ++f) pdl[(size_t)f * nnpH + l] = mms_pd_host(Ph, f, L.mpH.node[2 * g], L.mpH.node[2 * g + 1], 0.0);
+    for (int f = 0; f < 3; ++f) pdl[(size_t)f * nnpH + l] = mms_pd_node(ctx, f, L.mpH, g, 0.0);
   }
   CK(cudaMemcpy(ctx->d_uc_old, uc.data(), uc.size() * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_uc_new, uc.data(), uc.size() * 8, cudaMemcpyHostToDevice));
@@ -819,18 +902,17 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   CK(cudaMemcpy(ctx->d_pd_new, pdl.data(), pdl.size() * 8, cudaMemcpyHostToDevice));
   ctx->stats.h2d_bytes += (int64_t)(2 * uc.size() + pc.size() + 2 * pdl.size()) * 8;
   // fine interpolants of the coarse initial data (host, same tables as the device)
-  std::vector<double> Iuh((size_t)nnc * 2, 0.0), Ipdh((size_t)nnp * 3, 0.0);
+  std::vector<double> Iuh((size_t)nnc * DIM, 0.0), Ipdh((size_t)nnp * 3, 0.0);
   for (int i = 0; i < nnc; ++i)
-    for (int k = 0; k < 6; ++k) {
-      int c = L.pc2_idx[(size_t)i * 6 + k];
-      double w = L.pc2_w[(size_t)i * 6 + k];
-      Iuh[2 * i] += w * uc[2 * c];
-      Iuh[2 * i + 1] += w * uc[2 * c + 1];
+    for (int k = 0; k < NPE; ++k) {
+      int c = L.pc2_idx[(size_t)i * NPE + k];
+      double w = L.pc2_w[(size_t)i * NPE + k];
+      for (int d = 0; d < DIM; ++d) Iuh[(size_t)DIM * i + d] += w * uc[(size_t)DIM * c + d];
     }
   for (int i = 0; i < nnp; ++i)
-    for (int k = 0; k < 6; ++k) {
-      int c = pp2[(size_t)i * 6 + k];
-      double w = L.pp2_w[(size_t)i * 6 + k];
+    for (int k = 0; k < NPE; ++k) {
+      int c = pp2[(size_t)i * NPE + k];
+      double w = L.pp2_w[(size_t)i * NPE + k];
       for (int f = 0; f < 3; ++f) Ipdh[(size_t)f * nnp + i] += w * pdl[(size_t)f * nnpH + c];
     }
   for (int p = 0; p < ctx->nprob; ++p) {
@@ -838,14 +920,13 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     const Problem& P = *ctx->probs[p];
     std::vector<double> e0;
     if (P.kind == PK_OSEEN) {
-      e0.assign((size_t)2 * P.nn + P.nvl, 0.0);
+      e0.assign((size_t)DIM * P.nn + P.nvl, 0.0);
       for (int l = 0; l < P.nn; ++l) {
         if (P.nkind[l] == 2) continue;
         int g = P.gnode[l];
-        double u[2];
-        mms_u_host(Ph, L.mch.node[2 * g], L.mch.node[2 * g + 1], 0.0, u);
-        e0[2 * l] = u[0] - Iuh[2 * g];
-        e0[2 * l + 1] = u[1] - Iuh[2 * g + 1];
+        double u[3];
+        mms_u_node(ctx, L.mch, g, 0.0, u);
+        for (int d = 0; d < DIM; ++d) e0[(size_t)DIM * l + d] = u[d] - Iuh[(size_t)DIM * g + d];
       }
     } else {
       e0.assign((size_t)3 * P.nn, 0.0);
@@ -853,7 +934,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
         if (P.nkind[l] == 2) continue;
         int g = P.gnode[l];
         for (int f = 0; f < 3; ++f)
-          e0[(size_t)f * P.nn + l] = mms_pd_host(Ph, f, L.mph.node[2 * g], L.mph.node[2 * g + 1], 0.0) - Ipdh[(size_t)f * nnp + g];
+          e0[(size_t)f * P.nn + l] = mms_pd_node(ctx, f, L.mph, g, 0.0) - Ipdh[(size_t)f * nnp + g];
       }
     }
     CK(cudaMemcpy(state[p], e0.data(), e0.size() * 8, cudaMemcpyHostToDevice));
@@ -866,7 +947,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   A.probs = ctx->d_probs; A.eprob = ctx->d_eprob; A.geo = ctx->d_geo; A.e6 = ctx->d_e6; A.e3 = ctx->d_e3;
   A.egam = ctx->d_egam; A.gnode = ctx->d_gnode; A.nkind = ctx->d_nkind; A.gam_src = ctx->d_gam_src;
   A.node_dof = ctx->d_node_dof; A.vloc = ctx->d_vloc; A.vert_dof = ctx->d_vert_dof; A.ref = ctx->d_ref;
-  A.phys = ctx->phys; A.tnow = ctx->d_tnow;
+  A.phys = ctx->phys; A.tnow = ctx->d_tnow; A.dim = DIM;
   GlueArgs& G = ctx->glue;
   G.fluid = ctx->d_probs;
   G.porous = ctx->d_probs + (ctx->nf + 1);
@@ -875,7 +956,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   G.gv_ptr = ctx->d_gv_ptr; G.gv_prob = ctx->d_gv_prob; G.gv_vert = ctx->d_gv_vert; G.gv_w = ctx->d_gv_w;
   G.FW1 = ctx->d_FW1; G.FP1 = ctx->d_FP1; G.FPD1 = ctx->d_FPD1;
   G.out_u = ctx->d_out_u; G.out_p = ctx->d_out_p; G.out_pd = ctx->d_out_pd;
-  G.nnc = nnc; G.nvc = nvc; G.nnp = nnp;
+  G.nnc = nnc; G.nvc = nvc; G.nnp = nnp; G.dim = DIM;
   G.add_coarse = ctx->rank == 0 ? 1 : 0;
   ctx->mfl.vals = ctx->d_vals;
   ctx->mfl.status = ctx->d_status;
@@ -925,7 +1006,7 @@ static tpns_status prolong_and_glue(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   CK(launch_prolong(L.mch.nn, L.mch.nv, L.mph.nn, ctx->d_pc2i, ctx->d_pc2w, ctx->d_pc1i, ctx->d_pc1w, ctx->d_pp2i,
                     ctx->d_pp2w, ctx->d_uc_new, ctx->d_uc_old, ctx->d_pc_new, ctx->d_pd_new, ctx->d_pd_old, L.mpH.nn,
-                    ctx->d_FW1, ctx->d_FW0, ctx->d_FP1, ctx->d_FPD1, ctx->d_FPD0, L.mph.nn, st));
+                    ctx->d_FW1, ctx->d_FW0, ctx->d_FP1, ctx->d_FPD1, ctx->d_FPD0, L.mph.nn, st, ctx->dim));
   return TPNS_OK;
 }
 
@@ -939,7 +1020,7 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
   const Layout& L = ctx->L;
   // Step 1(1): coarse Darcy solves (eqs. pFFully, pfFully, pmFully), Cholesky factors fixed
   CK(cudaMemcpyAsync(ctx->d_pd_new, ctx->d_pd_old, (size_t)L.mpH.nn * 3 * 8, cudaMemcpyDeviceToDevice, st));
-  double* ReCP = ctx->d_ReD + ctx->ne_dl * 18;
+  double* ReCP = ctx->d_ReD + ctx->ne_dl * 3 * ctx->SD;
   CK(launch_darcy_elem(ctx->asmargs, ctx->e_off[CP], ctx->ne_cp, ReCP, nullptr, st));
   CK(launch_seg_reduce(ctx->d_rcp_t, ctx->d_rcp_s, ctx->n_rcp, ReCP, ctx->d_b, st, nullptr));
   CK(launch_band_solve<double>(ctx->d_sys, ctx->d_list_cp, 3, ctx->n_max_cp, ctx->kmax_cp, ctx->d_lslab_coarse,
@@ -947,7 +1028,7 @@ static tpns_status coarse_step(tpns_ctx* ctx) {
                                st, nullptr));
   CK(launch_state(ctx->asmargs, ctx->d_nprob, ctx->d_nvidx, ctx->nb_cp, ctx->nn_cp, ctx->d_x, st, nullptr));
   // Step 1(2): coarse conduit problem (eq. pcFully) by Newton's method
-  CK(cudaMemcpyAsync(ctx->d_uc_new, ctx->d_uc_old, (size_t)L.mcH.nn * 2 * 8, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_uc_new, ctx->d_uc_old, (size_t)L.mcH.nn * ctx->dim * 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(ctx->d_newton_done, 0, sizeof(int), st));
   CK(cudaMemsetAsync(ctx->d_newton_iters, 0, sizeof(int), st));
   const int* skip = ctx->d_newton_done;
@@ -1097,7 +1178,7 @@ static tpns_status end_step_device(tpns_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   const Layout& L = ctx->L;
   ph_begin(ctx, PH_COPIES);
-  CK(cudaMemcpyAsync(ctx->d_uc_old, ctx->d_uc_new, (size_t)L.mcH.nn * 2 * 8, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_uc_old, ctx->d_uc_new, (size_t)L.mcH.nn * ctx->dim * 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(ctx->d_pd_old, ctx->d_pd_new, (size_t)L.mpH.nn * 3 * 8, cudaMemcpyDeviceToDevice, st));
   CK(launch_set_time(ctx->d_tnow, ctx->d_step, ctx->dt, 1, st));
   ph_end(ctx, PH_COPIES);
@@ -1300,7 +1381,7 @@ static tpns_status run_steps(tpns_ctx* ctx, int nsteps, bool from_traj) {
         return TPNS_EINVAL;
       }
       const Layout& L = ctx->L;
-      size_t nu = (size_t)L.mcH.nn * 2, npc = L.mcH.nv, npd = (size_t)L.mpH.nn * 3;
+      size_t nu = (size_t)L.mcH.nn * ctx->dim, npc = L.mcH.nv, npd = (size_t)L.mpH.nn * 3;
       cudaStream_t st = ctx->stream;
       CK(cudaMemcpyAsync(ctx->d_uc_old, ctx->traj[k], nu * 8, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(ctx->d_pd_old, ctx->traj[k] + nu + npc, npd * 8, cudaMemcpyDeviceToDevice, st));
@@ -1384,7 +1465,8 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
   // Darcy element matrices (run once) -> CSR values -> band Cholesky
   const int64_t neD = ctx->ne_dl + ctx->ne_cp;
   double* KeD = nullptr;
-  TRY(dalloc(ctx, &KeD, (size_t)neD * 108));
+  const int SD = ctx->SD;
+  TRY(dalloc(ctx, &KeD, (size_t)neD * 3 * SD * SD));
   std::vector<int32_t> t1, s1, t2, s2;
   for (int p = ctx->nf + 1; p <= CP; ++p) {
     const Problem& P = *ctx->probs[p];
@@ -1393,9 +1475,9 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
       const SysDev& S = ctx->hsys[ctx->sys_first[p] + f];
       for (size_t k = 0; k < P.mtgt.size(); ++k) {
         if (P.mtgt[k] < 0) { t1.push_back(-1); s1.push_back(0); continue; }
-        int el = P.msrc[k] / 36, rem = P.msrc[k] % 36;
+        int el = P.msrc[k] / (SD * SD), rem = P.msrc[k] % (SD * SD);
         t1.push_back((int32_t)(S.val_off + P.mtgt[k]));
-        s1.push_back((int32_t)(((ebase + el) * 3 + f) * 36 + rem));
+        s1.push_back((int32_t)(((ebase + el) * 3 + f) * SD * SD + rem));
       }
     }
   }
@@ -1655,7 +1737,11 @@ tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params
     g_err = "invalid physical parameters";
     return TPNS_EINVAL;
   }
-  if (data->mms_id != 0 && data->mms_id != 1 && data->mms_id != 3) { g_err = "unknown mms_id"; return TPNS_EINVAL; }
+  if (mesh->dim == 3 ? (data->mms_id != 0 && data->mms_id != 2 && data->mms_id != 4)
+                     : (data->mms_id != 0 && data->mms_id != 1 && data->mms_id != 3)) {
+    g_err = "unknown mms_id for this mesh dimension";
+    return TPNS_EINVAL;
+  }
   tpns_mesh_desc md1 = *mesh;
   tpns_partition_desc pd1 = *part;
   if (opt.algorithm == 1) {
@@ -1712,7 +1798,7 @@ tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params
     tpns_destroy(ctx);
     return s;
   }
-  ctx->stats.n_fine_dofs = (int64_t)ctx->L.mch.nn * 2 + ctx->L.mch.nv + (int64_t)ctx->L.mph.nn * 3;
+  ctx->stats.n_fine_dofs = (int64_t)ctx->L.mch.nn * ctx->dim + ctx->L.mch.nv + (int64_t)ctx->L.mph.nn * 3;
   ctx->stats.n_local_systems = (int64_t)ctx->list_local.size();
   ctx->stats.device_bytes = (int64_t)ctx->bytes;
   ctx->stats.band_lu_flops = ctx->lu_flops_step;
@@ -1947,7 +2033,7 @@ tpns_status tpns_coarse_precompute(tpns_ctx* ctx, int32_t nsteps) {
   if (!ctx || nsteps < 0 || ctx->host_only) return TPNS_EINVAL;
   ctx->err.clear();
   const Layout& L = ctx->L;
-  size_t nu = (size_t)L.mcH.nn * 2, npc = L.mcH.nv, npd = (size_t)L.mpH.nn * 3;
+  size_t nu = (size_t)L.mcH.nn * ctx->dim, npc = L.mcH.nv, npd = (size_t)L.mpH.nn * 3;
   size_t len = nu + npc + npd;
   for (double* p : ctx->traj) cudaFree(p), ctx->bytes -= len * 8;
   for (double* p : ctx->traj) {
@@ -2008,6 +2094,13 @@ tpns_status tpns_local_step(tpns_ctx* ctx, int32_t nsteps) {
 tpns_status tpns_num_dofs(const tpns_ctx* ctx, int32_t field, size_t* n) {
   if (!ctx || !n) return TPNS_EINVAL;
   const Layout& L = ctx->L;
+  if (ctx->L.dim == 3) {
+    if (field >= 0 && field <= 2) *n = (size_t)L.mch.nn;
+    else if (field == 3) *n = (size_t)L.mch.nv;
+    else if (field >= 4 && field <= 6) *n = (size_t)L.mph.nn;
+    else return TPNS_EINVAL;
+    return TPNS_OK;
+  }
   switch (field) {
     case 0: case 1: *n = (size_t)L.mch.nn; return TPNS_OK;
     case 2: *n = (size_t)L.mch.nv; return TPNS_OK;
@@ -2026,16 +2119,17 @@ tpns_status tpns_get_field(tpns_ctx* ctx, int32_t field, double* dst, size_t n, 
   cudaStream_t st = ctx->stream;
   const Layout& L = ctx->L;
   CK(cudaStreamSynchronize(st));
-  if (field <= 1) {
+  const int D = ctx->dim;
+  if (field < D) {
     // strided component of the interleaved velocity
-    std::vector<double> tmp((size_t)L.mch.nn * 2);
+    std::vector<double> tmp((size_t)L.mch.nn * D);
     CK(cudaMemcpy(tmp.data(), ctx->d_out_u, tmp.size() * 8, cudaMemcpyDeviceToHost));
     std::vector<double> comp(L.mch.nn);
-    for (int i = 0; i < L.mch.nn; ++i) comp[i] = tmp[2 * i + field];
+    for (int i = 0; i < L.mch.nn; ++i) comp[i] = tmp[(size_t)D * i + field];
     CK(cudaMemcpy(dst, comp.data(), need * 8, dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
     return TPNS_OK;
   }
-  const double* src = field == 2 ? ctx->d_out_p : ctx->d_out_pd + (size_t)(field - 3) * L.mph.nn;
+  const double* src = field == D ? ctx->d_out_p : ctx->d_out_pd + (size_t)(field - D - 1) * L.mph.nn;
   CK(cudaMemcpyAsync(dst, src, need * 8, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return TPNS_OK;

@@ -11,22 +11,23 @@ namespace tpns {
 struct ProbDev {
   int kind;          // 0 Oseen, 1 Darcy
   int coarse;        // 1: coarse problem of Step 1
+  int dim;           // 2 or 3: velocity components per node and coordinates per node
   int ne, nn, nvl, n;
   int64_t e_off;     // elements: geometry, e6, e3, egam
   int64_t n_off;     // local nodes: gnode, nkind, gam_src, node_dof (Oseen: 2 per node)
   int64_t v_off;     // local vertices: vloc, vert_dof
   int64_t x_off;     // unknown vectors (Darcy: 3 consecutive blocks of n)
-  const double* W1;  // Oseen: velocity about which the problem is linearised (2/node);
+  const double* W1;  // Oseen: velocity about which the problem is linearised (dim/node);
                      // Darcy: new coarse pressures (3 fields, stride `fstride`)
   const double* W0;  // Oseen: previous coarse velocity; Darcy: previous coarse pressures
   const double* P1;  // Oseen: coarse pressure at vertices (unused for Darcy)
   const double* GAM; // Oseen: porous p_F^n at Gamma partner nodes; Darcy: conduit velocity
-                     // u^n (2/node) at Gamma partner nodes
+                     // u^n (dim/node) at Gamma partner nodes
   const double* EN;  // local correction e^n read by the element kernels;
-                     // Oseen: 2*nn velocity then nvl pressure; Darcy: 3 blocks of nn
+                     // Oseen: dim*nn velocity then nvl pressure; Darcy: 3 blocks of nn
   double* EOUT;      // where the new correction e^{n+1} is written (same layout; equal to
                      // EN for local problems, so the state is updated in place)
-  const double* XY;  // node coordinates of the region mesh (2/node)
+  const double* XY;  // node coordinates of the region mesh (dim/node)
   int64_t fstride;   // field stride of Darcy sources W1 / W0
 };
 
@@ -156,6 +157,126 @@ __device__ __forceinline__ double mms_gd(const Phys& P, int fld, double x, doubl
     return -2.0 * P.k[2] / P.mu;
   }
   return 0.0;   // mms 1: all three vanish on y = 1
+}
+
+// ---------------------------------------------------------------- 3D manufactured data
+// Gamma is z = 1, n_c = (0,0,-1), n_p = (0,0,1), P_tau v = (v_x, v_y, 0).
+// mms 2: u = (sx cy cz, cx sy cz, -2 cx cy sz) e^-t (sx = sin(pi x), cx = cos(pi x), ...),
+//        p = cx cy cz e^-t, p_F, p_f, p_m = 3, 2, 1 times cx cy cz e^-t (div u = 0).
+// mms 4: u = (x^2, y^2, -2 (x + y) z), p = x + y + z, p_F, p_f, p_m = 3, 2, 1 times
+//        (x^2 + y^2 + z^2).
+// Forcing, sources and Gamma defects below are derived by hand from the strong form of
+// Sec. 2 (the oracle derives them independently, symbolically).
+__device__ __forceinline__ void mms3_u(const Phys& P, const double* X, double t, double* u) {
+  const double x = X[0], y = X[1], z = X[2];
+  if (P.mms == 2) {
+    double sx, cx, sy, cy, sz, cz;
+    sincospi(x, &sx, &cx);
+    sincospi(y, &sy, &cy);
+    sincospi(z, &sz, &cz);
+    const double E = exp(-t);
+    u[0] = sx * cy * cz * E;
+    u[1] = cx * sy * cz * E;
+    u[2] = -2.0 * cx * cy * sz * E;
+  } else if (P.mms == 4) {
+    u[0] = x * x;
+    u[1] = y * y;
+    u[2] = -2.0 * (x + y) * z;
+  } else {
+    u[0] = u[1] = u[2] = 0.0;
+  }
+}
+
+__device__ __forceinline__ double mms3_pd(const Phys& P, int f, const double* X, double t) {
+  const double a = 3.0 - f;
+  if (P.mms == 2) return a * cospi(X[0]) * cospi(X[1]) * cospi(X[2]) * exp(-t);
+  if (P.mms == 4) return a * (X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+  return 0.0;
+}
+
+// conduit forcing f = du/dt - div T(u, p) + (u.grad)u
+__device__ __forceinline__ void mms3_f(const Phys& P, const double* X, double t, double* f) {
+  const double x = X[0], y = X[1], z = X[2];
+  if (P.mms == 2) {
+    const double pi = 3.141592653589793;
+    double sx, cx, sy, cy, sz, cz;
+    sincospi(x, &sx, &cx);
+    sincospi(y, &sy, &cy);
+    sincospi(z, &sz, &cz);
+    const double E = exp(-t), E2 = E * E;
+    const double a = 3.0 * P.nu * pi * pi - 1.0;   // -du/dt - nu lap u = (3 nu pi^2 - 1) u
+    f[0] = sx * cy * cz * E * (a - pi) + pi * E2 * sx * cx * (cy * cy * cz * cz - sy * sy * cz * cz + 2.0 * cy * cy * sz * sz);
+    f[1] = cx * sy * cz * E * (a - pi) + pi * E2 * sy * cy * (cx * cx * cz * cz - sx * sx * cz * cz + 2.0 * cx * cx * sz * sz);
+    f[2] = cx * cy * sz * E * (-2.0 * a - pi) +
+           2.0 * pi * E2 * sz * cz * (sx * sx * cy * cy + cx * cx * sy * sy + 2.0 * cx * cx * cy * cy);
+  } else if (P.mms == 4) {
+    f[0] = 1.0 - 2.0 * P.nu + 2.0 * x * x * x;
+    f[1] = 1.0 - 2.0 * P.nu + 2.0 * y * y * y;
+    f[2] = 1.0 - 2.0 * z * (x * x + y * y) + 4.0 * z * (x + y) * (x + y);
+  } else {
+    f[0] = f[1] = f[2] = 0.0;
+  }
+}
+
+// Darcy sources q_F, q_f, q_m
+__device__ __forceinline__ double mms3_q(const Phys& P, int fld, const double* X, double t) {
+  const double kf = P.k[1], km = P.k[2], mu = P.mu;
+  const double cFf = P.sigma_star * kf / mu, cfm = P.sigma * km / mu;
+  if (P.mms == 2) {
+    const double pi2 = 9.869604401089358;
+    const double C = cospi(X[0]) * cospi(X[1]) * cospi(X[2]) * exp(-t);
+    if (fld == 0) return C * (-3.0 * P.phiC[0] + 9.0 * pi2 * P.k[0] / mu + cFf);
+    if (fld == 1) return C * (-2.0 * P.phiC[1] + 6.0 * pi2 * kf / mu - cFf + cfm);
+    return C * (-P.phiC[2] + 3.0 * pi2 * km / mu - cfm);
+  }
+  if (P.mms == 4) {
+    const double r2 = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    if (fld == 0) return -18.0 * P.k[0] / mu + cFf * r2;
+    if (fld == 1) return -12.0 * kf / mu + (cfm - cFf) * r2;
+    return -6.0 * km / mu - cfm * r2;
+  }
+  return 0.0;
+}
+
+// g_N = -n_c.T n_c - p_F/rho on z = 1
+__device__ __forceinline__ double mms3_gN(const Phys& P, double x, double y, double t) {
+  if (P.mms == 2) {
+    const double pi = 3.141592653589793;
+    const double c = cospi(x) * cospi(y) * exp(-t);
+    return -(4.0 * pi * P.nu + 1.0) * c + 3.0 * c / P.rho;
+  }
+  if (P.mms == 4) return 4.0 * P.nu * (x + y) + x + y + 1.0 - 3.0 * (x * x + y * y + 1.0) / P.rho;
+  return 0.0;
+}
+
+// g_T = -P_tau(T n_c) - (alpha nu / sqrt(k_F)) P_tau(u + k_F/mu grad p_F) on z = 1 (x, y)
+__device__ __forceinline__ void mms3_gT(const Phys& P, double x, double y, double t, double* g) {
+  const double kF = P.k[0], c = P.alpha * P.nu / sqrt(kF);
+  if (P.mms == 2) {
+    const double pi = 3.141592653589793;
+    double sx, cx, sy, cy;
+    sincospi(x, &sx, &cx);
+    sincospi(y, &sy, &cy);
+    const double s = c * exp(-t) * (1.0 - 3.0 * pi * kF / P.mu);
+    g[0] = s * sx * cy;
+    g[1] = s * cx * sy;
+  } else if (P.mms == 4) {
+    g[0] = -2.0 * P.nu - c * (x * x + 6.0 * x * kF / P.mu);
+    g[1] = -2.0 * P.nu - c * (y * y + 6.0 * y * kF / P.mu);
+  } else {
+    g[0] = g[1] = 0.0;
+  }
+}
+
+// g_F = u.n_c - k_F/mu dp_F/dz, g_f = -k_f/mu dp_f/dz, g_m = -k_m/mu dp_m/dz on z = 1
+__device__ __forceinline__ double mms3_gd(const Phys& P, int fld, double x, double y, double t) {
+  (void)t;
+  if (P.mms == 4) {
+    if (fld == 0) return 2.0 * (x + y) - 6.0 * P.k[0] / P.mu;
+    if (fld == 1) return -4.0 * P.k[1] / P.mu;
+    return -2.0 * P.k[2] / P.mu;
+  }
+  return 0.0;   // mms 2: all three vanish on z = 1
 }
 
 }  // namespace tpns

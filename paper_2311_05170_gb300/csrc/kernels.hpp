@@ -108,17 +108,25 @@ struct AsmArgs {
   const int32_t* gnode;    // per local node (n_off)
   const int8_t* nkind;
   const int32_t* gam_src;
-  const int32_t* node_dof; // 2 per local node
+  const int32_t* node_dof; // dim per local node
   const int32_t* vloc;     // per local vertex (v_off)
   const int32_t* vert_dof;
-  const double* ref;       // reference tables (RefTables, as doubles)
+  const double* ref;       // reference tables (RefTables or RefTables3, as doubles)
   Phys phys;
   const double* tnow;      // device scalar: t_{n+1}
+  int dim;                 // 2: triangles (e6/e3 hold 6/3 per element, geo 11 doubles);
+                           // 3: tetrahedra (10/4 per element, geo 22 doubles)
 };
 cudaError_t launch_oseen_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Ke, double* Re,
                               cudaStream_t st, const int* skip);
 cudaError_t launch_darcy_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Re,
                               double* Ke, cudaStream_t st);
+// 3D (kernels_assemble3d.cu): element matrices 34 x 34 (Oseen; Re 34 per element) and
+// 3 fields x 10 x 10 (Darcy; Re 3 x 10 per element)
+cudaError_t launch_oseen_elem3(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Ke, double* Re,
+                               cudaStream_t st, const int* skip);
+cudaError_t launch_darcy_elem3(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Re, double* Ke,
+                               cudaStream_t st);
 cudaError_t launch_seg_reduce(const int32_t* tgt, const int32_t* src, int64_t nlanes,
                               const double* in, double* out, cudaStream_t st, const int* skip);
 // write e^{n+1} (all local nodes) from the unknowns x
@@ -130,7 +138,7 @@ cudaError_t launch_prolong(int n2c, int n1c, int n2p, const int32_t* pc2i, const
                            const double* pp2w, const double* uc_new, const double* uc_old,
                            const double* pc_new, const double* pd_new, const double* pd_old,
                            int64_t nnpH, double* FW1, double* FW0, double* FP1, double* FPD1,
-                           double* FPD0, int64_t nnp, cudaStream_t st);
+                           double* FPD0, int64_t nnp, cudaStream_t st, int dim = 2);
 struct GlueArgs {
   const ProbDev* fluid;
   const ProbDev* porous;
@@ -140,6 +148,7 @@ struct GlueArgs {
   const double *FW1, *FP1, *FPD1;
   double *out_u, *out_p, *out_pd;
   int nnc, nvc, nnp;
+  int dim;          // velocity components per node
   int add_coarse;   // 1: add the coarse interpolant (one rank of a split simulation, or the whole)
 };
 cudaError_t launch_glue(const GlueArgs& g, cudaStream_t st);

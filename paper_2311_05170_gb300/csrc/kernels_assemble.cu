@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(128) oseen_elem_kernel(AsmArgs A, int64_t e_be
 
 cudaError_t launch_oseen_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Ke, double* Re,
                               cudaStream_t st, const int* skip) {
+  if (a.dim == 3) return launch_oseen_elem3(a, e_begin, ne, Ke, Re, st, skip);
   if (ne <= 0) return cudaSuccess;
   int blocks = (int)((ne + 7) / 8);
   count_launches(1);
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(128) darcy_elem_kernel(AsmArgs A, int64_t e_be
 
 cudaError_t launch_darcy_elem(const AsmArgs& a, int64_t e_begin, int64_t ne, double* Re, double* Ke,
                               cudaStream_t st) {
+  if (a.dim == 3) return launch_darcy_elem3(a, e_begin, ne, Re, Ke, st);
   if (ne <= 0) return cudaSuccess;
   int blocks = (int)((ne * 3 + 127) / 128);
   count_launches(1);
@@ -413,30 +415,33 @@ __global__ void state_kernel(AsmArgs A, const int32_t* __restrict__ nprob, const
   const int kind = A.nkind[ln];
   const double t = *A.tnow;
   const Phys& Ph = A.phys;
+  const int D = P.dim;
   if (P.kind == 0) {
-    double ub[2] = {0.0, 0.0};
+    double ub[3] = {0.0, 0.0, 0.0};
     if (kind == 1) {
-      mms_u(Ph, P.XY[2 * (int64_t)g], P.XY[2 * (int64_t)g + 1], t, ub);
-      ub[0] -= P.W1[2 * (int64_t)g];
-      ub[1] -= P.W1[2 * (int64_t)g + 1];
+      if (D == 3) mms3_u(Ph, P.XY + 3 * (int64_t)g, t, ub);
+      else mms_u(Ph, P.XY[2 * (int64_t)g], P.XY[2 * (int64_t)g + 1], t, ub);
+      for (int c = 0; c < D; ++c) ub[c] -= P.W1[(int64_t)D * g + c];
     }
-    for (int c = 0; c < 2; ++c) {
-      const int d = A.node_dof[2 * ln + c];
-      P.EOUT[2 * l + c] = d >= 0 ? x[P.x_off + d] : ub[c];
+    for (int c = 0; c < D; ++c) {
+      const int d = A.node_dof[(int64_t)D * ln + c];
+      P.EOUT[(int64_t)D * l + c] = d >= 0 ? x[P.x_off + d] : ub[c];
     }
     const int v = nvidx[ln];
     if (v >= 0) {
       const int d = A.vert_dof[P.v_off + v];
-      P.EOUT[2 * P.nn + v] = d >= 0 ? x[P.x_off + d] : 0.0;
+      P.EOUT[(int64_t)D * P.nn + v] = d >= 0 ? x[P.x_off + d] : 0.0;
     }
   } else {
-    const int d = A.node_dof[2 * ln];
+    const int d = A.node_dof[(int64_t)D * ln];
     for (int f = 0; f < 3; ++f) {
       double val;
       if (d >= 0) {
         val = x[P.x_off + (int64_t)f * P.n + d];
       } else if (kind == 1) {
-        val = mms_pd(Ph, f, P.XY[2 * (int64_t)g], P.XY[2 * (int64_t)g + 1], t) - P.W1[f * P.fstride + g];
+        const double pd = D == 3 ? mms3_pd(Ph, f, P.XY + 3 * (int64_t)g, t)
+                                 : mms_pd(Ph, f, P.XY[2 * (int64_t)g], P.XY[2 * (int64_t)g + 1], t);
+        val = pd - P.W1[f * P.fstride + g];
       } else {
         val = 0.0;
       }
@@ -463,32 +468,35 @@ __global__ void prolong_kernel(int n2c, int n1c, int n2p, const int32_t* __restr
                                const double* __restrict__ pd_new, const double* __restrict__ pd_old,
                                int64_t nnpH, double* __restrict__ FW1, double* __restrict__ FW0,
                                double* __restrict__ FP1, double* __restrict__ FPD1,
-                               double* __restrict__ FPD0, int64_t nnp) {
+                               double* __restrict__ FPD0, int64_t nnp, int D) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb2 = D == 3 ? 10 : 6, nb1 = D + 1;
   if (i < n2c) {
-    double a0 = 0, a1 = 0, b0 = 0, b1 = 0;
-    for (int k = 0; k < 6; ++k) {
-      const int c = pc2i[i * 6 + k];
-      const double w = pc2w[i * 6 + k];
-      a0 += w * uc_new[2 * c];
-      a1 += w * uc_new[2 * c + 1];
-      b0 += w * uc_old[2 * c];
-      b1 += w * uc_old[2 * c + 1];
+    double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int k = 0; k < nb2; ++k) {
+      const int c = pc2i[i * nb2 + k];
+      const double w = pc2w[i * nb2 + k];
+      for (int d = 0; d < D; ++d) {
+        a[d] += w * uc_new[(int64_t)D * c + d];
+        b[d] += w * uc_old[(int64_t)D * c + d];
+      }
     }
-    FW1[2 * i] = a0; FW1[2 * i + 1] = a1;
-    FW0[2 * i] = b0; FW0[2 * i + 1] = b1;
+    for (int d = 0; d < D; ++d) {
+      FW1[D * i + d] = a[d];
+      FW0[D * i + d] = b[d];
+    }
   }
   if (i < n1c) {
     double a = 0;
-    for (int k = 0; k < 3; ++k) a += pc1w[i * 3 + k] * pc_new[pc1i[i * 3 + k]];
+    for (int k = 0; k < nb1; ++k) a += pc1w[i * nb1 + k] * pc_new[pc1i[i * nb1 + k]];
     FP1[i] = a;
   }
   if (i < n2p) {
     for (int f = 0; f < 3; ++f) {
       double a = 0, b = 0;
-      for (int k = 0; k < 6; ++k) {
-        const int c = pp2i[i * 6 + k];
-        const double w = pp2w[i * 6 + k];
+      for (int k = 0; k < nb2; ++k) {
+        const int c = pp2i[i * nb2 + k];
+        const double w = pp2w[i * nb2 + k];
         a += w * pd_new[f * nnpH + c];
         b += w * pd_old[f * nnpH + c];
       }
@@ -502,12 +510,12 @@ cudaError_t launch_prolong(int n2c, int n1c, int n2p, const int32_t* pc2i, const
                            const int32_t* pc1i, const double* pc1w, const int32_t* pp2i, const double* pp2w,
                            const double* uc_new, const double* uc_old, const double* pc_new,
                            const double* pd_new, const double* pd_old, int64_t nnpH, double* FW1, double* FW0,
-                           double* FP1, double* FPD1, double* FPD0, int64_t nnp, cudaStream_t st) {
+                           double* FP1, double* FPD1, double* FPD0, int64_t nnp, cudaStream_t st, int dim) {
   int n = n2c > n2p ? n2c : n2p;
   count_launches(1);
   prolong_kernel<<<(n + 255) / 256, 256, 0, st>>>(n2c, n1c, n2p, pc2i, pc2w, pc1i, pc1w, pp2i, pp2w, uc_new,
                                                    uc_old, pc_new, pd_new, pd_old, nnpH, FW1, FW0, FP1, FPD1,
-                                                   FPD0, nnp);
+                                                   FPD0, nnp, dim);
   return cudaGetLastError();
 }
 
@@ -516,22 +524,22 @@ cudaError_t launch_prolong(int n2c, int n1c, int n2p, const int32_t* pc2i, const
 // of closures containing the node), gathered per fine node in a fixed order.
 __global__ void glue_kernel(GlueArgs G) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int D = G.dim;
   if (i < G.nnc) {
-    double u0 = G.add_coarse ? G.FW1[2 * i] : 0.0, u1 = G.add_coarse ? G.FW1[2 * i + 1] : 0.0;
+    double u[3];
+    for (int d = 0; d < D; ++d) u[d] = G.add_coarse ? G.FW1[D * i + d] : 0.0;
     for (int k = G.gc_ptr[i]; k < G.gc_ptr[i + 1]; ++k) {
       const ProbDev& P = G.fluid[G.gc_prob[k]];
       const int l = G.gc_node[k];
-      u0 += G.gc_w[k] * P.EN[2 * l];
-      u1 += G.gc_w[k] * P.EN[2 * l + 1];
+      for (int d = 0; d < D; ++d) u[d] += G.gc_w[k] * P.EN[(int64_t)D * l + d];
     }
-    G.out_u[2 * i] = u0;
-    G.out_u[2 * i + 1] = u1;
+    for (int d = 0; d < D; ++d) G.out_u[D * i + d] = u[d];
   }
   if (i < G.nvc) {
     double p = G.add_coarse ? G.FP1[i] : 0.0;
     for (int k = G.gv_ptr[i]; k < G.gv_ptr[i + 1]; ++k) {
       const ProbDev& P = G.fluid[G.gv_prob[k]];
-      p += G.gv_w[k] * P.EN[2 * P.nn + G.gv_vert[k]];
+      p += G.gv_w[k] * P.EN[(int64_t)D * P.nn + G.gv_vert[k]];
     }
     G.out_p[i] = p;
   }
@@ -565,20 +573,21 @@ __global__ void __launch_bounds__(256) newton_update_kernel(const ProbDev* __res
   const ProbDev P = *prob;
   const double* d = P.EOUT;
   double sd = 0, sx = 0;
+  const int D = P.dim;
   for (int l = threadIdx.x; l < nn; l += blockDim.x) {
     const int g = gnode[P.n_off + l];
-    for (int c = 0; c < 2; ++c) {
-      const double v = u[2 * g + c] + d[2 * l + c];
-      u[2 * g + c] = v;
-      sd += d[2 * l + c] * d[2 * l + c];
+    for (int c = 0; c < D; ++c) {
+      const double v = u[(int64_t)D * g + c] + d[(int64_t)D * l + c];
+      u[(int64_t)D * g + c] = v;
+      sd += d[(int64_t)D * l + c] * d[(int64_t)D * l + c];
       sx += v * v;
     }
   }
   for (int v = threadIdx.x; v < nvl; v += blockDim.x) {
     const int g = gnode[P.n_off + vloc[P.v_off + v]];
-    const double val = p[g] + d[2 * nn + v];
+    const double val = p[g] + d[(int64_t)D * nn + v];
     p[g] = val;
-    sd += d[2 * nn + v] * d[2 * nn + v];
+    sd += d[(int64_t)D * nn + v] * d[(int64_t)D * nn + v];
     sx += val * val;
   }
   __shared__ double red[2][256];

@@ -161,6 +161,7 @@ def descriptors(w):
 
 
 FIELD_IDS = {"ux": 0, "uy": 1, "p": 2, "pF": 3, "pf": 4, "pm": 5}
+FIELD_IDS_3D = {"ux": 0, "uy": 1, "uz": 2, "p": 3, "pF": 4, "pf": 5, "pm": 6}
 
 
 class Solver:
@@ -171,6 +172,7 @@ class Solver:
                  ir_classic_max=0):
         self.lib = load()
         self.w = w
+        self.ids = FIELD_IDS_3D if getattr(w, "dim", 2) == 3 else FIELD_IDS
         md, pr, pd, dd = descriptors(w)
         opt = Options(FACTORS[factor], int(mf_leaf), 1 if cuda_cores else 0, int(mf_ctas), int(rank), int(nranks),
                       int(algorithm), 1 if gmres else 0, int(ir_classic_max))
@@ -197,12 +199,12 @@ class Solver:
 
     def num_dofs(self, field):
         n = C.c_size_t()
-        _check(self.lib, self.ctx, self.lib.tpns_num_dofs(self.ctx, FIELD_IDS.get(field, field), C.byref(n)))
+        _check(self.lib, self.ctx, self.lib.tpns_num_dofs(self.ctx, self.ids.get(field, field), C.byref(n)))
         return n.value
 
     def field(self, field, out=None):
         """Glued global fine field as a NumPy array (host copy)."""
-        fid = FIELD_IDS.get(field, field)
+        fid = self.ids.get(field, field)
         n = self.num_dofs(fid)
         if out is None:
             out = np.empty(n, dtype=np.float64)
@@ -210,11 +212,11 @@ class Solver:
         return out
 
     def field_to_device(self, field, dev_ptr, n):
-        fid = FIELD_IDS.get(field, field)
+        fid = self.ids.get(field, field)
         _check(self.lib, self.ctx, self.lib.tpns_get_field(self.ctx, fid, C.c_void_p(dev_ptr), n, 1))
 
     def fields(self):
-        return {k: self.field(k) for k in FIELD_IDS}
+        return {k: self.field(k) for k in self.ids}
 
     def stats(self):
         s = Stats()
