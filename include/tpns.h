@@ -190,6 +190,9 @@ typedef struct {
                                step then synchronises the stream to check */
   int32_t ir_classic_max;   /* classic refinement passes per step (0 = 12 for low-precision
                                factors, 2 for FP64) */
+  int32_t mf_big_m;         /* multifrontal: fronts of at least this order, and all their
+                               ancestors, are factored by all CTAs together, one height level
+                               of the elimination trees at a time (0 = 768; < 0: never) */
 } tpns_options;
 
 /* Build meshes, subdomains, sparsity, scatter maps and band orderings on the host, upload

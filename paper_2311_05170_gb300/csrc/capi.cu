@@ -11,6 +11,7 @@
 #include <atomic>
 #include <chrono>
 #include <mutex>
+#include <array>
 #include <vector>
 
 #include "kernels.hpp"
@@ -75,6 +76,12 @@ struct tpns_ctx {
   // multifrontal factorisation of the local Oseen systems
   bool mf = false;
   int mf_leaf = 96, mf_tc = 1, mf_m_max = 1, mf_oseen_fronts = 0;
+  // large fronts (factored by all CTAs): order threshold, fronts of the dataflow launch per
+  // group (Oseen, Darcy), and per group the height levels (offset into d_mf_big, count, max p)
+  int mf_big_m = 768;
+  int mf_small[2] = {0, 0};
+  std::vector<std::array<int, 3>> mf_big_levels[2];
+  int32_t* d_mf_big = nullptr;
   int mf_oseen_blocks = 0, mf_blocks = 0;   // pivot blocks of the Oseen fronts / of all fronts
   int64_t* d_mf_dblk = nullptr;
   int rank = 0, nranks = 1;   // split of one simulation over contexts (see tpns_options)
@@ -424,7 +431,7 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
   // per group, in which a front's children always precede it
   std::vector<MFFrontDev> h_fronts;
   std::vector<int64_t> h_dblk;   // pivot-block slots: the Oseen fronts' first, then the Darcy fronts'
-  std::vector<int32_t> h_mrows, h_relmap, h_origk, h_origi;
+  std::vector<int32_t> h_mrows, h_relmap, h_origk, h_origi, h_big;
   std::vector<int64_t> h_colptr;
   if (ctx->mf) {
     ctx->h_mfsys.clear();
@@ -441,7 +448,9 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     // their parents (the order stays topological) and the fronts on the longest remaining
     // chains are taken first.  Estimated cost of a front in microseconds: fixed work plus
     // per-pivot-block work plus the assembly and update traffic.
-    struct Key { int group; double prio; int q, t; };
+    // Large fronts (order >= mf_big_m) and all their ancestors go to the large-front path;
+    // the others (which then have no large descendant) to the dataflow launch.
+    struct Key { int group, big, lvl; double prio; int q, t; };
     std::vector<Key> keys;
     std::vector<std::vector<int>> newid(msys.size());
     for (int q = 0; q < (int)msys.size(); ++q) {
@@ -455,7 +464,15 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
         const double cost = 10.0 + 15.0 * ((F.p + MF_NB - 1) / MF_NB) + 1e-3 * (double)F.m * F.m;
         prio[t] = cost + (F.parent >= 0 ? prio[F.parent] : 0.0);
       }
-      for (int t = 0; t < nf; ++t) keys.push_back({oseen ? 0 : 1, prio[t], q, t});
+      std::vector<int> height(nf, 0);
+      std::vector<char> big(nf, 0);
+      for (int t = 0; t < nf; ++t) {
+        const MFFront& F = M.fronts[t];
+        for (int c = 0; c < F.nchild; ++c) height[t] = std::max(height[t], height[F.child[c]] + 1);
+        if (ctx->mf_big_m > 0 && F.m >= ctx->mf_big_m)
+          for (int u = t; u >= 0 && !big[u]; u = M.fronts[u].parent) big[u] = 1;
+      }
+      for (int t = 0; t < nf; ++t) keys.push_back({oseen ? 0 : 1, big[t], big[t] ? height[t] : 0, prio[t], q, t});
       const SysDev& Sd = ctx->hsys[msys[q].sid];
       MFSysDev D{};
       D.sid = msys[q].sid; D.n = ctx->probs[msys[q].prob]->n; D.x_off = Sd.x_off; D.val_off = Sd.val_off;
@@ -466,12 +483,32 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
       }
     }
     std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
-      return a.group != b.group ? a.group < b.group : a.prio > b.prio;
+      if (a.group != b.group) return a.group < b.group;
+      if (a.big != b.big) return a.big < b.big;
+      if (a.lvl != b.lvl) return a.lvl < b.lvl;
+      return a.prio > b.prio;
     });
     ctx->mf_oseen_fronts = 0;
+    ctx->mf_small[0] = ctx->mf_small[1] = 0;
+    ctx->mf_big_levels[0].clear();
+    ctx->mf_big_levels[1].clear();
+    h_big.clear();
     for (size_t i = 0; i < keys.size(); ++i) {
       newid[keys[i].q][keys[i].t] = (int)i;
-      if (keys[i].group == 0) ctx->mf_oseen_fronts = (int)i + 1;
+      const int g = keys[i].group;
+      if (g == 0) ctx->mf_oseen_fronts = (int)i + 1;
+      if (!keys[i].big) {
+        ctx->mf_small[g] += 1;
+        continue;
+      }
+      auto& lv = ctx->mf_big_levels[g];
+      const int p = ctx->probs[msys[keys[i].q].prob]->mf.fronts[keys[i].t].p;
+      if (lv.empty() || keys[i - 1].lvl != keys[i].lvl || !keys[i - 1].big || keys[i - 1].group != g ||
+          lv.back()[1] >= MF_BIG_LIST)
+        lv.push_back({(int)h_big.size(), 0, 0});
+      lv.back()[1] += 1;
+      lv.back()[2] = std::max(lv.back()[2], p);
+      h_big.push_back((int32_t)i);
     }
     for (const Key& k : keys) {
       const MFFront& F = ctx->probs[msys[k.q].prob]->mf.fronts[k.t];
@@ -714,6 +751,8 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
     TRY(upload(ctx, &d_oi, h_origi));
     ctx->mf_blocks = (int)h_dblk.size();
     if (h_dblk.empty()) h_dblk.push_back(0);
+    if (h_big.empty()) h_big.push_back(0);
+    TRY(upload(ctx, &ctx->d_mf_big, h_big));
     TRY(upload(ctx, &ctx->d_mf_dblk, h_dblk));
     // scheduling words: task counters and finished-CTA counts at 0, epochs from 1 (the flags
     // start at 0, so no flag of a launch is set before the launch sets it)
@@ -1112,7 +1151,9 @@ static tpns_status local_step(tpns_ctx* ctx) {
   T* mfD = reinterpret_cast<T*>(ctx->d_mf_dinv);
   if (ctx->mf) {
     ph_begin(ctx, PH_BAND_LU);
-    CK(launch_mf_factor<T>(ctx->mfl, 0, ctx->mf_oseen_fronts, mfF, mfD, ctx->mf_tc, st));
+    CK(launch_mf_factor<T>(ctx->mfl, 0, ctx->mf_small[0], mfF, mfD, ctx->mf_tc, st));
+    for (const auto& lv : ctx->mf_big_levels[0])
+      CK(launch_mf_big<T>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], mfF, mfD, ctx->mf_tc, st));
     CK(launch_mf_dinv<T>(mfD, ctx->d_mf_dblk, ctx->mf_oseen_blocks, st));
     ph_end(ctx, PH_BAND_LU);
   } else {
@@ -1505,14 +1546,21 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
     // the local Darcy systems: multifrontal LU once (their matrices do not change)
     const int nd = ctx->mfl.nfront - ctx->mf_oseen_fronts;
     const int nb = ctx->mf_blocks - ctx->mf_oseen_blocks;
+    (void)nd;
     if (ctx->prec == TPNS_FP64) {
-      CK(launch_mf_factor<double>(ctx->mfl, ctx->mf_oseen_fronts, nd, reinterpret_cast<double*>(ctx->d_mf_F),
+      CK(launch_mf_factor<double>(ctx->mfl, ctx->mf_oseen_fronts, ctx->mf_small[1], reinterpret_cast<double*>(ctx->d_mf_F),
                                   reinterpret_cast<double*>(ctx->d_mf_dinv), 0, st));
+      for (const auto& lv : ctx->mf_big_levels[1])
+        CK(launch_mf_big<double>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], reinterpret_cast<double*>(ctx->d_mf_F),
+                                 reinterpret_cast<double*>(ctx->d_mf_dinv), 0, st));
       CK(launch_mf_dinv<double>(reinterpret_cast<double*>(ctx->d_mf_dinv), ctx->d_mf_dblk + ctx->mf_oseen_blocks, nb,
                                 st));
     } else {
-      CK(launch_mf_factor<float>(ctx->mfl, ctx->mf_oseen_fronts, nd, reinterpret_cast<float*>(ctx->d_mf_F),
+      CK(launch_mf_factor<float>(ctx->mfl, ctx->mf_oseen_fronts, ctx->mf_small[1], reinterpret_cast<float*>(ctx->d_mf_F),
                                  reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->mf_tc, st));
+      for (const auto& lv : ctx->mf_big_levels[1])
+        CK(launch_mf_big<float>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], reinterpret_cast<float*>(ctx->d_mf_F),
+                                reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->mf_tc, st));
       CK(launch_mf_dinv<float>(reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->d_mf_dblk + ctx->mf_oseen_blocks, nb,
                                st));
     }
@@ -1708,6 +1756,8 @@ static bool read_options(const tpns_options* o, tpns_options& opt) {
   if (opt.refinement < 0 || opt.refinement > 1 || opt.ir_classic_max < 0 || opt.ir_classic_max > 64) return false;
   if (opt.mf_leaf == 0) opt.mf_leaf = 96;
   if (opt.mf_leaf < 8) return false;
+  if (opt.mf_big_m == 0) opt.mf_big_m = 768;
+  if (opt.mf_big_m > 0 && opt.mf_big_m < 128) return false;
   return true;
 }
 
@@ -1778,6 +1828,7 @@ tpns_status tpns_create_ex(const tpns_mesh_desc* mesh, const tpns_params* params
   ctx->dt = dt;
   ctx->mf = opt.local_factor == TPNS_FACTOR_MULTIFRONTAL;
   ctx->mf_leaf = opt.mf_leaf;
+  ctx->mf_big_m = opt.mf_big_m;
   ctx->mf_tc = precision != TPNS_FP64 && !opt.mf_cuda_cores;
   ctx->rank = opt.rank;
   ctx->nranks = opt.nranks;

@@ -231,12 +231,18 @@ __device__ __forceinline__ void put_split(float*, float*, int, const double (&)[
 // One thread per row or column.  With `pk`
 // (FP32 tensor-core path) the first 128 rows and 256 columns also go straight into the
 // packed operand tiles of the first update chunk.
+// The rows / columns handled by a thread are q_first, q_first + q_step, ... (default: this
+// CTA's threads over all of them).
 template <typename T>
 __device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, int ld, int m, int k0, int kb, int k1,
                                       float* pAh = nullptr, float* pAl = nullptr, float* pBh = nullptr,
-                                      float* pBl = nullptr) {
+                                      float* pBl = nullptr, int q_first = -1, int q_step = 0) {
   const int rest = m - k1;
-  for (int q = threadIdx.x; q < 2 * rest; q += blockDim.x) {
+  if (q_step == 0) {
+    q_first = threadIdx.x;
+    q_step = blockDim.x;
+  }
+  for (int q = q_first; q < 2 * rest; q += q_step) {
     const bool row = q < rest;
     const int idx = k1 + (row ? q : q - rest);
     T a[MF_NB];
@@ -615,6 +621,189 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
   finish_launch(A.sched);
 }
 
+// ---------------------------------------------------------------- large fronts
+// Fronts of large order (and all their ancestors) are factored by many CTAs together,
+// level by level of the elimination trees (all fronts of one height at once): a column-
+// parallel assembly, then per 32-column pivot block one launch for the panel (every CTA of a
+// front factors the 32 x 32 pivot block itself and substitutes its share of the L21 rows and
+// U12 columns) and one launch for the trailing update, whose 128 x 128 tiles over all fronts
+// of the level are spread over all CTAs (tensor cores for FP32 fronts, CUDA cores otherwise).
+// Launch order on the stream orders the steps: no CTA waits for another.
+struct MFBigArgs {
+  const MFSysDev* sys;
+  const MFFrontDev* fronts;
+  const int32_t* list;   // fronts of this launch
+  int nlist;
+  const int32_t* relmap;
+  const int64_t* colptr;
+  const int32_t* orig_k;
+  const int32_t* orig_ij;
+  const double* vals;
+  int* status;
+};
+
+// phase 0: zero the front and place its CSR values; phase 1 / 2: add the Schur complement of
+// child 0 / 1 (distinct positions within one child).  Columns are spread over the CTAs of
+// the front (blockIdx.y).
+template <typename T>
+__global__ void __launch_bounds__(MF_THREADS) mf_big_assemble_kernel(MFBigArgs A, T* __restrict__ Fall, int phase) {
+  const MFFrontDev& Fd = A.fronts[A.list[blockIdx.y]];
+  T* F = Fall + Fd.f_off;
+  const int ld = Fd.ld, m = Fd.m;
+  if (phase == 0) {
+    const double* vals = A.vals + A.sys[Fd.sys].val_off;
+    for (int j = blockIdx.x; j < m; j += gridDim.x) {
+      for (int i = threadIdx.x; i < ld; i += blockDim.x) F[(int64_t)j * ld + i] = T(0);
+      __syncthreads();
+      const int64_t b = A.colptr[Fd.colptr_off + j], e = A.colptr[Fd.colptr_off + j + 1];
+      for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) {
+        const int32_t ij = A.orig_ij[q];
+        F[(int64_t)(ij >> 16) * ld + (ij & 0xFFFF)] = (T)vals[A.orig_k[q]];
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  if (phase > Fd.nchild) return;
+  const MFFrontDev& C = A.fronts[phase == 1 ? Fd.child0 : Fd.child1];
+  const int qc = C.m - C.p;
+  const T* src = Fall + C.f_off + (int64_t)C.p * C.ld + C.p;
+  const int32_t* rm = A.relmap + C.relmap_off;
+  for (int jc = blockIdx.x; jc < qc; jc += gridDim.x) {
+    T* dcol = F + (int64_t)rm[jc] * ld;
+    const T* scol = src + (int64_t)jc * C.ld;
+    for (int ic = threadIdx.x; ic < qc; ic += blockDim.x) dcol[rm[ic]] += ldcg(scol + ic);
+  }
+}
+
+// pivot block k0 of every listed front with p > k0: its LU (written by CTA 0 to the block's
+// slot for mf_dinv_kernel) and the substitutions of L21 rows / U12 columns, spread over the
+// CTAs of the front
+template <typename T>
+__global__ void __launch_bounds__(MF_THREADS) mf_big_panel_kernel(MFBigArgs A, T* __restrict__ Fall,
+                                                                  T* __restrict__ dinv, int k0) {
+  __shared__ PanelSmem<T> P;
+  __shared__ int s_flag;
+  const MFFrontDev& Fd = A.fronts[A.list[blockIdx.y]];
+  if (k0 >= Fd.p) return;
+  if (threadIdx.x == 0) s_flag = 0;
+  __syncthreads();
+  T* F = Fall + Fd.f_off;
+  const int ld = Fd.ld;
+  const int kb = min(MF_NB, Fd.p - k0), k1 = k0 + kb;
+  pivot_block<T>(P, F, ld, k0, kb, &s_flag);
+  if (blockIdx.x == 0) {
+    T* dv = dinv + Fd.dinv_off + (int64_t)(k0 / MF_NB) * 2 * MF_NB * MF_NB + MF_NB * MF_NB;
+    for (int q = threadIdx.x; q < MF_NB * MF_NB; q += blockDim.x) dv[q] = P.D[q >> 5][q & 31];
+    if (threadIdx.x == 0 && s_flag) atomicOr(&A.status[A.sys[Fd.sys].sid], s_flag);
+  }
+  if (k1 < Fd.m)
+    panel_lu<T>(P, F, ld, Fd.m, k0, kb, k1, nullptr, nullptr, nullptr, nullptr,
+                blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// trailing update of pivot block k0: the 128 x 128 tiles of F[k1:m, k1:m] of all listed
+// fronts (with p > k0), enumerated front by front, taken round robin by the CTAs
+template <typename T, bool TC>
+__global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs A, T* __restrict__ Fall, int k0) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ int s_pre[MF_BIG_LIST + 1];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    int acc = 0;
+    for (int i = 0; i < A.nlist; ++i) {
+      s_pre[i] = acc;
+      const MFFrontDev& Fd = A.fronts[A.list[i]];
+      if (k0 < Fd.p) {
+        const int k1 = min(k0 + MF_NB, Fd.p);
+        const int nt = (Fd.m - k1 + MF_TILE - 1) / MF_TILE;
+        acc += nt * nt;
+      }
+    }
+    s_pre[A.nlist] = acc;
+    s_flag = 0;
+  }
+  TcSmem& TS = *reinterpret_cast<TcSmem*>(smem_raw);
+  unsigned ph = 0;
+  if constexpr (TC) {
+    if (tid == 0) {
+      mb_init(&TS.bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tm_alloc(&TS.tmem, MF_TMEM_COLS);
+    tc_before();
+  }
+  __syncthreads();
+  if constexpr (TC) tc_after();
+  const int total = s_pre[A.nlist];
+  int fi = 0;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    while (s_pre[fi + 1] <= t) ++fi;
+    const MFFrontDev& Fd = A.fronts[A.list[fi]];
+    T* F = Fall + Fd.f_off;
+    const int ld = Fd.ld, m = Fd.m;
+    const int kb = min(MF_NB, Fd.p - k0), k1 = k0 + kb;
+    const int nt = (m - k1 + MF_TILE - 1) / MF_TILE;
+    const int tl = t - s_pre[fi];
+    const int r0 = k1 + (tl % nt) * MF_TILE, c0 = k1 + (tl / nt) * MF_TILE;
+    if constexpr (TC) {
+      if (s_flag & 2) break;   // a bounded wait gave up: issue no further products
+      const int nr = min(MF_TILE, m - r0), nc = min(MF_CN, m - c0);
+      float* Ff = reinterpret_cast<float*>(F);
+      if (tid < MF_TILE) pack_panel(Ff, ld, k0, kb, r0, nr, true, tid, TS.Ahi, TS.Alo);
+      else if (tid - MF_TILE < MF_CN) pack_panel(Ff, ld, k0, kb, c0, nc, false, tid - MF_TILE, TS.Bhi, TS.Blo);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_before();
+      __syncthreads();
+      tc_after();
+      if (tid == 0) issue_chunk(TS, &TS.bar);
+      if (!mb_wait(&TS.bar, ph) && lane == 0) atomicOr(&s_flag, 2);
+      ph ^= 1u;
+      tc_after();
+      const int q4 = warp & 3, hcol = warp >> 2;
+      const int r = r0 + 32 * q4 + lane;
+      const int cb = c0 + 64 * hcol;
+      if (r0 + 32 * q4 < m && cb < m) {
+        const uint32_t base = TS.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(64 * hcol);
+        const int rr = r < m ? r : m - 1;
+#pragma unroll 1
+        for (int h16 = 0; h16 < 4; ++h16) {
+          const int cb2 = cb + 16 * h16;
+          if (cb2 >= m) break;
+          uint32_t d[16];
+          tm_ld16(base + (uint32_t)(16 * h16), d);
+          float f[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) f[c] = Ff[(int64_t)(cb2 + c < m ? cb2 + c : m - 1) * ld + rr];
+          tm_wait_ld();
+          if (r < m) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              if (cb2 + c < m) Ff[(int64_t)(cb2 + c) * ld + r] = f[c] - __uint_as_float(d[c]);
+          }
+        }
+      }
+      tc_before();
+      __syncthreads();
+      tc_after();
+    } else {
+      T* As = reinterpret_cast<T*>(smem_raw);
+      update_tile_fma<T>(F, ld, m, k0, kb, r0, c0, As, As + MF_NB * (MF_TILE + 4));
+    }
+  }
+  if constexpr (TC) {
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (warp == 0) tm_dealloc(TS.tmem, MF_TMEM_COLS);
+    if (tid == 0 && (s_flag & 2)) {
+      // report the expired wait on the first listed front's system
+      atomicOr(&A.status[A.sys[A.fronts[A.list[0]].sys].sid], 2);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- block inverses
 // For every pivot block in the list (offset of its 2 x 32 x 32 slot): read the factored block
 // (row-major, second half of the slot), write L11^{-1} (unit lower) to the first half and
@@ -888,10 +1077,45 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int max_p, T* F, T* dinv, int tc,
+                          cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  if (nlist > MF_BIG_LIST) return cudaErrorInvalidValue;
+  MFBigArgs A{L.sys, L.fronts, list, nlist, L.relmap, L.colptr, L.orig_k, L.orig_ij, L.vals, L.status};
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // CTAs per front for the column-parallel and row-parallel steps: enough to cover the device
+  const int per = std::max(1, std::min(64, (2 * nsm + nlist - 1) / nlist));
+  for (int phase = 0; phase < 3; ++phase) {
+    count_launches(1);
+    mf_big_assemble_kernel<T><<<dim3(per, nlist), MF_THREADS, 0, st>>>(A, F, phase);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const bool use_tc = tc && sizeof(T) == 4;
+  const size_t smem = use_tc ? sizeof(TcSmem) : (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T);
+  auto ufn = use_tc ? mf_big_update_kernel<T, true> : mf_big_update_kernel<T, false>;
+  e = cudaFuncSetAttribute(ufn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int ugrid = mf_grid((const void*)ufn, smem, L.grid_cap);
+  for (int k0 = 0; k0 < max_p; k0 += MF_NB) {
+    count_launches(2);
+    mf_big_panel_kernel<T><<<dim3(per, nlist), MF_THREADS, 0, st>>>(A, F, dinv, k0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ufn<<<ugrid, MF_THREADS, smem, st>>>(A, F, k0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 #define TPNS_MF_INST(T)                                                                                      \
   template size_t mf_factor_smem<T>(bool);                                                                  \
   template cudaError_t launch_mf_factor<T>(const MFLaunch&, int, int, T*, T*, int, cudaStream_t);          \
   template cudaError_t launch_mf_dinv<T>(T*, const int64_t*, int, cudaStream_t);                            \
+  template cudaError_t launch_mf_big<T>(const MFLaunch&, const int32_t*, int, int, T*, T*, int, cudaStream_t); \
   template cudaError_t launch_mf_solve<T>(const MFLaunch&, const T*, const T*, const double*, double*, int, \
                                           const int*, T*, T*, T*, int, cudaStream_t);
 TPNS_MF_INST(float)

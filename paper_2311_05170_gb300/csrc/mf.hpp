@@ -19,6 +19,7 @@ namespace tpns {
 constexpr int MF_NB = 32;      // pivot block (panel width) of the front factorisation
 constexpr int MF_TILE = 128;   // rows / columns of one trailing-update tile
 constexpr int MF_PACK_TILE = MF_TILE * MF_NB;   // elements of one packed operand tile
+constexpr int MF_BIG_LIST = 1024;  // fronts per launch of the large-front path at most
 
 struct MFFront {
   int m = 0, p = 0;              // front order, pivots (own unknowns)

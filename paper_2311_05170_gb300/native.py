@@ -38,7 +38,7 @@ class DataDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("local_factor", C.c_int32), ("mf_leaf", C.c_int32), ("mf_cuda_cores", C.c_int32),
                 ("mf_ctas", C.c_int32), ("rank", C.c_int32), ("nranks", C.c_int32), ("algorithm", C.c_int32),
-                ("refinement", C.c_int32), ("ir_classic_max", C.c_int32)]
+                ("refinement", C.c_int32), ("ir_classic_max", C.c_int32), ("mf_big_m", C.c_int32)]
 
 
 FACTORS = {"mf": 0, "band": 1}
@@ -169,13 +169,13 @@ class Solver:
 
     def __init__(self, w, precision="fp64", hbm_budget_bytes=0, stream=None, host_only=False, factor="mf",
                  mf_leaf=0, cuda_cores=False, mf_ctas=0, rank=0, nranks=0, algorithm=3, gmres=False,
-                 ir_classic_max=0):
+                 ir_classic_max=0, mf_big_m=0):
         self.lib = load()
         self.w = w
         self.ids = FIELD_IDS_3D if getattr(w, "dim", 2) == 3 else FIELD_IDS
         md, pr, pd, dd = descriptors(w)
         opt = Options(FACTORS[factor], int(mf_leaf), 1 if cuda_cores else 0, int(mf_ctas), int(rank), int(nranks),
-                      int(algorithm), 1 if gmres else 0, int(ir_classic_max))
+                      int(algorithm), 1 if gmres else 0, int(ir_classic_max), int(mf_big_m))
         ctx = C.c_void_p()
         if host_only:
             _check(self.lib, None, self.lib.tpns_layout_create_ex(C.byref(md), C.byref(pd), C.byref(opt),

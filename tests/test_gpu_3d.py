@@ -119,3 +119,31 @@ def test_3d_deterministic_and_graph_equals_eager(native):
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
         assert np.array_equal(out[0][k], out[2][k]), k
+
+
+@pytest.mark.parametrize("dim,prec", [(2, "fp32"), (2, "fp64"), (3, "fp32"), (3, "fp64")])
+def test_large_front_path_bitwise_equal(native, dim, prec):
+    """Fronts factored by all CTAs together (forced down to order 128) give the same bits as
+    the one-CTA dataflow path: the same operations in the same order."""
+    w = W.config_3d_small(n_coarse=2, r=3, nsub=(1, 1, 1), overlap=1, nsteps=2) if dim == 3 else \
+        W.config_graded(nsteps=2)
+    out = []
+    for big in (-1, 128):
+        s = native.Solver(w, precision=prec, mf_big_m=big)
+        s.step(2)
+        out.append(s.fields())
+        s.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_large_front_path_parity_3d(native):
+    w = W.config_3d_small(n_coarse=2, r=4, nsub=(1, 1, 1), overlap=1, nsteps=2)
+    o = TwoGridOracle3D(w)
+    o.run(2)
+    s = native.Solver(w, precision="fp32", mf_big_m=256)
+    s.step(2)
+    f = s.fields()
+    s.close()
+    for k in f:
+        assert rel(f[k], o.fine[k]) <= TOL["fp32"], (k, rel(f[k], o.fine[k]))
