@@ -8,7 +8,8 @@ dofs, 16 Oseen systems (3.3k-8.3k unknowns) and 48 Darcy systems per step.
 Metric: fine dof-steps per second of the hot path, mixed precision (FP32 multifrontal factors
 with tensor-core trailing updates, FP32 solves, FP64 assembly and refinement residuals), valid
 only if every field is within relative L2 1e-8 of the FP64 GPU path on the same steps.  One
-JSON line on rank 0.
+JSON line on rank 0.  The line also carries the same measurement on the 3D workload (H = 1/4,
+h = 1/24, 2 x 2 x 2 subdomains per region, 721,519 fine dofs) under "workload_3d".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -40,11 +41,15 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-sample-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--steps-3d", type=int, default=3,
+                    help="timed steps of the 3D workload (0: skip it)")
     ap.add_argument("--serving-requests", type=int, default=16)
     ap.add_argument("--serving-steps", type=int, default=10)
     ap.add_argument("--profile", action="store_true",
                     help="only create the mixed-precision context and run W + K hot-path steps (for ncu); "
                          "prints no bench line")
+    ap.add_argument("--profile-3d", action="store_true",
+                    help="the same on the 3D workload (721,519 fine dofs)")
     return ap.parse_args()
 
 
@@ -270,6 +275,17 @@ def main():
     w = W.config_graded(nsteps=Wm + K)
     stream = torch.cuda.Stream()
     handle = stream.cuda_stream
+    if args.profile_3d:
+        w3 = W.config_3d(nsteps=Wm + K)
+        s = Solver(w3, precision=args.precision, stream=handle)
+        s.coarse_precompute(Wm + K)
+        s.local_step(Wm)
+        torch.cuda.synchronize()
+        s.local_step(K)
+        torch.cuda.synchronize()
+        s.close()
+        print("profile run: %d + %d hot-path steps of the 3D workload (H = 1/4, h = 1/24)" % (Wm, K))
+        return
     if args.profile:
         s = Solver(w, precision=args.precision, stream=handle)
         s.coarse_precompute(Wm + K)
@@ -429,6 +445,75 @@ def main():
     e.close()
     e2e_val = ndofs * K * world / e2e_s
     full_ms = steps_s * 1e3 / K
+    # ---------------------------------------------------------------- 3D workload
+    # H = 1/4, h = 1/24, 2 x 2 x 2 subdomains per region, overlap 2 fine layers, 3D trigonometric
+    # manufactured solution: 721,519 fine dofs, 8 Oseen systems of about 63k unknowns (fronts up
+    # to order 3,654, 1.43e12 factorisation flops per step) and 24 Darcy systems.  Same timing
+    # rules as the 2D line: W warm-up steps, K3 steps replayed from the CUDA graph on coarse
+    # states precomputed in HBM, CUDA events on the library's stream; FP64 GPU path on the
+    # same steps for the validity check.
+    w3d = None
+    if args.steps_3d > 0:
+        w3 = W.config_3d(nsteps=Wm + 2 * args.steps_3d)
+        K3 = args.steps_3d
+
+        def timed_3d(prec, with_phases=False):
+            s3 = Solver(w3, precision=prec, stream=handle)
+            s3.coarse_precompute(Wm + 2 * K3)
+            s3.local_step(Wm)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            s3.local_step(K3)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms3 = max_over_ranks(a0.elapsed_time(a1), dist is not None, device="cuda")
+            f3 = s3.fields()
+            ph3 = None
+            if with_phases:
+                s3.set_timing(True)
+                sb = 0.0
+                for _ in range(K3):
+                    s3.local_step(1)
+                    sb += s3.stats()["last_solve_bytes"]
+                torch.cuda.synchronize()
+                ph3 = s3.timings()
+                ph3["_solve_bytes"] = sb
+                s3.set_timing(False)
+            st3 = s3.stats()
+            s3.close()
+            return ms3, f3, ph3, st3
+
+        m64, g64, _, _ = timed_3d("fp64")
+        m32, g32, ph3, st3 = timed_3d(args.precision, with_phases=True)
+        rel3 = {k: float(np.linalg.norm(g32[k] - g64[k]) / np.linalg.norm(g64[k])) for k in g32}
+        nd3 = ndofs_of(st3)
+        v3 = nd3 * K3 * world / (m32 / 1e3)
+        v64 = nd3 * K3 * world / (m64 / 1e3)
+        p3 = {k: v[0] / K3 for k, v in ph3.items() if not k.startswith("_")}
+        f_ms = p3["band_lu"]
+        f_tf = st3["band_lu_flops"] / (f_ms / 1e3) / 1e12
+        sb3 = ph3["_solve_bytes"] / K3
+        w3d = {
+            "workload": "3d_H4_h24_2x2x2sub_overlap2h_dt0.01 (%s fine dofs)" % format(nd3, ","),
+            "value": v3 if max(rel3.values()) <= 1e-8 else None, "unit": UNIT, "ms_per_step": m32 / K3,
+            "steps": K3, "warmup": Wm, "valid": max(rel3.values()) <= 1e-8, "relL2_vs_fp64_gpu": rel3,
+            "fp64_gpu": {"value": v64, "ms_per_step": m64 / K3}, "speedup_vs_fp64_gpu": v3 / v64,
+            "phases_ms_per_step": p3,
+            "mf_factor": {"bound": "tensor", "achieved": f_tf, "peak": tf32_peak, "unit": "TFLOP/s",
+                          "frac": f_tf / tf32_peak, "ms_per_step": f_ms, "flops_per_step": st3["band_lu_flops"],
+                          "fronts": st3["mf_fronts"],
+                          "note": "fronts of order >= 768 and their ancestors factored by all CTAs per tree level"},
+            "solves": {**hbm(sb3, p3["solve"])},
+            "ir": {"iters_max": st3["last_ir_iters_max"], "relres_max": st3["last_ir_relres_max"]},
+            "config": {"oseen_unknowns": st3["oseen_unknowns"], "oseen_nnz": st3["oseen_nnz"],
+                       "oseen_elements": st3["oseen_elements"], "factor_entries": st3["factor_entries"],
+                       "device_bytes": st3["device_bytes"], "create_ms": st3["create_ms"],
+                       "l2": "inputs larger than L2 (fronts %.1f GB)" % (st3["factor_entries"] * tsz / 1e9)},
+        }
     # ---------------------------------------------------------------- serving (bounded sample)
     serving = None
     if args.serving_requests > 0:
@@ -516,6 +601,7 @@ def main():
                     "full_step_what": "one tpns_step (coarse solve + hot path) plus the read-back of all fields, "
                                       "create excluded"},
             "gpu_launches": launches,
+            "workload_3d": w3d,
             "serving": serving,
             "clocks": clocks,
             "cpu_baseline": cpu,
