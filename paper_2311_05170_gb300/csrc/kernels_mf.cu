@@ -847,6 +847,23 @@ __global__ void __launch_bounds__(256) mf_dinv_kernel(T* __restrict__ dinv, cons
 }
 
 // ---------------------------------------------------------------- solves
+// 32 contiguous values of a front column (16-byte aligned: ld and the front offsets are
+// multiples of 4 elements and k0 of 32)
+__device__ __forceinline__ void load_col32(const float* p, float (&v)[MF_NB]) {
+#pragma unroll
+  for (int q = 0; q < MF_NB / 4; ++q) {
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(p) + q);
+    v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void load_col32(const double* p, double (&v)[MF_NB]) {
+#pragma unroll
+  for (int q = 0; q < MF_NB / 2; ++q) {
+    const double2 t = __ldcg(reinterpret_cast<const double2*>(p) + q);
+    v[2 * q] = t.x; v[2 * q + 1] = t.y;
+  }
+}
+
 struct MFSolveArgs {
   const MFSysDev* sys;
   int nsys;
@@ -870,6 +887,7 @@ __global__ void __launch_bounds__(MF_STHREADS, 4)
   __shared__ T red[MF_STHREADS / 32][MF_NB];
   __shared__ T blk[MF_NB];
   __shared__ T Dinv[MF_NB * MF_NB];
+  __shared__ T part[MF_NB][MF_STHREADS + 1];   // backward: per-row partial sums of the threads
   __shared__ int s_task, s_any;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int epoch = ld_acquire(&A.sched[2]);
@@ -960,22 +978,40 @@ __global__ void __launch_bounds__(MF_STHREADS, 4)
         const int k0 = kk * MF_NB;
         const int kb = min(MF_NB, p - k0);
         const int k1 = k0 + kb;
-        T s = T(0);
         const T* Ui = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB + MF_NB * MF_NB;
 #pragma unroll
         for (int u = 0; u < MF_NB * MF_NB / MF_STHREADS; ++u) Dinv[tid + u * MF_STHREADS] = ldcg(Ui + tid + u * MF_STHREADS);
-        if (lane < kb) {
-          int j = k1 + warp;
-          for (; j + 3 * (MF_STHREADS / 32) < m; j += 4 * (MF_STHREADS / 32)) {
-            T f4[4];
+        // U12 (rows k0 .. k1) times w[k1:m]: thread t takes the columns k1 + t, k1 + t + 128, ...
+        // (each 32 contiguous values, vector loads, many in flight) and keeps one partial sum
+        // per row; the partials are then added over the threads in a fixed order
+        {
+          T acc[MF_NB];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) f4[u] = ldcg(F + (int64_t)(j + u * (MF_STHREADS / 32)) * Fd.ld + k0 + lane);
+          for (int c = 0; c < MF_NB; ++c) acc[c] = T(0);
+          const bool vec = k0 + MF_NB <= Fd.ld;   // the 32 rows stay inside every column
+          for (int j = k1 + tid; j < m; j += MF_STHREADS) {
+            const T* col = F + (int64_t)j * Fd.ld + k0;
+            T v[MF_NB];
+            if (vec) {
+              load_col32(col, v);
+            } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s += f4[u] * w[j + u * (MF_STHREADS / 32)];
+              for (int c = 0; c < MF_NB; ++c) v[c] = ldcg(col + (c < kb ? c : 0));
+            }
+            const T wj = w[j];
+#pragma unroll
+            for (int c = 0; c < MF_NB; ++c) acc[c] += v[c] * wj;
           }
-          for (; j < m; j += MF_STHREADS / 32) s += ldcg(F + (int64_t)j * Fd.ld + k0 + lane) * w[j];
+#pragma unroll
+          for (int c = 0; c < MF_NB; ++c) part[c][tid] = c < kb ? acc[c] : T(0);
         }
-        red[warp][lane] = s;
+        __syncthreads();
+        {
+          T s = T(0);
+#pragma unroll 8
+          for (int q = 0; q < 32; ++q) s += part[lane][32 * warp + q];
+          red[warp][lane] = s;
+        }
         __syncthreads();
         if (warp == 0) {
           T z = T(0);
