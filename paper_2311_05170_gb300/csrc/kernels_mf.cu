@@ -44,6 +44,7 @@ namespace {
 
 constexpr int MF_THREADS = 256;           // factorisation CTA
 constexpr int MF_STHREADS = 128;          // solve CTA: fronts are small, more of them in flight per SM
+constexpr int MF_SOLVE_WIDE_M = 1024;     // solves with fronts of at least this order use 512-thread CTAs
 constexpr int MF_WAIT_LIMIT = 1 << 22;
 constexpr int MF_CN = MF_TILE;             // columns of one tensor-core update chunk (rows: MF_TILE)
 constexpr int MF_TMEM_COLS = MF_CN;        // one 128 x 128 FP32 accumulator
@@ -877,17 +878,16 @@ struct MFSolveArgs {
   int* bflag;   // backward done, per front
 };
 
-template <typename T>
-__global__ void __launch_bounds__(MF_STHREADS, 4)
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
     mf_solve_kernel(MFSolveArgs A, const T* __restrict__ Fall, const T* __restrict__ dinv,
                     const double* __restrict__ rhs, double* __restrict__ x, int accumulate, T* __restrict__ yv,
                     T* __restrict__ dvec, T* __restrict__ upd) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   T* w = reinterpret_cast<T*>(smem_raw);
-  __shared__ T red[MF_STHREADS / 32][MF_NB];
+  __shared__ T red[NT / 32][MF_NB];
   __shared__ T blk[MF_NB];
   __shared__ T Dinv[MF_NB * MF_NB];
-  __shared__ T part[MF_NB][MF_STHREADS + 1];   // backward: per-row partial sums of the threads
   __shared__ int s_task, s_any;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int epoch = ld_acquire(&A.sched[2]);
@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(MF_STHREADS, 4)
         const int kb = min(MF_NB, p - k0);
         const T* Li = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB;
 #pragma unroll
-        for (int u = 0; u < MF_NB * MF_NB / MF_STHREADS; ++u) Dinv[tid + u * MF_STHREADS] = ldcg(Li + tid + u * MF_STHREADS);
+        for (int u = 0; u < MF_NB * MF_NB / NT; ++u) Dinv[tid + u * NT] = ldcg(Li + tid + u * NT);
         __syncthreads();
         if (warp == 0) {
           T s = T(0);
@@ -980,7 +980,7 @@ __global__ void __launch_bounds__(MF_STHREADS, 4)
         const int k1 = k0 + kb;
         const T* Ui = dinv + Fd.dinv_off + (int64_t)kk * 2 * MF_NB * MF_NB + MF_NB * MF_NB;
 #pragma unroll
-        for (int u = 0; u < MF_NB * MF_NB / MF_STHREADS; ++u) Dinv[tid + u * MF_STHREADS] = ldcg(Ui + tid + u * MF_STHREADS);
+        for (int u = 0; u < MF_NB * MF_NB / NT; ++u) Dinv[tid + u * NT] = ldcg(Ui + tid + u * NT);
         // U12 (rows k0 .. k1) times w[k1:m]: thread t takes the columns k1 + t, k1 + t + 128, ...
         // (each 32 contiguous values, vector loads, many in flight) and keeps one partial sum
         // per row; the partials are then added over the threads in a fixed order
@@ -989,7 +989,7 @@ __global__ void __launch_bounds__(MF_STHREADS, 4)
 #pragma unroll
           for (int c = 0; c < MF_NB; ++c) acc[c] = T(0);
           const bool vec = k0 + MF_NB <= Fd.ld;   // the 32 rows stay inside every column
-          for (int j = k1 + tid; j < m; j += MF_STHREADS) {
+          for (int j = k1 + tid; j < m; j += NT) {
             const T* col = F + (int64_t)j * Fd.ld + k0;
             T v[MF_NB];
             if (vec) {
@@ -1003,14 +1003,21 @@ __global__ void __launch_bounds__(MF_STHREADS, 4)
             for (int c = 0; c < MF_NB; ++c) acc[c] += v[c] * wj;
           }
 #pragma unroll
-          for (int c = 0; c < MF_NB; ++c) part[c][tid] = c < kb ? acc[c] : T(0);
-        }
-        __syncthreads();
-        {
-          T s = T(0);
-#pragma unroll 8
-          for (int q = 0; q < 32; ++q) s += part[lane][32 * warp + q];
-          red[warp][lane] = s;
+          for (int c = 0; c < MF_NB; ++c)
+            if (c >= kb) acc[c] = T(0);
+          // transpose-reduce over the warp: after the five halving rounds lane l holds the
+          // warp's sum for row l (fixed order)
+#pragma unroll
+          for (int k = 16; k >= 1; k >>= 1) {
+            const bool upper = (lane & k) != 0;
+#pragma unroll
+            for (int i = 0; i < k; ++i) {
+              const T send = upper ? acc[i] : acc[i + k];
+              const T keep = upper ? acc[i + k] : acc[i];
+              acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+            }
+          }
+          red[warp][lane] = acc[0];
         }
         __syncthreads();
         if (warp == 0) {
@@ -1018,7 +1025,7 @@ __global__ void __launch_bounds__(MF_STHREADS, 4)
           if (lane < kb) {
             z = w[k0 + lane];
 #pragma unroll
-            for (int q = 0; q < MF_STHREADS / 32; ++q) z -= red[q][lane];
+            for (int q = 0; q < NT / 32; ++q) z -= red[q][lane];
           }
           blk[lane] = z;
           __syncwarp();
@@ -1105,11 +1112,15 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
   MFSolveArgs A{L.sys, L.nsys, L.fronts, L.nfront, L.rows, L.relmap, done, L.sched + 4, L.sflag, L.sflag + L.nfront};
   const size_t smem = (size_t)(m_max + 4) * sizeof(T);
   count_launches(1);
-  auto fn = mf_solve_kernel<T>;
+  // large fronts: 512 threads per CTA keep more of a front's loads in flight; small fronts:
+  // 128, more fronts in flight per SM
+  const bool wide = m_max >= MF_SOLVE_WIDE_M;
+  auto fn = wide ? mf_solve_kernel<T, 512> : mf_solve_kernel<T, MF_STHREADS>;
+  const int nt = wide ? 512 : MF_STHREADS;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap, MF_STHREADS), 2 * L.nfront);
-  fn<<<grid, MF_STHREADS, smem, st>>>(A, F, dinv, r, x, accumulate, yv, dv, upd);
+  const int grid = std::min(mf_grid((const void*)fn, smem, L.grid_cap, nt), 2 * L.nfront);
+  fn<<<grid, nt, smem, st>>>(A, F, dinv, r, x, accumulate, yv, dv, upd);
   return cudaGetLastError();
 }
 
