@@ -759,29 +759,29 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
       __syncthreads();
       tc_after();
       if (tid == 0) issue_chunk(TS, &TS.bar);
-      if (!mb_wait(&TS.bar, ph) && lane == 0) atomicOr(&s_flag, 2);
-      ph ^= 1u;
-      tc_after();
+      // the tile's current values are loaded while the products run (clamped addresses)
       const int q4 = warp & 3, hcol = warp >> 2;
       const int r = r0 + 32 * q4 + lane;
       const int cb = c0 + 64 * hcol;
+      const int rr = r < m ? r : m - 1;
+      float f[64];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) f[c] = Ff[(int64_t)(cb + c < m ? cb + c : m - 1) * ld + rr];
+      if (!mb_wait(&TS.bar, ph) && lane == 0) atomicOr(&s_flag, 2);
+      ph ^= 1u;
+      tc_after();
       if (r0 + 32 * q4 < m && cb < m) {
         const uint32_t base = TS.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(64 * hcol);
-        const int rr = r < m ? r : m - 1;
-#pragma unroll 1
+#pragma unroll
         for (int h16 = 0; h16 < 4; ++h16) {
           const int cb2 = cb + 16 * h16;
-          if (cb2 >= m) break;
           uint32_t d[16];
           tm_ld16(base + (uint32_t)(16 * h16), d);
-          float f[16];
-#pragma unroll
-          for (int c = 0; c < 16; ++c) f[c] = Ff[(int64_t)(cb2 + c < m ? cb2 + c : m - 1) * ld + rr];
           tm_wait_ld();
           if (r < m) {
 #pragma unroll
             for (int c = 0; c < 16; ++c)
-              if (cb2 + c < m) Ff[(int64_t)(cb2 + c) * ld + r] = f[c] - __uint_as_float(d[c]);
+              if (cb2 + c < m) Ff[(int64_t)(cb2 + c) * ld + r] = f[16 * h16 + c] - __uint_as_float(d[c]);
           }
         }
       }
