@@ -50,6 +50,8 @@ def parse():
                          "prints no bench line")
     ap.add_argument("--profile-3d", action="store_true",
                     help="the same on the 3D workload (721,519 fine dofs)")
+    ap.add_argument("--profile-3d-small", action="store_true",
+                    help="the same on one 3D subdomain per region (H = 1/2, h = 1/12), for detailed captures")
     return ap.parse_args()
 
 
@@ -275,8 +277,9 @@ def main():
     w = W.config_graded(nsteps=Wm + K)
     stream = torch.cuda.Stream()
     handle = stream.cuda_stream
-    if args.profile_3d:
-        w3 = W.config_3d(nsteps=Wm + K)
+    if args.profile_3d or args.profile_3d_small:
+        w3 = W.config_3d(nsteps=Wm + K) if args.profile_3d else \
+            W.config_3d_small(n_coarse=2, r=6, nsub=(1, 1, 1), overlap=1, nsteps=Wm + K)
         s = Solver(w3, precision=args.precision, stream=handle)
         s.coarse_precompute(Wm + K)
         s.local_step(Wm)
@@ -284,7 +287,7 @@ def main():
         s.local_step(K)
         torch.cuda.synchronize()
         s.close()
-        print("profile run: %d + %d hot-path steps of the 3D workload (H = 1/4, h = 1/24)" % (Wm, K))
+        print("profile run: %d + %d hot-path steps of %s" % (Wm, K, w3.name))
         return
     if args.profile:
         s = Solver(w, precision=args.precision, stream=handle)
