@@ -1319,9 +1319,14 @@ static tpns_status read_stats(tpns_ctx* ctx) {
   ctx->stats.last_ir_relres_max = mr;
   ctx->stats.last_newton_iters = nit;
   for (int s = 0; s < ctx->nsys; ++s)
-    if (stt[s]) {
+    if (stt[s] & 1) {
       ctx->err = "zero or non-finite pivot in system " + std::to_string(s);
       return TPNS_EBREAKDOWN;
+    }
+  for (int s = 0; s < ctx->nsys; ++s)
+    if (stt[s]) {
+      ctx->err = "a bounded wait of a device kernel gave up (system " + std::to_string(s) + ")";
+      return TPNS_ETIMEOUT;
     }
   if (!(mr <= 1e-9)) {
     ctx->err = "iterative refinement stopped at relative residual " + std::to_string(mr);
@@ -1596,9 +1601,14 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
   std::vector<int> stt(ctx->nsys);
   CK(cudaMemcpy(stt.data(), ctx->d_status, ctx->nsys * sizeof(int), cudaMemcpyDeviceToHost));
   for (int s = 0; s < ctx->nsys; ++s)
-    if (stt[s]) {
-      ctx->err = "Darcy Cholesky: non-positive pivot in system " + std::to_string(s);
+    if (stt[s] & 1) {
+      ctx->err = "Darcy factorisation: zero, non-positive or non-finite pivot in system " + std::to_string(s);
       return TPNS_EBREAKDOWN;
+    }
+  for (int s = 0; s < ctx->nsys; ++s)
+    if (stt[s]) {
+      ctx->err = "a bounded wait of a device kernel gave up (system " + std::to_string(s) + ")";
+      return TPNS_ETIMEOUT;
     }
   return TPNS_OK;
 }
@@ -1679,9 +1689,13 @@ static tpns_status band_solve_run(int n, int kl, int ku, const int32_t* rowptr, 
   CKS(cudaMemcpyAsync(&hrel, rel, sizeof(double), cudaMemcpyDeviceToHost, st));
   CKS(cudaStreamSynchronize(st));
   if (relres_out) *relres_out = hrel;
-  if (hst) {
+  if (hst & 1) {
     err = "zero or non-finite pivot";
     return TPNS_EBREAKDOWN;
+  }
+  if (hst) {
+    err = "a bounded wait of a device kernel gave up";
+    return TPNS_ETIMEOUT;
   }
   if (!(hrel <= 1e-9)) {
     err = "iterative refinement stopped at relative residual " + std::to_string(hrel);
