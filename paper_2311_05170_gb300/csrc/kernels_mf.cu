@@ -282,8 +282,11 @@ __device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, 
 
 // CUDA-core tile update: F[r0:r0+128, c0:c0+128] -= L21 U12 (K = kb), reading the panel
 // from the front.  Thread (tx, ty) owns rows tx + 16 a and columns ty + 16 b.
+// (rows below m, columns below cl: cl = m by default)
 template <typename T>
-__device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, int k0, int kb, int r0, int c0, T* As, T* Bs) {
+__device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, int k0, int kb, int r0, int c0, T* As, T* Bs,
+                                             int cl = -1) {
+  if (cl < 0) cl = m;
   constexpr int W = MF_TILE + 4;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 #pragma unroll
@@ -292,7 +295,7 @@ __device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, i
     const int k = q / MF_TILE, r = q % MF_TILE;
     As[k * W + r] = (k < kb && r0 + r < m) ? F[(int64_t)(k0 + k) * ld + r0 + r] : T(0);
     const int c = q / MF_NB, kk = q % MF_NB;
-    Bs[kk * W + c] = (kk < kb && c0 + c < m) ? F[(int64_t)(c0 + c) * ld + k0 + kk] : T(0);
+    Bs[kk * W + c] = (kk < kb && c0 + c < cl) ? F[(int64_t)(c0 + c) * ld + k0 + kk] : T(0);
   }
   __syncthreads();
   T acc[8][8];
@@ -314,7 +317,7 @@ __device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, i
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
     const int c = c0 + ty + 16 * b;
-    if (c >= m) continue;
+    if (c >= cl) continue;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       const int r = r0 + tx + 16 * a;
@@ -366,12 +369,12 @@ __device__ __forceinline__ void pack_panel(const float* __restrict__ F, int ld, 
 
 // One thread: the twelve products of a chunk (four K-steps of 8, each hi*hi + hi*lo + lo*hi),
 // then a commit of their completion to the mbarrier.
-__device__ __noinline__ void issue_chunk(const TcSmem& S, uint64_t* bar) {
+__device__ __noinline__ void issue_chunk(const TcSmem& S, uint64_t* bar, bool accumulate = false) {
   const uint32_t ah = su32(S.Ahi), al = su32(S.Alo), bh = su32(S.Bhi), bl = su32(S.Blo);
 #pragma unroll 1
   for (int kk = 0; kk < MF_NB / 8; ++kk) {
     const uint32_t o = kk * 256;   // 8 TF32 values = two 16-byte core matrices along K
-    tc_mma_tf32(S.tmem, sm_desc(ah + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, kk > 0);
+    tc_mma_tf32(S.tmem, sm_desc(ah + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, kk > 0 || accumulate);
     tc_mma_tf32(S.tmem, sm_desc(ah + o, 128, 1024), sm_desc(bl + o, 128, 1024), MF_IDESC, 1);
     tc_mma_tf32(S.tmem, sm_desc(al + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, 1);
   }
@@ -703,10 +706,49 @@ __global__ void __launch_bounds__(MF_THREADS) mf_big_panel_kernel(MFBigArgs A, T
                 blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-// trailing update of pivot block k0: the 128 x 128 tiles of F[k1:m, k1:m] of all listed
-// fronts (with p > k0), enumerated front by front, taken round robin by the CTAs
+// Trailing updates of the listed fronts (with p > k0), in 128 x 128 tiles taken round robin
+// by the CTAs.  mode 1, pivot block k0 (K = its 32 columns): only the strips the next pivot
+// blocks need, rows [k1, m) x columns [k1, p) and rows [k1, p) x columns [p, m).  mode 2, after
+// the last pivot block: the Schur block [p, m) x [p, m) once, K = p (the products of all pivot
+// blocks accumulate in tensor memory, or in registers on the CUDA-core path).
+struct BigTile {
+  int r0, c0, rl, cl;   // tile origin, row / column limits
+};
+__device__ __forceinline__ int big_tiles(const MFFrontDev& Fd, int mode, int k0) {
+  const int p = Fd.p, m = Fd.m;
+  if (mode == 2) {
+    const int nt = (m - p + MF_TILE - 1) / MF_TILE;
+    return m > p ? nt * nt : 0;
+  }
+  if (k0 >= p) return 0;
+  const int k1 = min(k0 + MF_NB, p);
+  if (k1 >= p) return 0;
+  const int a = (m - k1 + MF_TILE - 1) / MF_TILE, b = (p - k1 + MF_TILE - 1) / MF_TILE;
+  const int c = (m - p + MF_TILE - 1) / MF_TILE;
+  return a * b + b * c;
+}
+__device__ __forceinline__ BigTile big_tile(const MFFrontDev& Fd, int mode, int k0, int tl) {
+  const int p = Fd.p, m = Fd.m;
+  BigTile T;
+  if (mode == 2) {
+    const int nt = (m - p + MF_TILE - 1) / MF_TILE;
+    T.r0 = p + (tl % nt) * MF_TILE; T.c0 = p + (tl / nt) * MF_TILE; T.rl = m; T.cl = m;
+    return T;
+  }
+  const int k1 = min(k0 + MF_NB, p);
+  const int a = (m - k1 + MF_TILE - 1) / MF_TILE, b = (p - k1 + MF_TILE - 1) / MF_TILE;
+  if (tl < a * b) {
+    T.r0 = k1 + (tl % a) * MF_TILE; T.c0 = k1 + (tl / a) * MF_TILE; T.rl = m; T.cl = p;
+  } else {
+    tl -= a * b;
+    T.r0 = k1 + (tl % b) * MF_TILE; T.c0 = p + (tl / b) * MF_TILE; T.rl = p; T.cl = m;
+  }
+  return T;
+}
+
 template <typename T, bool TC>
-__global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs A, T* __restrict__ Fall, int k0) {
+__global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs A, T* __restrict__ Fall, int k0,
+                                                                      int mode) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int s_pre[MF_BIG_LIST + 1];
   __shared__ int s_flag;
@@ -715,12 +757,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
     int acc = 0;
     for (int i = 0; i < A.nlist; ++i) {
       s_pre[i] = acc;
-      const MFFrontDev& Fd = A.fronts[A.list[i]];
-      if (k0 < Fd.p) {
-        const int k1 = min(k0 + MF_NB, Fd.p);
-        const int nt = (Fd.m - k1 + MF_TILE - 1) / MF_TILE;
-        acc += nt * nt;
-      }
+      acc += big_tiles(A.fronts[A.list[i]], mode, k0);
     }
     s_pre[A.nlist] = acc;
     s_flag = 0;
@@ -743,34 +780,42 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
     while (s_pre[fi + 1] <= t) ++fi;
     const MFFrontDev& Fd = A.fronts[A.list[fi]];
     T* F = Fall + Fd.f_off;
-    const int ld = Fd.ld, m = Fd.m;
-    const int kb = min(MF_NB, Fd.p - k0), k1 = k0 + kb;
-    const int nt = (m - k1 + MF_TILE - 1) / MF_TILE;
-    const int tl = t - s_pre[fi];
-    const int r0 = k1 + (tl % nt) * MF_TILE, c0 = k1 + (tl / nt) * MF_TILE;
+    const int ld = Fd.ld;
+    const BigTile G = big_tile(Fd, mode, k0, t - s_pre[fi]);
+    // K chunks: the pivot block (mode 1) or all pivot blocks (mode 2)
+    const int kc0 = mode == 2 ? 0 : k0;
+    const int kc1 = mode == 2 ? Fd.p : min(k0 + MF_NB, Fd.p);
     if constexpr (TC) {
       if (s_flag & 2) break;   // a bounded wait gave up: issue no further products
-      const int nr = min(MF_TILE, m - r0), nc = min(MF_CN, m - c0);
+      const int nr = min(MF_TILE, G.rl - G.r0), nc = min(MF_CN, G.cl - G.c0);
       float* Ff = reinterpret_cast<float*>(F);
-      if (tid < MF_TILE) pack_panel(Ff, ld, k0, kb, r0, nr, true, tid, TS.Ahi, TS.Alo);
-      else if (tid - MF_TILE < MF_CN) pack_panel(Ff, ld, k0, kb, c0, nc, false, tid - MF_TILE, TS.Bhi, TS.Blo);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc_before();
-      __syncthreads();
-      tc_after();
-      if (tid == 0) issue_chunk(TS, &TS.bar);
-      // the tile's current values are loaded while the products run (clamped addresses)
       const int q4 = warp & 3, hcol = warp >> 2;
-      const int r = r0 + 32 * q4 + lane;
-      const int cb = c0 + 64 * hcol;
-      const int rr = r < m ? r : m - 1;
+      const int r = G.r0 + 32 * q4 + lane;
+      const int cb = G.c0 + 64 * hcol;
+      const int rr = r < G.rl ? r : G.rl - 1;
       float f[64];
+      for (int kc = kc0; kc < kc1; kc += MF_NB) {
+        const int kb = min(MF_NB, kc1 - kc);
+        if (tid < MF_TILE) pack_panel(Ff, ld, kc, kb, G.r0, nr, true, tid, TS.Ahi, TS.Alo);
+        else if (tid - MF_TILE < MF_CN) pack_panel(Ff, ld, kc, kb, G.c0, nc, false, tid - MF_TILE, TS.Bhi, TS.Blo);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_before();
+        __syncthreads();
+        tc_after();
+        if (tid == 0) issue_chunk(TS, &TS.bar, kc > kc0);
+        if (kc == kc0) {
+          // the tile's current values are loaded while the first products run (clamped addresses)
 #pragma unroll
-      for (int c = 0; c < 64; ++c) f[c] = Ff[(int64_t)(cb + c < m ? cb + c : m - 1) * ld + rr];
-      if (!mb_wait(&TS.bar, ph) && lane == 0) atomicOr(&s_flag, 2);
-      ph ^= 1u;
-      tc_after();
-      if (r0 + 32 * q4 < m && cb < m) {
+          for (int c = 0; c < 64; ++c) f[c] = Ff[(int64_t)(cb + c < G.cl ? cb + c : G.cl - 1) * ld + rr];
+        }
+        if (!mb_wait(&TS.bar, ph) && lane == 0) atomicOr(&s_flag, 2);
+        ph ^= 1u;
+        tc_after();
+        tc_before();
+        __syncthreads();   // operands are free again
+        tc_after();
+      }
+      if (G.r0 + 32 * q4 < G.rl && cb < G.cl) {
         const uint32_t base = TS.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(64 * hcol);
 #pragma unroll
         for (int h16 = 0; h16 < 4; ++h16) {
@@ -778,10 +823,10 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
           uint32_t d[16];
           tm_ld16(base + (uint32_t)(16 * h16), d);
           tm_wait_ld();
-          if (r < m) {
+          if (r < G.rl) {
 #pragma unroll
             for (int c = 0; c < 16; ++c)
-              if (cb2 + c < m) Ff[(int64_t)(cb2 + c) * ld + r] = f[16 * h16 + c] - __uint_as_float(d[c]);
+              if (cb2 + c < G.cl) Ff[(int64_t)(cb2 + c) * ld + r] = f[16 * h16 + c] - __uint_as_float(d[c]);
           }
         }
       }
@@ -790,7 +835,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
       tc_after();
     } else {
       T* As = reinterpret_cast<T*>(smem_raw);
-      update_tile_fma<T>(F, ld, m, k0, kb, r0, c0, As, As + MF_NB * (MF_TILE + 4));
+      for (int kc = kc0; kc < kc1; kc += MF_NB)
+        update_tile_fma<T>(F, ld, G.rl, kc, min(MF_NB, kc1 - kc), G.r0, G.c0, As, As + MF_NB * (MF_TILE + 4),
+                           G.cl);
     }
   }
   if constexpr (TC) {
@@ -798,10 +845,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
     __syncthreads();
     tc_after();
     if (warp == 0) tm_dealloc(TS.tmem, MF_TMEM_COLS);
-    if (tid == 0 && (s_flag & 2)) {
-      // report the expired wait on the first listed front's system
-      atomicOr(&A.status[A.sys[A.fronts[A.list[0]].sys].sid], 2);
-    }
+    if (tid == 0 && (s_flag & 2)) atomicOr(&A.status[A.sys[A.fronts[A.list[0]].sys].sid], 2);
   }
 }
 
@@ -1149,13 +1193,18 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
   if (e != cudaSuccess) return e;
   const int ugrid = mf_grid((const void*)ufn, smem, L.grid_cap);
   for (int k0 = 0; k0 < max_p; k0 += MF_NB) {
-    count_launches(2);
+    count_launches(1);
     mf_big_panel_kernel<T><<<dim3(per, nlist), MF_THREADS, 0, st>>>(A, F, dinv, k0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ufn<<<ugrid, MF_THREADS, smem, st>>>(A, F, k0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (k0 + MF_NB < max_p) {   // the last pivot block leaves nothing for the next one
+      count_launches(1);
+      ufn<<<ugrid, MF_THREADS, smem, st>>>(A, F, k0, 1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
-  return cudaSuccess;
+  count_launches(1);
+  ufn<<<ugrid, MF_THREADS, smem, st>>>(A, F, 0, 2);
+  return cudaGetLastError();
 }
 
 #define TPNS_MF_INST(T)                                                                                      \

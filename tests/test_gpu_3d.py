@@ -122,19 +122,22 @@ def test_3d_deterministic_and_graph_equals_eager(native):
 
 
 @pytest.mark.parametrize("dim,prec", [(2, "fp32"), (2, "fp64"), (3, "fp32"), (3, "fp64")])
-def test_large_front_path_bitwise_equal(native, dim, prec):
-    """Fronts factored by all CTAs together (forced down to order 128) give the same bits as
-    the one-CTA dataflow path: the same operations in the same order."""
+def test_large_front_path_matches_one_cta_path(native, dim, prec):
+    """Fronts factored by all CTAs together (forced down to order 128) give the fields of the
+    one-CTA dataflow path up to the refinement's tolerance (the Schur block of a large front is
+    updated once with all its pivot columns, a different rounding order), and the large-front
+    path itself is deterministic."""
     w = W.config_3d_small(n_coarse=2, r=3, nsub=(1, 1, 1), overlap=1, nsteps=2) if dim == 3 else \
         W.config_graded(nsteps=2)
     out = []
-    for big in (-1, 128):
+    for big in (-1, 128, 128):
         s = native.Solver(w, precision=prec, mf_big_m=big)
         s.step(2)
         out.append(s.fields())
         s.close()
     for k in out[0]:
-        assert np.array_equal(out[0][k], out[1][k]), k
+        assert rel(out[1][k], out[0][k]) <= 1e-11, (k, rel(out[1][k], out[0][k]))
+        assert np.array_equal(out[1][k], out[2][k]), k
 
 
 def test_large_front_path_parity_3d(native):
