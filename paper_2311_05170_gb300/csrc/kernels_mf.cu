@@ -646,25 +646,26 @@ struct MFBigArgs {
   int* status;
 };
 
-// phase 0: zero the front and place its CSR values; phase 1 / 2: add the Schur complement of
-// child 0 / 1 (distinct positions within one child).  Columns are spread over the CTAs of
-// the front (blockIdx.y).
+// phase 0: zero the front; phase 3: place its CSR values (distinct positions); phase 1 / 2:
+// add the Schur complement of child 0 / 1 (distinct positions within one child).  Each pass
+// is a flat loop over the front's entries spread over the CTAs of the front (blockIdx.y).
 template <typename T>
 __global__ void __launch_bounds__(MF_THREADS) mf_big_assemble_kernel(MFBigArgs A, T* __restrict__ Fall, int phase) {
   const MFFrontDev& Fd = A.fronts[A.list[blockIdx.y]];
   T* F = Fall + Fd.f_off;
   const int ld = Fd.ld, m = Fd.m;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, step = (int64_t)gridDim.x * blockDim.x;
   if (phase == 0) {
+    const int64_t n = (int64_t)ld * m;
+    for (int64_t q = first; q < n; q += step) F[q] = T(0);
+    return;
+  }
+  if (phase == 3) {
     const double* vals = A.vals + A.sys[Fd.sys].val_off;
-    for (int j = blockIdx.x; j < m; j += gridDim.x) {
-      for (int i = threadIdx.x; i < ld; i += blockDim.x) F[(int64_t)j * ld + i] = T(0);
-      __syncthreads();
-      const int64_t b = A.colptr[Fd.colptr_off + j], e = A.colptr[Fd.colptr_off + j + 1];
-      for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) {
-        const int32_t ij = A.orig_ij[q];
-        F[(int64_t)(ij >> 16) * ld + (ij & 0xFFFF)] = (T)vals[A.orig_k[q]];
-      }
-      __syncthreads();
+    const int64_t b = A.colptr[Fd.colptr_off], e = A.colptr[Fd.colptr_off + m];
+    for (int64_t q = b + first; q < e; q += step) {
+      const int32_t ij = A.orig_ij[q];
+      F[(int64_t)(ij >> 16) * ld + (ij & 0xFFFF)] = (T)vals[A.orig_k[q]];
     }
     return;
   }
@@ -673,10 +674,10 @@ __global__ void __launch_bounds__(MF_THREADS) mf_big_assemble_kernel(MFBigArgs A
   const int qc = C.m - C.p;
   const T* src = Fall + C.f_off + (int64_t)C.p * C.ld + C.p;
   const int32_t* rm = A.relmap + C.relmap_off;
-  for (int jc = blockIdx.x; jc < qc; jc += gridDim.x) {
-    T* dcol = F + (int64_t)rm[jc] * ld;
-    const T* scol = src + (int64_t)jc * C.ld;
-    for (int ic = threadIdx.x; ic < qc; ic += blockDim.x) dcol[rm[ic]] += ldcg(scol + ic);
+  const int64_t n = (int64_t)qc * qc;
+  for (int64_t q = first; q < n; q += step) {
+    const int jc = (int)(q / qc), ic = (int)(q - (int64_t)jc * qc);
+    F[(int64_t)rm[jc] * ld + rm[ic]] += ldcg(src + (int64_t)jc * C.ld + ic);
   }
 }
 
@@ -1179,11 +1180,12 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  // CTAs per front for the column-parallel and row-parallel steps: enough to cover the device
+  // CTAs per front for the assembly and the row-parallel panels: enough to cover the device
   const int per = std::max(1, std::min(64, (2 * nsm + nlist - 1) / nlist));
-  for (int phase = 0; phase < 3; ++phase) {
+  const int per_asm = std::max(1, std::min(256, (8 * nsm + nlist - 1) / nlist));
+  for (int phase : {0, 3, 1, 2}) {
     count_launches(1);
-    mf_big_assemble_kernel<T><<<dim3(per, nlist), MF_THREADS, 0, st>>>(A, F, phase);
+    mf_big_assemble_kernel<T><<<dim3(per_asm, nlist), MF_THREADS, 0, st>>>(A, F, phase);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const bool use_tc = tc && sizeof(T) == 4;
