@@ -192,7 +192,7 @@ typedef struct {
                                factors, 2 for FP64) */
   int32_t mf_big_m;         /* multifrontal: fronts of at least this order, and all their
                                ancestors, are factored by all CTAs together, one height level
-                               of the elimination trees at a time (0 = 768; < 0: never) */
+                               of the elimination trees at a time (0 = 256; < 0: never) */
 } tpns_options;
 
 /* Build meshes, subdomains, sparsity, scatter maps and band orderings on the host, upload

@@ -78,7 +78,7 @@ struct tpns_ctx {
   int mf_leaf = 96, mf_tc = 1, mf_m_max = 1, mf_oseen_fronts = 0;
   // large fronts (factored by all CTAs): order threshold, fronts of the dataflow launch per
   // group (Oseen, Darcy), and per group the height levels (offset into d_mf_big, count, max p)
-  int mf_big_m = 768;
+  int mf_big_m = 256;
   int mf_small[2] = {0, 0};
   std::vector<std::array<int, 3>> mf_big_levels[2];
   int32_t* d_mf_big = nullptr;
@@ -1770,7 +1770,7 @@ static bool read_options(const tpns_options* o, tpns_options& opt) {
   if (opt.refinement < 0 || opt.refinement > 1 || opt.ir_classic_max < 0 || opt.ir_classic_max > 64) return false;
   if (opt.mf_leaf == 0) opt.mf_leaf = 96;
   if (opt.mf_leaf < 8) return false;
-  if (opt.mf_big_m == 0) opt.mf_big_m = 768;
+  if (opt.mf_big_m == 0) opt.mf_big_m = 256;
   if (opt.mf_big_m > 0 && opt.mf_big_m < 128) return false;
   return true;
 }

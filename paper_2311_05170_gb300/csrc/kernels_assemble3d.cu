@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(OTHREADS) oseen_elem3_kernel(AsmArgs A, int64_
     double res = 0.0;
     if (r < 30) {
       const int i = r / 3, a = r % 3;
+#pragma unroll
       for (int j = 0; j < 10; ++j) {
         // Sp[c][d] = |det| sum_{p,q} J[p][c] J[q][d] S[i][j][p][q]; only Sp[b][a] and the trace
         double tq[3][3];
@@ -218,10 +219,19 @@ __global__ void __launch_bounds__(OTHREADS) oseen_elem3_kernel(AsmArgs A, int64_
           const double kF = Ph.k[0], fd = E.F.det;
           if (a < 2) {
             const double bjs = eta * Ph.nu * Ph.alpha / sqrt(kF);
+            double mb[6];
             for (int b = 0; b < 6; ++b) {
-              const double m = bjs * fd * R.fM[pa][b];
-              K[3 * E.F.sl[b] + a] += m;
-              res += m * E.w1[3 * E.F.sl[b] + a];
+              mb[b] = bjs * fd * R.fM[pa][b];
+              res += mb[b] * E.w1[3 * E.F.sl[b] + a];
+            }
+            // add to the row entries of the face nodes (static register indices)
+#pragma unroll
+            for (int j = 0; j < 10; ++j) {
+              double add = 0.0;
+#pragma unroll
+              for (int b = 0; b < 6; ++b) add += E.F.sl[b] == j ? mb[b] : 0.0;
+              if (a == 0) K[3 * j] += add;
+              else K[3 * j + 1] += add;
             }
             double d = 0.0, g = 0.0;
             for (int q = 0; q < 7; ++q) {
@@ -243,7 +253,9 @@ __global__ void __launch_bounds__(OTHREADS) oseen_elem3_kernel(AsmArgs A, int64_
       res = rhs - res;
     } else {
       const int k = r - 30;
+#pragma unroll
       for (int j = 0; j < 10; ++j)
+#pragma unroll
         for (int b = 0; b < 3; ++b) {
           const double v = eta * ad * (J[b] * R.B[k][j][0] + J[3 + b] * R.B[k][j][1] + J[6 + b] * R.B[k][j][2]);
           K[3 * j + b] = v;
@@ -252,9 +264,11 @@ __global__ void __launch_bounds__(OTHREADS) oseen_elem3_kernel(AsmArgs A, int64_
       K[30] = K[31] = K[32] = K[33] = 0.0;
       res = -res;
     }
+#pragma unroll
     for (int c = 0; c < 34; ++c)
       if (E.fixed[c]) res -= K[c] * E.eB[c];
     double* ko = Ke + e * (OROWS * OROWS) + r * OROWS;
+#pragma unroll
     for (int c = 0; c < 34; ++c) ko[c] = K[c];
     Re[e * OROWS + r] = res;
   }
