@@ -69,6 +69,10 @@ struct ElemO {
   Face F;
   double pF[6];
   double gN[7], gT[7][2];
+  // per node pair (i, j): |det J| int d_c phi_i d_d phi_j (Sp[c][d]) and the convection
+  // integral eta |det J| int (w . grad phi_j) phi_i, formed once for the three components
+  double Sp[100][9];
+  double c1[100];
 };
 
 }  // namespace
@@ -164,6 +168,27 @@ __global__ void __launch_bounds__(OTHREADS) oseen_elem3_kernel(AsmArgs A, int64_
         }
       }
     }
+    __syncthreads();   // what, fq, face data ready
+    // the pair quantities (three pairs per thread)
+    if (valid) {
+      const double* J = E.J;
+      const double ad = E.ad;
+      for (int q = r; q < 100; q += OROWS) {
+        const int i = q / 10, j = q % 10;
+        double tq[3][3];
+        for (int p = 0; p < 3; ++p)
+          for (int d = 0; d < 3; ++d)
+            tq[p][d] = R.S[i][j][p][0] * J[d] + R.S[i][j][p][1] * J[3 + d] + R.S[i][j][p][2] * J[6 + d];
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d)
+            E.Sp[q][3 * c + d] = ad * (J[c] * tq[0][d] + J[3 + c] * tq[1][d] + J[6 + c] * tq[2][d]);
+        double c1 = 0.0;
+        for (int k = 0; k < 10; ++k)
+          c1 += E.what[3 * k] * R.T[k][j][i][0] + E.what[3 * k + 1] * R.T[k][j][i][1] +
+                E.what[3 * k + 2] * R.T[k][j][i][2];
+        E.c1[q] = ad * c1;
+      }
+    }
     __syncthreads();
     if (!valid) continue;
     const double eta = Ph.eta, nueta = Ph.nu * Ph.eta, eta_dt = Ph.eta / Ph.dt, ad = E.ad;
@@ -174,27 +199,19 @@ __global__ void __launch_bounds__(OTHREADS) oseen_elem3_kernel(AsmArgs A, int64_
       const int i = r / 3, a = r % 3;
 #pragma unroll
       for (int j = 0; j < 10; ++j) {
-        // Sp[c][d] = |det| sum_{p,q} J[p][c] J[q][d] S[i][j][p][q]; only Sp[b][a] and the trace
-        double tq[3][3];
-        for (int p = 0; p < 3; ++p)
-          for (int d = 0; d < 3; ++d)
-            tq[p][d] = R.S[i][j][p][0] * J[d] + R.S[i][j][p][1] * J[3 + d] + R.S[i][j][p][2] * J[6 + d];
-        double Sba[3], lap = 0.0;
-        for (int b = 0; b < 3; ++b) {
-          Sba[b] = ad * (J[b] * tq[0][a] + J[3 + b] * tq[1][a] + J[6 + b] * tq[2][a]);
-          lap += ad * (J[b] * tq[0][b] + J[3 + b] * tq[1][b] + J[6 + b] * tq[2][b]);
-        }
+        const double* Sp = E.Sp[10 * i + j];
+        double Sba[3];
+        for (int b = 0; b < 3; ++b) Sba[b] = Sp[3 * b + a];
+        const double lap = Sp[0] + Sp[4] + Sp[8];
         const double mij = ad * R.M[i][j];
-        double c1 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0;
+        const double c1 = E.c1[10 * i + j];
+        double u0 = 0.0, u1 = 0.0, u2 = 0.0;
         for (int k = 0; k < 10; ++k) {
-          c1 += E.what[3 * k] * R.T[k][j][i][0] + E.what[3 * k + 1] * R.T[k][j][i][1] +
-                E.what[3 * k + 2] * R.T[k][j][i][2];
           const double wk = E.w1[3 * k + a];
           u0 += wk * R.U[i][j][k][0];
           u1 += wk * R.U[i][j][k][1];
           u2 += wk * R.U[i][j][k][2];
         }
-        c1 *= ad;
         for (int b = 0; b < 3; ++b) {
           const double visc = nueta * (Sba[b] + (a == b ? lap : 0.0));
           double v = visc + eta * ad * (J[b] * u0 + J[3 + b] * u1 + J[6 + b] * u2);

@@ -8,6 +8,7 @@ import pytest
 
 import workloads as W
 from oracle.scheme import TwoGridOracle
+from oracle.scheme3d import TwoGridOracle3D
 
 pytestmark = pytest.mark.gpu
 
@@ -27,10 +28,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("cfg,prec,nranks", [("small", "fp64", 2), ("small", "fp32", 3), ("graded", "fp32", 2)])
+@pytest.mark.parametrize("cfg,prec,nranks", [("small", "fp64", 2), ("small", "fp32", 3), ("graded", "fp32", 2),
+                                              ("small3d", "fp32", 3)])
 def test_split_parts_sum_to_the_whole(native, cfg, prec, nranks):
     from paper_2311_05170_gb300.shard import reduce_fields
-    w = W.config_small(nsteps=3) if cfg == "small" else W.config_graded(nsteps=3)
+    w = {"small": lambda: W.config_small(nsteps=3), "graded": lambda: W.config_graded(nsteps=3),
+         "small3d": lambda: W.config_3d_small(n_coarse=2, r=2, nsub=(2, 2, 1), overlap=1, nsteps=3)}[cfg]()
     whole = native.Solver(w, precision=prec)
     whole.step(3)
     ref = whole.fields()
@@ -44,8 +47,8 @@ def test_split_parts_sum_to_the_whole(native, cfg, prec, nranks):
     tot = {k: sum(p[k] for p in parts) for k in ref}
     for k in ref:
         assert rel(tot[k], ref[k]) <= 1e-14, (k, rel(tot[k], ref[k]))
-    if cfg == "small":
-        o = TwoGridOracle(w)
+    if cfg in ("small", "small3d"):
+        o = TwoGridOracle(w) if cfg == "small" else TwoGridOracle3D(w)
         o.run(3)
         for k in ref:
             assert rel(tot[k], o.fine[k]) <= (1e-10 if prec == "fp64" else 1e-8), k
