@@ -936,11 +936,14 @@ __global__ void __launch_bounds__(NT, 512 / NT)
   __shared__ int s_task, s_any;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int epoch = ld_acquire(&A.sched[2]);
-  // a pass after every system has converged takes no task at all
-  if (tid == 0) {
-    int any = A.done ? 0 : 1;
-    for (int i = 0; i < A.nsys && !any; ++i) any = !A.done[A.sys[i].sid];
-    s_any = any;
+  // a pass after every system has converged takes no task at all (the threads check the
+  // systems' done flags side by side)
+  {
+    int pending = A.done ? 0 : 1;
+    if (A.done)
+      for (int i = tid; i < A.nsys; i += blockDim.x) pending |= !A.done[A.sys[i].sid];
+    pending = __syncthreads_or(pending);
+    if (tid == 0) s_any = pending;
   }
   __syncthreads();
   for (; s_any;) {
