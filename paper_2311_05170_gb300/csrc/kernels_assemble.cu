@@ -39,6 +39,10 @@ struct ElemS {
   double pF[3];
   double L;
   double gN[3], gT[3];
+  // per node pair (i, j): |det J| int d_c phi_i d_d phi_j (Sp[c][d]) and the convection
+  // integral |det J| int (w . grad phi_j) phi_i, formed once for both components
+  double Sp[36][4];
+  double c1[36];
 };
 
 __device__ __forceinline__ void copy_tables(RefTables* dst, const double* src) {
@@ -142,6 +146,23 @@ __global__ void __launch_bounds__(128) oseen_elem_kernel(AsmArgs A, int64_t e_be
     }
   }
   __syncthreads();
+  // the pair quantities (36 pairs over the element's 16 threads)
+  if (valid) {
+    const double* J = E.J;
+    const double ad = E.ad;
+    for (int q = r; q < 36; q += 16) {
+      const int i = q / 6, j = q % 6;
+      const double s00 = R.S[i][j][0][0], s01 = R.S[i][j][0][1], s10 = R.S[i][j][1][0], s11 = R.S[i][j][1][1];
+      for (int c = 0; c < 2; ++c)
+        for (int d = 0; d < 2; ++d)
+          E.Sp[q][2 * c + d] =
+              ad * (J[0 + c] * (J[0 + d] * s00 + J[2 + d] * s01) + J[2 + c] * (J[0 + d] * s10 + J[2 + d] * s11));
+      double c1 = 0.0;
+      for (int k = 0; k < 6; ++k) c1 += E.what[2 * k] * R.T[k][j][i][0] + E.what[2 * k + 1] * R.T[k][j][i][1];
+      E.c1[q] = ad * c1;
+    }
+  }
+  __syncthreads();
   if (!valid || r >= 15) return;
   const double eta = Ph.eta, nueta = Ph.nu * Ph.eta, eta_dt = Ph.eta / Ph.dt, ad = E.ad;
   const double* J = E.J;
@@ -150,19 +171,15 @@ __global__ void __launch_bounds__(128) oseen_elem_kernel(AsmArgs A, int64_t e_be
   if (r < 12) {
     const int i = r >> 1, a = r & 1;
     for (int j = 0; j < 6; ++j) {
-      const double s00 = R.S[i][j][0][0], s01 = R.S[i][j][0][1], s10 = R.S[i][j][1][0], s11 = R.S[i][j][1][1];
-      double Sp[2][2];
-      for (int c = 0; c < 2; ++c)
-        for (int d = 0; d < 2; ++d)
-          Sp[c][d] = ad * (J[0 + c] * (J[0 + d] * s00 + J[2 + d] * s01) + J[2 + c] * (J[0 + d] * s10 + J[2 + d] * s11));
+      const double* Spq = E.Sp[6 * i + j];
+      const double Sp[2][2] = {{Spq[0], Spq[1]}, {Spq[2], Spq[3]}};
       const double mij = ad * R.M[i][j];
-      double c1 = 0.0, u0 = 0.0, u1 = 0.0;
+      const double c1 = E.c1[6 * i + j];
+      double u0 = 0.0, u1 = 0.0;
       for (int k = 0; k < 6; ++k) {
-        c1 += E.what[2 * k] * R.T[k][j][i][0] + E.what[2 * k + 1] * R.T[k][j][i][1];
         u0 += E.w1[2 * k + a] * R.U[i][j][k][0];
         u1 += E.w1[2 * k + a] * R.U[i][j][k][1];
       }
-      c1 *= ad;
       const double lap = Sp[0][0] + Sp[1][1];
       for (int b = 0; b < 2; ++b) {
         const double visc = nueta * (Sp[b][a] + (a == b ? lap : 0.0));
