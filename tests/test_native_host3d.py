@@ -117,3 +117,31 @@ def test_multifrontal_structure_3d_reproduces_sparse_solve(native):
         x_ref = spla.spsolve(A.tocsc(), b)
         assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
     s.close()
+
+
+def test_3d_descriptor_and_option_errors(native):
+    """3D descriptors and the large-front option are validated on the host: a coarse mesh that
+    is not a cube, subdomains that do not split the coarse cells, a 2D manufactured solution on
+    a 3D mesh, an unknown mesh dimension and a large-front threshold below 128 are refused with
+    TPNS_EINVAL before anything is allocated."""
+    import ctypes as C
+    lib = native.load()
+    w = W.config_3d_small(n_coarse=2, r=2, nsub=(2, 2, 1), overlap=1)
+    ctx = C.c_void_p()
+    md, pr, pd, dd = native.descriptors(w)
+    md.ny_coarse = 3
+    assert lib.tpns_layout_create(C.byref(md), C.byref(pd), C.byref(ctx)) == native.TPNS_EINVAL
+    md, pr, pd, dd = native.descriptors(w)
+    pd.nsub_z = 3
+    assert lib.tpns_layout_create(C.byref(md), C.byref(pd), C.byref(ctx)) == native.TPNS_EINVAL
+    md, pr, pd, dd = native.descriptors(w)
+    md.dim = 5
+    assert lib.tpns_layout_create(C.byref(md), C.byref(pd), C.byref(ctx)) == native.TPNS_EINVAL
+    md, pr, pd, dd = native.descriptors(w)
+    dd.mms_id = 1                                   # the 2D trigonometric field
+    st = lib.tpns_create(C.byref(md), C.byref(pr), C.byref(pd), C.byref(dd), 0.01, 0, 0, None, C.byref(ctx))
+    assert st == native.TPNS_EINVAL and not ctx.value
+    with pytest.raises(native.TpnsError):
+        native.Solver(w, host_only=True, mf_big_m=64)
+    s = native.Solver(w, host_only=True, mf_big_m=-1)   # never: accepted
+    s.close()
