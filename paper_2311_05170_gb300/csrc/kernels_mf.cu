@@ -747,9 +747,13 @@ __device__ __forceinline__ BigTile big_tile(const MFFrontDev& Fd, int mode, int 
   return T;
 }
 
+// Tensor-core variant: 512 threads (16 warps: warp w reads accumulator lanes 32 (w % 4) ..
+// and columns 32 (w / 4) ..), so that more of a tile's loads are in flight; CUDA-core variant:
+// MF_THREADS (the 16 x 16 thread layout of update_tile_fma).
+constexpr int MF_BIG_UTHREADS = 512;
 template <typename T, bool TC>
-__global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs A, T* __restrict__ Fall, int k0,
-                                                                      int mode) {
+__global__ void __launch_bounds__(TC ? MF_BIG_UTHREADS : MF_THREADS, 1)
+    mf_big_update_kernel(MFBigArgs A, T* __restrict__ Fall, int k0, int mode) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int s_pre[MF_BIG_LIST + 1];
   __shared__ int s_flag;
@@ -792,9 +796,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
       float* Ff = reinterpret_cast<float*>(F);
       const int q4 = warp & 3, hcol = warp >> 2;
       const int r = G.r0 + 32 * q4 + lane;
-      const int cb = G.c0 + 64 * hcol;
+      const int cb = G.c0 + 32 * hcol;
       const int rr = r < G.rl ? r : G.rl - 1;
-      float f[64];
+      float f[32];
       for (int kc = kc0; kc < kc1; kc += MF_NB) {
         const int kb = min(MF_NB, kc1 - kc);
         if (tid < MF_TILE) pack_panel(Ff, ld, kc, kb, G.r0, nr, true, tid, TS.Ahi, TS.Alo);
@@ -807,7 +811,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
         if (kc == kc0) {
           // the tile's current values are loaded while the first products run (clamped addresses)
 #pragma unroll
-          for (int c = 0; c < 64; ++c) f[c] = Ff[(int64_t)(cb + c < G.cl ? cb + c : G.cl - 1) * ld + rr];
+          for (int c = 0; c < 32; ++c) f[c] = Ff[(int64_t)(cb + c < G.cl ? cb + c : G.cl - 1) * ld + rr];
         }
         if (!mb_wait(&TS.bar, ph) && lane == 0) atomicOr(&s_flag, 2);
         ph ^= 1u;
@@ -817,9 +821,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) mf_big_update_kernel(MFBigArgs 
         tc_after();
       }
       if (G.r0 + 32 * q4 < G.rl && cb < G.cl) {
-        const uint32_t base = TS.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(64 * hcol);
+        const uint32_t base = TS.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(32 * hcol);
 #pragma unroll
-        for (int h16 = 0; h16 < 4; ++h16) {
+        for (int h16 = 0; h16 < 2; ++h16) {
           const int cb2 = cb + 16 * h16;
           uint32_t d[16];
           tm_ld16(base + (uint32_t)(16 * h16), d);
@@ -1194,21 +1198,22 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
   const bool use_tc = tc && sizeof(T) == 4;
   const size_t smem = use_tc ? sizeof(TcSmem) : (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T);
   auto ufn = use_tc ? mf_big_update_kernel<T, true> : mf_big_update_kernel<T, false>;
+  const int uthreads = use_tc ? MF_BIG_UTHREADS : MF_THREADS;
   e = cudaFuncSetAttribute(ufn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int ugrid = mf_grid((const void*)ufn, smem, L.grid_cap);
+  const int ugrid = mf_grid((const void*)ufn, smem, L.grid_cap, uthreads);
   for (int k0 = 0; k0 < max_p; k0 += MF_NB) {
     count_launches(1);
     mf_big_panel_kernel<T><<<dim3(per, nlist), MF_THREADS, 0, st>>>(A, F, dinv, k0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (k0 + MF_NB < max_p) {   // the last pivot block leaves nothing for the next one
       count_launches(1);
-      ufn<<<ugrid, MF_THREADS, smem, st>>>(A, F, k0, 1);
+      ufn<<<ugrid, uthreads, smem, st>>>(A, F, k0, 1);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
   count_launches(1);
-  ufn<<<ugrid, MF_THREADS, smem, st>>>(A, F, 0, 2);
+  ufn<<<ugrid, uthreads, smem, st>>>(A, F, 0, 2);
   return cudaGetLastError();
 }
 
