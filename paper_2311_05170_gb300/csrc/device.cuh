@@ -238,6 +238,21 @@ __device__ __forceinline__ double mms3_q(const Phys& P, int fld, const double* X
   return 0.0;
 }
 
+// the three sources at one point (the trigonometric base is formed once)
+__device__ __forceinline__ void mms3_q3(const Phys& P, const double* X, double t, double* q) {
+  if (P.mms == 2) {
+    const double kf = P.k[1], km = P.k[2], mu = P.mu;
+    const double cFf = P.sigma_star * kf / mu, cfm = P.sigma * km / mu;
+    const double pi2 = 9.869604401089358;
+    const double C = cospi(X[0]) * cospi(X[1]) * cospi(X[2]) * exp(-t);
+    q[0] = C * (-3.0 * P.phiC[0] + 9.0 * pi2 * P.k[0] / mu + cFf);
+    q[1] = C * (-2.0 * P.phiC[1] + 6.0 * pi2 * kf / mu - cFf + cfm);
+    q[2] = C * (-P.phiC[2] + 3.0 * pi2 * km / mu - cfm);
+    return;
+  }
+  for (int f = 0; f < 3; ++f) q[f] = mms3_q(P, f, X, t);
+}
+
 // g_N = -n_c.T n_c - p_F/rho on z = 1
 __device__ __forceinline__ double mms3_gN(const Phys& P, double x, double y, double t) {
   if (P.mms == 2) {

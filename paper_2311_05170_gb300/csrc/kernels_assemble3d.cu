@@ -305,6 +305,7 @@ struct ElemD {
   Face F;
   double gd[3][7];      // Gamma flux defects at the face points
   double ucn[6];        // u^n . n_c at the face nodes (partner velocities)
+  double Kst[100];      // int grad phi_i . grad phi_j (reference integrals and J^{-1}, without |det J|)
 };
 
 }  // namespace
@@ -349,13 +350,29 @@ __global__ void __launch_bounds__(DTHREADS) darcy_elem3_kernel(AsmArgs A, int64_
       }
     }
     __syncthreads();
+    if (valid) {
+      // the stiffness integrals, shared by the three fields
+      const double* J = E.J;
+      for (int q = r; q < 100; q += DROWS) {
+        const int i2 = q / 10, j2 = q % 10;
+        double s = 0.0;
+        for (int c = 0; c < 3; ++c)
+          s += R.S[i2][j2][0][0] * J[c] * J[c] + R.S[i2][j2][1][1] * J[3 + c] * J[3 + c] +
+               R.S[i2][j2][2][2] * J[6 + c] * J[6 + c] + (R.S[i2][j2][0][1] + R.S[i2][j2][1][0]) * J[c] * J[3 + c] +
+               (R.S[i2][j2][0][2] + R.S[i2][j2][2][0]) * J[c] * J[6 + c] +
+               (R.S[i2][j2][1][2] + R.S[i2][j2][2][1]) * J[3 + c] * J[6 + c];
+        E.Kst[q] = s;
+      }
+    }
     if (valid && !Ke) {
       if (r < 27) {
         double x[3];
         for (int c = 0; c < 3; ++c)
           x[c] = E.X[c] + (E.X[3 + c] - E.X[c]) * R.qp[r][0] + (E.X[6 + c] - E.X[c]) * R.qp[r][1] +
                  (E.X[9 + c] - E.X[c]) * R.qp[r][2];
-        for (int fl = 0; fl < 3; ++fl) E.fq[r][fl] = E.ad * R.qw[r] * mms3_q(Ph, fl, x, t);
+        double q3[3];
+        mms3_q3(Ph, x, t, q3);
+        for (int fl = 0; fl < 3; ++fl) E.fq[r][fl] = E.ad * R.qw[r] * q3[fl];
       }
       // node values per field: thread (f, i) fills node i of field f
       {
@@ -388,23 +405,11 @@ __global__ void __launch_bounds__(DTHREADS) darcy_elem3_kernel(AsmArgs A, int64_
     }
     __syncthreads();
     if (!valid) continue;
-    const double* J = E.J;
     const double ad = E.ad;
     const double cself = f == 0 ? cFf : (f == 1 ? cfm + cFf : cfm);
     const double af = Ph.phiC[f] / Ph.dt + cself, bf = Ph.k[f] / mu;
     double Arow[10];
-    for (int j = 0; j < 10; ++j) {
-      double s = 0.0;
-      for (int c = 0; c < 3; ++c) {
-        const double tc = R.S[i][j][0][0] * J[c] * J[c] + R.S[i][j][1][1] * J[3 + c] * J[3 + c] +
-                          R.S[i][j][2][2] * J[6 + c] * J[6 + c] +
-                          (R.S[i][j][0][1] + R.S[i][j][1][0]) * J[c] * J[3 + c] +
-                          (R.S[i][j][0][2] + R.S[i][j][2][0]) * J[c] * J[6 + c] +
-                          (R.S[i][j][1][2] + R.S[i][j][2][1]) * J[3 + c] * J[6 + c];
-        s += tc;
-      }
-      Arow[j] = ad * (af * R.M[i][j] + bf * s);
-    }
+    for (int j = 0; j < 10; ++j) Arow[j] = ad * (af * R.M[i][j] + bf * E.Kst[10 * i + j]);
     if (Ke) {
       double* ko = Ke + ((e - e_begin) * 3 + f) * 100 + i * 10;
       for (int j = 0; j < 10; ++j) ko[j] = Arow[j];
