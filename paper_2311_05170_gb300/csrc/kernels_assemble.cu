@@ -278,13 +278,13 @@ __global__ void __launch_bounds__(128) darcy_elem_kernel(AsmArgs A, int64_t e_be
   const double cself = f == 0 ? cFf : (f == 1 ? cfm + cFf : cfm);
   const double af = Ph.phiC[f] / Ph.dt + cself, bf = Ph.k[f] / mu;
   (void)kF;
+  // grad phi_i . grad phi_j = sum_{r,s} G[r][s] d_r phi_i d_s phi_j with the metric G = J^{-1} J^{-T}
+  const double G00 = J[0] * J[0] + J[1] * J[1], G11 = J[2] * J[2] + J[3] * J[3];
+  const double G01 = J[0] * J[2] + J[1] * J[3];
   double Ael[6][6];
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) {
-      double s = 0.0;
-      for (int c = 0; c < 2; ++c)
-        s += J[0 + c] * (J[0 + c] * R.S[i][j][0][0] + J[2 + c] * R.S[i][j][0][1]) +
-             J[2 + c] * (J[0 + c] * R.S[i][j][1][0] + J[2 + c] * R.S[i][j][1][1]);
+      const double s = G00 * R.S[i][j][0][0] + G01 * (R.S[i][j][0][1] + R.S[i][j][1][0]) + G11 * R.S[i][j][1][1];
       Ael[i][j] = ad * (af * R.M[i][j] + bf * s);
     }
   if (Ke) {
