@@ -1188,7 +1188,8 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   // CTAs per front for the assembly and the row-parallel panels: enough to cover the device
-  const int per = std::max(1, std::min(64, (2 * nsm + nlist - 1) / nlist));
+  // several times (every CTA of a front repeats the small pivot-block factorisation)
+  const int per = std::max(1, std::min(64, (8 * nsm + nlist - 1) / nlist));
   const int per_asm = std::max(1, std::min(256, (8 * nsm + nlist - 1) / nlist));
   for (int phase : {0, 3, 1, 2}) {
     count_launches(1);
