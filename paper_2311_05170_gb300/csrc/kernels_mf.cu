@@ -161,6 +161,8 @@ __device__ __forceinline__ bool bad_val(double v) { return !(fabs(v) > 0.0) || !
 // register arrays in registers instead of sharing one allocation with every other phase.
 
 // ---------------------------------------------------------------- pivot block
+__device__ __forceinline__ float shfl_t(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_t(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 template <typename T>
 struct alignas(16) PanelSmem {
   T D[MF_NB][DS];      // the pivot block's LU (unit L below, U on and above the diagonal)
@@ -187,24 +189,20 @@ __device__ __noinline__ void pivot_block(PanelSmem<T>& S, const T* __restrict__ 
     for (int c = 0; c < MF_NB; ++c)
       if (c >= kb || lane >= kb) a[c] = (c == lane) ? T(1) : T(0);
     bool bad = false;
+    // step k: lane k's (final) row is broadcast by shuffles; the lanes below eliminate
 #pragma unroll
     for (int k = 0; k < MF_NB; ++k) {
-      if (lane == k) {
-#pragma unroll
-        for (int c = 0; c < MF_NB; ++c) S.P[c] = a[c];
-      }
-      __syncwarp();
-      const T piv = S.P[k];
+      const T piv = shfl_t(a[k], k);
       if (k < kb) bad |= bad_val(piv);
       const T rp = recip(piv);
       if (lane == 0) S.R[k] = rp;
-      if (lane > k) {
-        const T l = a[k] * rp;
-        a[k] = l;
+      const T l = a[k] * rp;
 #pragma unroll
-        for (int c = k + 1; c < MF_NB; ++c) a[c] -= l * S.P[c];
+      for (int c = k + 1; c < MF_NB; ++c) {
+        const T pc = shfl_t(a[c], k);
+        if (lane > k) a[c] -= l * pc;
       }
-      __syncwarp();
+      if (lane > k) a[k] = l;
     }
 #pragma unroll
     for (int c = 0; c < MF_NB; ++c) S.D[lane][c] = a[c];
