@@ -80,7 +80,7 @@ struct tpns_ctx {
   // group (Oseen, Darcy), and per group the height levels (offset into d_mf_big, count, max p)
   int mf_big_m = 256;
   int mf_small[2] = {0, 0};
-  std::vector<std::array<int, 3>> mf_big_levels[2];
+  std::vector<std::array<int, 4>> mf_big_levels[2];   // (offset in the list, fronts, max p, max m)
   int32_t* d_mf_big = nullptr;
   int mf_oseen_blocks = 0, mf_blocks = 0;   // pivot blocks of the Oseen fronts / of all fronts
   int64_t* d_mf_dblk = nullptr;
@@ -502,12 +502,13 @@ static tpns_status build_ctx(tpns_ctx* ctx, const tpns_mesh_desc& md, const tpns
         continue;
       }
       auto& lv = ctx->mf_big_levels[g];
-      const int p = ctx->probs[msys[keys[i].q].prob]->mf.fronts[keys[i].t].p;
+      const MFFront& BF = ctx->probs[msys[keys[i].q].prob]->mf.fronts[keys[i].t];
       if (lv.empty() || keys[i - 1].lvl != keys[i].lvl || !keys[i - 1].big || keys[i - 1].group != g ||
           lv.back()[1] >= MF_BIG_LIST)
-        lv.push_back({(int)h_big.size(), 0, 0});
+        lv.push_back({(int)h_big.size(), 0, 0, 0});
       lv.back()[1] += 1;
-      lv.back()[2] = std::max(lv.back()[2], p);
+      lv.back()[2] = std::max(lv.back()[2], BF.p);
+      lv.back()[3] = std::max(lv.back()[3], BF.m);
       h_big.push_back((int32_t)i);
     }
     for (const Key& k : keys) {
@@ -1153,7 +1154,7 @@ static tpns_status local_step(tpns_ctx* ctx) {
     ph_begin(ctx, PH_BAND_LU);
     CK(launch_mf_factor<T>(ctx->mfl, 0, ctx->mf_small[0], mfF, mfD, ctx->mf_tc, st));
     for (const auto& lv : ctx->mf_big_levels[0])
-      CK(launch_mf_big<T>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], mfF, mfD, ctx->mf_tc, st));
+      CK(launch_mf_big<T>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], lv[3], mfF, mfD, ctx->mf_tc, st));
     CK(launch_mf_dinv<T>(mfD, ctx->d_mf_dblk, ctx->mf_oseen_blocks, st));
     ph_end(ctx, PH_BAND_LU);
   } else {
@@ -1556,7 +1557,7 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
       CK(launch_mf_factor<double>(ctx->mfl, ctx->mf_oseen_fronts, ctx->mf_small[1], reinterpret_cast<double*>(ctx->d_mf_F),
                                   reinterpret_cast<double*>(ctx->d_mf_dinv), 0, st));
       for (const auto& lv : ctx->mf_big_levels[1])
-        CK(launch_mf_big<double>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], reinterpret_cast<double*>(ctx->d_mf_F),
+        CK(launch_mf_big<double>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], lv[3], reinterpret_cast<double*>(ctx->d_mf_F),
                                  reinterpret_cast<double*>(ctx->d_mf_dinv), 0, st));
       CK(launch_mf_dinv<double>(reinterpret_cast<double*>(ctx->d_mf_dinv), ctx->d_mf_dblk + ctx->mf_oseen_blocks, nb,
                                 st));
@@ -1564,7 +1565,7 @@ static tpns_status setup_factors(tpns_ctx* ctx) {
       CK(launch_mf_factor<float>(ctx->mfl, ctx->mf_oseen_fronts, ctx->mf_small[1], reinterpret_cast<float*>(ctx->d_mf_F),
                                  reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->mf_tc, st));
       for (const auto& lv : ctx->mf_big_levels[1])
-        CK(launch_mf_big<float>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], reinterpret_cast<float*>(ctx->d_mf_F),
+        CK(launch_mf_big<float>(ctx->mfl, ctx->d_mf_big + lv[0], lv[1], lv[2], lv[3], reinterpret_cast<float*>(ctx->d_mf_F),
                                 reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->mf_tc, st));
       CK(launch_mf_dinv<float>(reinterpret_cast<float*>(ctx->d_mf_dinv), ctx->d_mf_dblk + ctx->mf_oseen_blocks, nb,
                                st));

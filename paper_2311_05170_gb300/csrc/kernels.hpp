@@ -81,10 +81,11 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
 template <typename T>
 size_t mf_factor_smem(bool tc);
 // Large fronts: factor the listed fronts (one height level of the trees; their children are
-// factored) with all CTAs, pivot block by pivot block up to max_p (at most MF_BIG_LIST fronts).
+// factored) with all CTAs, pivot block by pivot block up to max_p (at most MF_BIG_LIST fronts;
+// max_m: their largest order).
 template <typename T>
-cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int max_p, T* F, T* dinv, int tc,
-                          cudaStream_t st);
+cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int max_p, int max_m, T* F, T* dinv,
+                          int tc, cudaStream_t st);
 // Inverses of the factored pivot blocks (the solves' diagonal blocks): `blocks` lists the
 // offsets of the blocks' 2 x 32 x 32 slots in dinv.
 template <typename T>

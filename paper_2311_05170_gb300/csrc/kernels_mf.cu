@@ -365,16 +365,18 @@ __device__ __forceinline__ void pack_panel(const float* __restrict__ F, int ld, 
   }
 }
 
-// One thread: the twelve products of a chunk (four K-steps of 8, each hi*hi + hi*lo + lo*hi),
-// then a commit of their completion to the mbarrier.
-__device__ __noinline__ void issue_chunk(const TcSmem& S, uint64_t* bar, bool accumulate = false) {
-  const uint32_t ah = su32(S.Ahi), al = su32(S.Alo), bh = su32(S.Bhi), bl = su32(S.Blo);
+// One thread: the twelve products of a chunk (four K-steps of 8, each hi*hi + hi*lo + lo*hi)
+// into the accumulator at tensor-memory address `tmem`, then a commit of their completion to
+// the mbarrier.
+__device__ __noinline__ void issue_chunk(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo,
+                                         uint32_t tmem, uint64_t* bar, bool accumulate = false) {
+  const uint32_t ah = su32(Ahi), al = su32(Alo), bh = su32(Bhi), bl = su32(Blo);
 #pragma unroll 1
   for (int kk = 0; kk < MF_NB / 8; ++kk) {
     const uint32_t o = kk * 256;   // 8 TF32 values = two 16-byte core matrices along K
-    tc_mma_tf32(S.tmem, sm_desc(ah + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, kk > 0 || accumulate);
-    tc_mma_tf32(S.tmem, sm_desc(ah + o, 128, 1024), sm_desc(bl + o, 128, 1024), MF_IDESC, 1);
-    tc_mma_tf32(S.tmem, sm_desc(al + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, 1);
+    tc_mma_tf32(tmem, sm_desc(ah + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, kk > 0 || accumulate);
+    tc_mma_tf32(tmem, sm_desc(ah + o, 128, 1024), sm_desc(bl + o, 128, 1024), MF_IDESC, 1);
+    tc_mma_tf32(tmem, sm_desc(al + o, 128, 1024), sm_desc(bh + o, 128, 1024), MF_IDESC, 1);
   }
   tc_commit(bar);
 }
@@ -398,7 +400,7 @@ __device__ __noinline__ void update_tc(TcSmem& S, float* __restrict__ F, int ld,
       tc_before();
       __syncthreads();
       tc_after();
-      if (tid == 0) issue_chunk(S, &S.bar);
+      if (tid == 0) issue_chunk(S.Ahi, S.Alo, S.Bhi, S.Blo, S.tmem, &S.bar);
       if (!mb_wait(&S.bar, ph) && lane == 0) atomicOr(s_flag, 2);
       ph ^= 1u;
       tc_after();
@@ -745,110 +747,212 @@ __device__ __forceinline__ BigTile big_tile(const MFFrontDev& Fd, int mode, int 
   return T;
 }
 
-// Tensor-core variant: 512 threads (16 warps: warp w reads accumulator lanes 32 (w % 4) ..
-// and columns 32 (w / 4) ..), so that more of a tile's loads are in flight; CUDA-core variant:
-// MF_THREADS (the 16 x 16 thread layout of update_tile_fma).
+// Operands of one K chunk (32 columns) of a 128 x 128 tile in the packed layout of pack_idx:
+// L21 rows (A) and U12 columns (B), each split into TF32 hi and lo parts (64 KB).
+struct TcOps {
+  float Ahi[MF_TILE * MF_NB], Alo[MF_TILE * MF_NB], Bhi[MF_CN * MF_NB], Blo[MF_CN * MF_NB];
+};
+// Shared memory of the tensor-core trailing update: two operand stages, so that the next
+// chunk is packed while the tensor core multiplies the current one, their mbarriers (each
+// receives the commits of the chunks packed into its stage) and the accumulator's address.
+struct BigUSmem {
+  TcOps op[2];
+  uint64_t bar[2];
+  uint32_t tmem;
+};
+
+// A tile of the update with the K range of its products (one chunk per pivot block)
+struct UTile {
+  float* F;
+  int ld, r0, c0, rl, cl, kc0, kc1;
+};
+__device__ __forceinline__ UTile u_tile(const MFBigArgs& A, float* Fall, const int* s_pre, int mode, int k0, int t,
+                                        int& fi) {
+  while (s_pre[fi + 1] <= t) ++fi;
+  const MFFrontDev& Fd = A.fronts[A.list[fi]];
+  const BigTile G = big_tile(Fd, mode, k0, t - s_pre[fi]);
+  UTile u;
+  u.F = Fall + Fd.f_off;
+  u.ld = Fd.ld;
+  u.r0 = G.r0; u.c0 = G.c0; u.rl = G.rl; u.cl = G.cl;
+  u.kc0 = mode == 2 ? 0 : k0;
+  u.kc1 = mode == 2 ? Fd.p : min(k0 + MF_NB, Fd.p);
+  return u;
+}
+
+// Half of one operand row or column of chunk kc (16 of its 32 values, columns kc + 16 h ..):
+// A (op 0): L21 row r0 + l, values F[kc + c, r0 + l]; B (op 1): U12 column c0 + l, values
+// F[c0 + l, kc + c].  Loads only (clamped addresses, masked afterwards), so that they stay in
+// flight while the tensor core works; entries past the tile or the pivot range are zero.
+__device__ __forceinline__ void load_half(const UTile& u, int kc, int op, int l, int h, float (&v)[16]) {
+  const int kb = min(MF_NB, u.kc1 - kc);
+  const int first = op == 0 ? u.r0 : u.c0;
+  const int valid = op == 0 ? u.rl - u.r0 : u.cl - u.c0;
+  const bool ok = l < valid;
+  const int li = ok ? l : 0;
+  const float* base = op == 0 ? u.F + (int64_t)kc * u.ld + first + li : u.F + (int64_t)(first + li) * u.ld + kc;
+  const int64_t step = op == 0 ? u.ld : 1;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int cc = 16 * h + c;
+    v[c] = base[(cc < kb ? cc : 0) * step];
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    if (!ok || 16 * h + c >= kb) v[c] = 0.f;
+}
+__device__ __forceinline__ void store_half(TcOps& O, int op, int l, int h, const float (&v)[16]) {
+  float* hi = op == 0 ? O.Ahi : O.Bhi;
+  float* lo = op == 0 ? O.Alo : O.Blo;
+#pragma unroll
+  for (int c4 = 0; c4 < 16; c4 += 4) {
+    float4 a, b;
+    a.x = tf32_rn(v[c4]); b.x = tf32_rn(v[c4] - a.x);
+    a.y = tf32_rn(v[c4 + 1]); b.y = tf32_rn(v[c4 + 1] - a.y);
+    a.z = tf32_rn(v[c4 + 2]); b.z = tf32_rn(v[c4 + 2] - a.z);
+    a.w = tf32_rn(v[c4 + 3]); b.w = tf32_rn(v[c4 + 3] - a.w);
+    *reinterpret_cast<float4*>(hi + pack_idx(l, 16 * h + c4)) = a;
+    *reinterpret_cast<float4*>(lo + pack_idx(l, 16 * h + c4)) = b;
+  }
+}
+
+// The tensor-core update of this CTA's tiles (t = blockIdx.x, + gridDim.x, ...), as one
+// sequence of K chunks: chunk g is packed into stage g % 2 once the products of chunk g - 2
+// (the stage's previous contents) have completed, one thread issues its products, and the
+// loads of chunk g + 1 are in flight while they run.  After a tile's last chunk, the epilogue
+// waits for its products and subtracts the accumulator from the tile (warp w: accumulator
+// lanes 32 (w % 4) .., columns 32 (w / 4) ..); the tile's current values were loaded while its
+// first products ran.  512 threads: thread (op, h, l) packs half of L21 row l (op 0) or of U12
+// column l (op 1).  Every wait is bounded; a wait that gives up stops the sequence (a uniform
+// decision) and sets bit 1 of the system's status.
+__device__ __forceinline__ void big_update_tc(const MFBigArgs& A, float* Fall, const int* s_pre, int k0, int mode) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  BigUSmem& S = *reinterpret_cast<BigUSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int op = tid >> 8, h = (tid >> 7) & 1, l = tid & (MF_TILE - 1);
+  const int q4 = warp & 3, hcol = warp >> 2;
+  if (tid == 0) {
+    mb_init(&S.bar[0], 1);
+    mb_init(&S.bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tm_alloc(&S.tmem, MF_TMEM_COLS);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const int total = s_pre[A.nlist];
+  int t = blockIdx.x, fi = 0, issued = 0;
+  bool stopped = false;
+  if (t < total) {
+    UTile cur = u_tile(A, Fall, s_pre, mode, k0, t, fi);
+    int kc = cur.kc0;
+    float v[16], f[32];
+    load_half(cur, kc, op, l, h, v);
+    for (;;) {
+      const int g = issued, s = g & 1;
+      // the stage's previous chunk (g - 2) has been multiplied
+      const bool free_ok = g < 2 || mb_wait(&S.bar[s], ((g - 2) >> 1) & 1);
+      store_half(S.op[s], op, l, h, v);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_before();
+      stopped = __syncthreads_or(!free_ok);
+      tc_after();
+      if (stopped) break;
+      const bool first = kc == cur.kc0, last = kc + MF_NB >= cur.kc1;
+      if (tid == 0) issue_chunk(S.op[s].Ahi, S.op[s].Alo, S.op[s].Bhi, S.op[s].Blo, S.tmem, &S.bar[s], !first);
+      ++issued;
+      const int r = cur.r0 + 32 * q4 + lane, cb = cur.c0 + 32 * hcol;
+      const int rr = r < cur.rl ? r : cur.rl - 1;
+      if (first) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) f[c] = cur.F[(int64_t)(cb + c < cur.cl ? cb + c : cur.cl - 1) * cur.ld + rr];
+      }
+      // the next chunk: the tile's next 32 pivot columns, or the first chunk of the next tile
+      UTile nxt = cur;
+      int nkc = kc + MF_NB;
+      bool more = true;
+      if (last) {
+        t += gridDim.x;
+        more = t < total;
+        if (more) {
+          nxt = u_tile(A, Fall, s_pre, mode, k0, t, fi);
+          nkc = nxt.kc0;
+        }
+      }
+      if (more) load_half(nxt, nkc, op, l, h, v);
+      if (last) {
+        const bool ok = mb_wait(&S.bar[s], (g >> 1) & 1);
+        tc_after();
+        if (cur.r0 + 32 * q4 < cur.rl && cb < cur.cl) {   // warp-uniform
+          const uint32_t base = S.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(32 * hcol);
+#pragma unroll
+          for (int h16 = 0; h16 < 2; ++h16) {
+            const int cb2 = cb + 16 * h16;
+            uint32_t d[16];
+            tm_ld16(base + (uint32_t)(16 * h16), d);
+            tm_wait_ld();
+            if (r < cur.rl) {
+#pragma unroll
+              for (int c = 0; c < 16; ++c)
+                if (cb2 + c < cur.cl) cur.F[(int64_t)(cb2 + c) * cur.ld + r] = f[16 * h16 + c] - __uint_as_float(d[c]);
+            }
+          }
+        }
+        // the accumulator is free for the next tile
+        tc_before();
+        stopped = __syncthreads_or(!ok);
+        tc_after();
+        if (stopped) break;
+      }
+      if (!more) break;
+      cur = nxt;
+      kc = nkc;
+    }
+  }
+  // products still in flight (only after a wait gave up) complete before the accumulator is
+  // released
+  if (issued > 0 && !mb_wait(&S.bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1)) stopped = true;
+  tc_before();
+  __syncthreads();
+  tc_after();
+  if (warp == 0) tm_dealloc(S.tmem, MF_TMEM_COLS);
+  if (tid == 0 && stopped) atomicOr(&A.status[A.sys[A.fronts[A.list[0]].sys].sid], 2);
+}
+
+// Tensor-core variant (FP32 fronts): big_update_tc, 512 threads; CUDA-core variant: MF_THREADS
+// (the 16 x 16 thread layout of update_tile_fma), one tile after another.
 constexpr int MF_BIG_UTHREADS = 512;
 template <typename T, bool TC>
 __global__ void __launch_bounds__(TC ? MF_BIG_UTHREADS : MF_THREADS, 1)
     mf_big_update_kernel(MFBigArgs A, T* __restrict__ Fall, int k0, int mode) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int s_pre[MF_BIG_LIST + 1];
-  __shared__ int s_flag;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     int acc = 0;
     for (int i = 0; i < A.nlist; ++i) {
       s_pre[i] = acc;
       acc += big_tiles(A.fronts[A.list[i]], mode, k0);
     }
     s_pre[A.nlist] = acc;
-    s_flag = 0;
-  }
-  TcSmem& TS = *reinterpret_cast<TcSmem*>(smem_raw);
-  unsigned ph = 0;
-  if constexpr (TC) {
-    if (tid == 0) {
-      mb_init(&TS.bar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) tm_alloc(&TS.tmem, MF_TMEM_COLS);
-    tc_before();
   }
   __syncthreads();
-  if constexpr (TC) tc_after();
-  const int total = s_pre[A.nlist];
-  int fi = 0;
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    while (s_pre[fi + 1] <= t) ++fi;
-    const MFFrontDev& Fd = A.fronts[A.list[fi]];
-    T* F = Fall + Fd.f_off;
-    const int ld = Fd.ld;
-    const BigTile G = big_tile(Fd, mode, k0, t - s_pre[fi]);
-    // K chunks: the pivot block (mode 1) or all pivot blocks (mode 2)
-    const int kc0 = mode == 2 ? 0 : k0;
-    const int kc1 = mode == 2 ? Fd.p : min(k0 + MF_NB, Fd.p);
-    if constexpr (TC) {
-      if (s_flag & 2) break;   // a bounded wait gave up: issue no further products
-      const int nr = min(MF_TILE, G.rl - G.r0), nc = min(MF_CN, G.cl - G.c0);
-      float* Ff = reinterpret_cast<float*>(F);
-      const int q4 = warp & 3, hcol = warp >> 2;
-      const int r = G.r0 + 32 * q4 + lane;
-      const int cb = G.c0 + 32 * hcol;
-      const int rr = r < G.rl ? r : G.rl - 1;
-      float f[32];
-      for (int kc = kc0; kc < kc1; kc += MF_NB) {
-        const int kb = min(MF_NB, kc1 - kc);
-        if (tid < MF_TILE) pack_panel(Ff, ld, kc, kb, G.r0, nr, true, tid, TS.Ahi, TS.Alo);
-        else if (tid - MF_TILE < MF_CN) pack_panel(Ff, ld, kc, kb, G.c0, nc, false, tid - MF_TILE, TS.Bhi, TS.Blo);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_before();
-        __syncthreads();
-        tc_after();
-        if (tid == 0) issue_chunk(TS, &TS.bar, kc > kc0);
-        if (kc == kc0) {
-          // the tile's current values are loaded while the first products run (clamped addresses)
-#pragma unroll
-          for (int c = 0; c < 32; ++c) f[c] = Ff[(int64_t)(cb + c < G.cl ? cb + c : G.cl - 1) * ld + rr];
-        }
-        if (!mb_wait(&TS.bar, ph) && lane == 0) atomicOr(&s_flag, 2);
-        ph ^= 1u;
-        tc_after();
-        tc_before();
-        __syncthreads();   // operands are free again
-        tc_after();
-      }
-      if (G.r0 + 32 * q4 < G.rl && cb < G.cl) {
-        const uint32_t base = TS.tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(32 * hcol);
-#pragma unroll
-        for (int h16 = 0; h16 < 2; ++h16) {
-          const int cb2 = cb + 16 * h16;
-          uint32_t d[16];
-          tm_ld16(base + (uint32_t)(16 * h16), d);
-          tm_wait_ld();
-          if (r < G.rl) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-              if (cb2 + c < G.cl) Ff[(int64_t)(cb2 + c) * ld + r] = f[16 * h16 + c] - __uint_as_float(d[c]);
-          }
-        }
-      }
-      tc_before();
-      __syncthreads();
-      tc_after();
-    } else {
-      T* As = reinterpret_cast<T*>(smem_raw);
-      for (int kc = kc0; kc < kc1; kc += MF_NB)
-        update_tile_fma<T>(F, ld, G.rl, kc, min(MF_NB, kc1 - kc), G.r0, G.c0, As, As + MF_NB * (MF_TILE + 4),
-                           G.cl);
-    }
-  }
   if constexpr (TC) {
-    tc_before();
-    __syncthreads();
-    tc_after();
-    if (warp == 0) tm_dealloc(TS.tmem, MF_TMEM_COLS);
-    if (tid == 0 && (s_flag & 2)) atomicOr(&A.status[A.sys[A.fronts[A.list[0]].sys].sid], 2);
+    big_update_tc(A, reinterpret_cast<float*>(Fall), s_pre, k0, mode);
+  } else {
+    const int total = s_pre[A.nlist];
+    int fi = 0;
+    T* As = reinterpret_cast<T*>(smem_raw);
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      while (s_pre[fi + 1] <= t) ++fi;
+      const MFFrontDev& Fd = A.fronts[A.list[fi]];
+      const BigTile G = big_tile(Fd, mode, k0, t - s_pre[fi]);
+      // K chunks: the pivot block (mode 1) or all pivot blocks (mode 2)
+      const int kc0 = mode == 2 ? 0 : k0;
+      const int kc1 = mode == 2 ? Fd.p : min(k0 + MF_NB, Fd.p);
+      for (int kc = kc0; kc < kc1; kc += MF_NB)
+        update_tile_fma<T>(Fall + Fd.f_off, Fd.ld, G.rl, kc, min(MF_NB, kc1 - kc), G.r0, G.c0, As,
+                           As + MF_NB * (MF_TILE + 4), G.cl);
+    }
   }
 }
 
@@ -1175,8 +1279,8 @@ cudaError_t launch_mf_solve(const MFLaunch& L, const T* F, const T* dinv, const 
 }
 
 template <typename T>
-cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int max_p, T* F, T* dinv, int tc,
-                          cudaStream_t st) {
+cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int max_p, int max_m, T* F, T* dinv,
+                          int tc, cudaStream_t st) {
   if (nlist <= 0) return cudaSuccess;
   if (nlist > MF_BIG_LIST) return cudaErrorInvalidValue;
   MFBigArgs A{L.sys, L.fronts, list, nlist, L.relmap, L.colptr, L.orig_k, L.orig_ij, L.vals, L.status};
@@ -1185,9 +1289,7 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  // CTAs per front for the assembly and the row-parallel panels: enough to cover the device
-  // several times (every CTA of a front repeats the small pivot-block factorisation)
-  const int per = std::max(1, std::min(64, (8 * nsm + nlist - 1) / nlist));
+  // CTAs per front for the assembly passes: enough to cover the device several times
   const int per_asm = std::max(1, std::min(256, (8 * nsm + nlist - 1) / nlist));
   for (int phase : {0, 3, 1, 2}) {
     count_launches(1);
@@ -1195,13 +1297,17 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const bool use_tc = tc && sizeof(T) == 4;
-  const size_t smem = use_tc ? sizeof(TcSmem) : (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T);
+  const size_t smem = use_tc ? sizeof(BigUSmem) : (size_t)2 * MF_NB * (MF_TILE + 4) * sizeof(T);
   auto ufn = use_tc ? mf_big_update_kernel<T, true> : mf_big_update_kernel<T, false>;
   const int uthreads = use_tc ? MF_BIG_UTHREADS : MF_THREADS;
   e = cudaFuncSetAttribute(ufn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int ugrid = mf_grid((const void*)ufn, smem, L.grid_cap, uthreads);
   for (int k0 = 0; k0 < max_p; k0 += MF_NB) {
+    // CTAs per front for the panel: one L21 row or U12 column per thread at most (every CTA
+    // of a front repeats the pivot-block factorisation, so no more CTAs than that)
+    const int rows = 2 * std::max(0, max_m - k0);
+    const int per = std::max(1, std::min(64, (rows + MF_THREADS - 1) / MF_THREADS));
     count_launches(1);
     mf_big_panel_kernel<T><<<dim3(per, nlist), MF_THREADS, 0, st>>>(A, F, dinv, k0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1220,7 +1326,7 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
   template size_t mf_factor_smem<T>(bool);                                                                  \
   template cudaError_t launch_mf_factor<T>(const MFLaunch&, int, int, T*, T*, int, cudaStream_t);          \
   template cudaError_t launch_mf_dinv<T>(T*, const int64_t*, int, cudaStream_t);                            \
-  template cudaError_t launch_mf_big<T>(const MFLaunch&, const int32_t*, int, int, T*, T*, int, cudaStream_t); \
+  template cudaError_t launch_mf_big<T>(const MFLaunch&, const int32_t*, int, int, int, T*, T*, int, cudaStream_t); \
   template cudaError_t launch_mf_solve<T>(const MFLaunch&, const T*, const T*, const double*, double*, int, \
                                           const int*, T*, T*, T*, int, cudaStream_t);
 TPNS_MF_INST(float)
