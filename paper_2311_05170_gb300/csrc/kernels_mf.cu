@@ -707,42 +707,78 @@ __global__ void __launch_bounds__(MF_THREADS) mf_big_panel_kernel(MFBigArgs A, T
                 blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-// Trailing updates of the listed fronts (with p > k0), in 128 x 128 tiles taken round robin
-// by the CTAs.  mode 1, pivot block k0 (K = its 32 columns): only the strips the next pivot
-// blocks need, rows [k1, m) x columns [k1, p) and rows [k1, p) x columns [p, m).  mode 2, after
-// the last pivot block: the Schur block [p, m) x [p, m) once, K = p (the products of all pivot
-// blocks accumulate in tensor memory, or in registers on the CUDA-core path).
+// Trailing updates of the listed fronts, in 128 x 128 tiles taken round robin by the CTAs.
+// The pivot columns [0, p) go in groups of MF_BIG_GROUP (a group [gs, ge), ge = min(gs +
+// MF_BIG_GROUP, p)); for entries outside the Schur block the updates of a group are applied
+// together once the group is factored, so that the trailing region is rewritten once per
+// group instead of once per pivot block:
+//   mode 1, pivot block k0 of group [gs, ge) (K = its 32 columns, k1 = k0 + 32): only the
+//     group's own panels, rows [k1, m) x columns [k1, ge) and rows [k1, ge) x columns [ge, m);
+//   mode 3, after the last pivot block of group [gs, ge) (K = the group's columns): the
+//     entries the later pivot blocks need, rows [ge, m) x columns [ge, p) and rows [ge, p) x
+//     columns [p, m);
+//   mode 2, after the last pivot block (K = p): the Schur block [p, m) x [p, m) once (the
+//     products of all pivot blocks accumulate in tensor memory, or in registers on the
+//     CUDA-core path).
+// Every entry thus receives the product of each earlier pivot block exactly once before it is
+// read by a panel (the blocked right-looking LU with a two-level panel).
+constexpr int MF_BIG_GROUP = 4 * MF_NB;
 struct BigTile {
   int r0, c0, rl, cl;   // tile origin, row / column limits
 };
+__device__ __forceinline__ int ceil_tiles(int n) { return n > 0 ? (n + MF_TILE - 1) / MF_TILE : 0; }
+// K range [kc0, kc1) of the products of a tile
+__device__ __forceinline__ void big_krange(const MFFrontDev& Fd, int mode, int k0, int& kc0, int& kc1) {
+  if (mode == 2) {
+    kc0 = 0;
+    kc1 = Fd.p;
+  } else if (mode == 1) {
+    kc0 = k0;
+    kc1 = min(k0 + MF_NB, Fd.p);
+  } else {
+    kc0 = (k0 / MF_BIG_GROUP) * MF_BIG_GROUP;
+    kc1 = min(kc0 + MF_BIG_GROUP, Fd.p);
+  }
+}
 __device__ __forceinline__ int big_tiles(const MFFrontDev& Fd, int mode, int k0) {
   const int p = Fd.p, m = Fd.m;
-  if (mode == 2) {
-    const int nt = (m - p + MF_TILE - 1) / MF_TILE;
-    return m > p ? nt * nt : 0;
-  }
+  if (mode == 2) return m > p ? ceil_tiles(m - p) * ceil_tiles(m - p) : 0;
   if (k0 >= p) return 0;
-  const int k1 = min(k0 + MF_NB, p);
-  if (k1 >= p) return 0;
-  const int a = (m - k1 + MF_TILE - 1) / MF_TILE, b = (p - k1 + MF_TILE - 1) / MF_TILE;
-  const int c = (m - p + MF_TILE - 1) / MF_TILE;
-  return a * b + b * c;
+  const int ge = min((k0 / MF_BIG_GROUP) * MF_BIG_GROUP + MF_BIG_GROUP, p);
+  if (mode == 1) {
+    const int k1 = min(k0 + MF_NB, p);
+    if (k1 >= ge) return 0;
+    return ceil_tiles(m - k1) + ceil_tiles(m - ge);   // ge - k1 < MF_TILE: one tile column / row
+  }
+  if (ge >= p) return 0;
+  const int b = ceil_tiles(p - ge);
+  return ceil_tiles(m - ge) * b + b * ceil_tiles(m - p);
 }
 __device__ __forceinline__ BigTile big_tile(const MFFrontDev& Fd, int mode, int k0, int tl) {
   const int p = Fd.p, m = Fd.m;
   BigTile T;
   if (mode == 2) {
-    const int nt = (m - p + MF_TILE - 1) / MF_TILE;
+    const int nt = ceil_tiles(m - p);
     T.r0 = p + (tl % nt) * MF_TILE; T.c0 = p + (tl / nt) * MF_TILE; T.rl = m; T.cl = m;
     return T;
   }
-  const int k1 = min(k0 + MF_NB, p);
-  const int a = (m - k1 + MF_TILE - 1) / MF_TILE, b = (p - k1 + MF_TILE - 1) / MF_TILE;
+  const int ge = min((k0 / MF_BIG_GROUP) * MF_BIG_GROUP + MF_BIG_GROUP, p);
+  if (mode == 1) {
+    const int k1 = min(k0 + MF_NB, p);
+    const int a = ceil_tiles(m - k1);
+    if (tl < a) {
+      T.r0 = k1 + tl * MF_TILE; T.c0 = k1; T.rl = m; T.cl = ge;
+    } else {
+      T.r0 = k1; T.c0 = ge + (tl - a) * MF_TILE; T.rl = ge; T.cl = m;
+    }
+    return T;
+  }
+  const int a = ceil_tiles(m - ge), b = ceil_tiles(p - ge);
   if (tl < a * b) {
-    T.r0 = k1 + (tl % a) * MF_TILE; T.c0 = k1 + (tl / a) * MF_TILE; T.rl = m; T.cl = p;
+    T.r0 = ge + (tl % a) * MF_TILE; T.c0 = ge + (tl / a) * MF_TILE; T.rl = m; T.cl = p;
   } else {
     tl -= a * b;
-    T.r0 = k1 + (tl % b) * MF_TILE; T.c0 = p + (tl / b) * MF_TILE; T.rl = p; T.cl = m;
+    T.r0 = ge + (tl % b) * MF_TILE; T.c0 = p + (tl / b) * MF_TILE; T.rl = p; T.cl = m;
   }
   return T;
 }
@@ -775,8 +811,7 @@ __device__ __forceinline__ UTile u_tile(const MFBigArgs& A, float* Fall, const i
   u.F = Fall + Fd.f_off;
   u.ld = Fd.ld;
   u.r0 = G.r0; u.c0 = G.c0; u.rl = G.rl; u.cl = G.cl;
-  u.kc0 = mode == 2 ? 0 : k0;
-  u.kc1 = mode == 2 ? Fd.p : min(k0 + MF_NB, Fd.p);
+  big_krange(Fd, mode, k0, u.kc0, u.kc1);
   return u;
 }
 
@@ -946,9 +981,8 @@ __global__ void __launch_bounds__(TC ? MF_BIG_UTHREADS : MF_THREADS, 1)
       while (s_pre[fi + 1] <= t) ++fi;
       const MFFrontDev& Fd = A.fronts[A.list[fi]];
       const BigTile G = big_tile(Fd, mode, k0, t - s_pre[fi]);
-      // K chunks: the pivot block (mode 1) or all pivot blocks (mode 2)
-      const int kc0 = mode == 2 ? 0 : k0;
-      const int kc1 = mode == 2 ? Fd.p : min(k0 + MF_NB, Fd.p);
+      int kc0, kc1;
+      big_krange(Fd, mode, k0, kc0, kc1);
       for (int kc = kc0; kc < kc1; kc += MF_NB)
         update_tile_fma<T>(Fall + Fd.f_off, Fd.ld, G.rl, kc, min(MF_NB, kc1 - kc), G.r0, G.c0, As,
                            As + MF_NB * (MF_TILE + 4), G.cl);
@@ -1312,8 +1346,11 @@ cudaError_t launch_mf_big(const MFLaunch& L, const int32_t* list, int nlist, int
     mf_big_panel_kernel<T><<<dim3(per, nlist), MF_THREADS, 0, st>>>(A, F, dinv, k0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (k0 + MF_NB < max_p) {   // the last pivot block leaves nothing for the next one
+      // within a group: its own panels; after its last pivot block: the rest of the trailing
+      // region but the Schur block (the group's panels are then complete)
+      const int mode = (k0 + MF_NB) % MF_BIG_GROUP == 0 ? 3 : 1;
       count_launches(1);
-      ufn<<<ugrid, uthreads, smem, st>>>(A, F, k0, 1);
+      ufn<<<ugrid, uthreads, smem, st>>>(A, F, k0, mode);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
