@@ -509,7 +509,7 @@ def main():
             "mf_factor": {"bound": "tensor", "achieved": f_tf, "peak": tf32_peak, "unit": "TFLOP/s",
                           "frac": f_tf / tf32_peak, "ms_per_step": f_ms, "flops_per_step": st3["band_lu_flops"],
                           "fronts": st3["mf_fronts"],
-                          "note": "fronts of order >= 768 and their ancestors factored by all CTAs per tree level"},
+                          "note": "fronts of order >= 256 and their ancestors factored by all CTAs per tree level"},
             "solves": {**hbm(sb3, p3["solve"])},
             "ir": {"iters_max": st3["last_ir_iters_max"], "relres_max": st3["last_ir_relres_max"]},
             "config": {"oseen_unknowns": st3["oseen_unknowns"], "oseen_nnz": st3["oseen_nnz"],
