@@ -525,7 +525,8 @@ __device__ __forceinline__ void row_update(T (&acc)[W], LF lf, const T* __restri
 
 // Tensor-core trailing update (TPNS_TF32_IR): mma.sync m16n8k8 with TF32 operands and FP32
 // accumulation; each operand is split as x = hi + lo (hi, lo TF32) and the product taken as
-// hi*hi + hi*lo + lo*hi, which keeps the update close to FP32 accuracy.
+// hi*hi + hi*lo + lo*hi, which keeps the update close to FP32 accuracy (the error-compensated
+// split of Ootomo and Yokota, 2022).
 __device__ __forceinline__ unsigned to_tf32(float x) {
   unsigned r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));

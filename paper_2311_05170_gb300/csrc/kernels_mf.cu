@@ -12,16 +12,25 @@
 //   assembly   every column: zero, the CSR values the front owns, then the Schur
 //              complements of the children added column by column (extend-add), one warp
 //              per column, children in a fixed order: no atomics, deterministic;
-//   panel k    warp 0 factors the 32 x 32 pivot block (shuffles), two warps form the
-//              inverses of its unit-lower and upper triangles, then all threads form
-//              L21 = A21 U11^{-1} and U12 = L11^{-1} A12 in place;
-//   update k   A22 -= L21 U12.  FP32 fronts: 256 x 256 chunks; the threads write both
+//   panel k    warp 0 factors the 32 x 32 pivot block (pivot rows broadcast by shuffles),
+//              then all threads form L21 = A21 U11^{-1} and U12 = L11^{-1} A12 in place by
+//              substitution (the inverses of the blocks' triangles, which only the solves
+//              use, are formed afterwards for all blocks at once);
+//   update k   A22 -= L21 U12.  FP32 fronts: 128 x 128 chunks; the threads write both
 //              operands into shared memory as core-matrix tiles with every value split into
 //              two TF32 parts, one thread issues tcgen05.mma kind::tf32 (hi*hi + hi*lo +
-//              lo*hi, FP32 accumulation) into four 128 x 128 tensor-memory accumulators, and
-//              all warps read them back with tcgen05.ld and subtract them from the front.
-//              FP64 fronts (and FP32 fronts on request) use a CUDA-core tile product.
+//              lo*hi, FP32 accumulation: the error-compensated split of Ootomo and Yokota,
+//              2022, which keeps the product close to FP32 accuracy) into a 128 x 128
+//              tensor-memory accumulator, and all warps read it back with tcgen05.ld and
+//              subtract it from the front.  FP64 fronts (and FP32 fronts on request) use a
+//              CUDA-core tile product.
 // The Schur complement left in a front's trailing block is consumed by its parent.
+//
+// Large fronts (order >= a threshold, and their ancestors) are left out of that launch and
+// factored afterwards by all CTAs together, one tree level at a time: flat assembly passes,
+// then per pivot block a panel launch and a tile-parallel update launch (the trailing
+// updates of every four pivot blocks grouped, the Schur block updated once with all pivot
+// columns).
 //
 // Solves (one pass of iterative refinement), one launch with the same scheduling: the
 // forward tasks in that order (a front waits for its children: right-hand side plus the
