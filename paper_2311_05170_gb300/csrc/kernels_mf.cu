@@ -59,6 +59,7 @@ constexpr int MF_CN = MF_TILE;             // columns of one tensor-core update 
 constexpr int MF_TMEM_COLS = MF_CN;        // one 128 x 128 FP32 accumulator
 constexpr int MF_SMEM = 226 * 1024;        // dynamic shared memory of the factorisation (near the opt-in maximum)
 constexpr int DS = MF_NB + 1;              // padded stride of the 32 x 32 shared tiles
+constexpr int DSV = MF_NB + 4;             // row stride of the pivot block in shared memory (16-byte rows)
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -174,7 +175,7 @@ __device__ __forceinline__ float shfl_t(float v, int src) { return __shfl_sync(0
 __device__ __forceinline__ double shfl_t(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 template <typename T>
 struct alignas(16) PanelSmem {
-  T D[MF_NB][DS];      // the pivot block's LU (unit L below, U on and above the diagonal)
+  T D[MF_NB][DSV];     // the pivot block's LU (unit L below, U on and above the diagonal)
   T R[MF_NB];          // reciprocals of the pivots
   T P[MF_NB];          // the pivot row being broadcast
 };
@@ -234,9 +235,21 @@ __device__ __forceinline__ void put_split(float* hi, float* lo, int l, const flo
 }
 __device__ __forceinline__ void put_split(float*, float*, int, const double (&)[MF_NB]) {}
 
+// Four consecutive entries of a 16-byte-aligned row of the pivot block in shared memory (all
+// threads of a warp read the same address: one broadcast vector load)
+__device__ __forceinline__ void ld4(const float* p, float (&d)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&d)[4]) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+  d[0] = v0.x; d[1] = v0.y; d[2] = v1.x; d[3] = v1.y;
+}
+
 // L rows r in [k1, m): F[r, k0:k0+kb] <- F[r, k0:k0+kb] U11^{-1}; U columns c in [k1, m):
-// F[k0:k0+kb, c] <- L11^{-1} F[k0:k0+kb, c], by substitution with the factored pivot block.
-// One thread per row or column.  With `pk`
+// F[k0:k0+kb, c] <- L11^{-1} F[k0:k0+kb, c], by substitution with the factored pivot block,
+// which both read by rows (U's rows for the L rows, L's rows for the U columns), four entries
+// at a time.  One thread per row or column.  With `pk`
 // (FP32 tensor-core path) the first 128 rows and 256 columns also go straight into the
 // packed operand tiles of the first update chunk.
 // The rows / columns handled by a thread are q_first, q_first + q_step, ... (default: this
@@ -262,15 +275,39 @@ __device__ __noinline__ void panel_lu(const PanelSmem<T>& S, T* __restrict__ F, 
 #pragma unroll
     for (int c = 0; c < MF_NB; ++c)
       if (c >= kb) a[c] = T(0);
-    // row: solve l U11 = a (l_c = a_c / u_cc, then a_c' -= l_c u_cc' for c' > c);
-    // column: solve L11 u = a (unit diagonal: u_c = a_c, then a_c' -= l_c'c u_c)
     T o[MF_NB];
+    if (row) {
+      // l U11 = a: l_c = a_c / u_cc, then a_c' -= l_c u_cc' for c' > c (row c of U)
 #pragma unroll
-    for (int c = 0; c < MF_NB; ++c) {
-      const T v = row ? a[c] * S.R[c] : a[c];
-      o[c] = v;
+      for (int c = 0; c < MF_NB; ++c) {
+        const T v = a[c] * S.R[c];
+        o[c] = v;
 #pragma unroll
-      for (int c2 = c + 1; c2 < MF_NB; ++c2) a[c2] -= v * (row ? S.D[c][c2] : S.D[c2][c]);
+        for (int c4 = (c + 1) & ~3; c4 < MF_NB; c4 += 4) {
+          T d[4];
+          ld4(&S.D[c][c4], d);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (c4 + j > c) a[c4 + j] -= v * d[j];
+        }
+      }
+    } else {
+      // L11 u = a (unit diagonal): u_c = a_c - l_c0 u_0 - l_c1 u_1 - ... (row c of L; the
+      // terms are taken in the order of the column-oriented elimination, so the rounding is
+      // the same)
+#pragma unroll
+      for (int c = 0; c < MF_NB; ++c) {
+        T acc = a[c];
+#pragma unroll
+        for (int c4 = 0; c4 < c; c4 += 4) {
+          T d[4];
+          ld4(&S.D[c][c4], d);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (c4 + j < c) acc -= d[j] * o[c4 + j];
+        }
+        o[c] = acc;
+      }
     }
     if (row) {
 #pragma unroll
@@ -694,7 +731,7 @@ __global__ void __launch_bounds__(MF_THREADS) mf_big_assemble_kernel(MFBigArgs A
 // slot for mf_dinv_kernel) and the substitutions of L21 rows / U12 columns, spread over the
 // CTAs of the front
 template <typename T>
-__global__ void __launch_bounds__(MF_THREADS) mf_big_panel_kernel(MFBigArgs A, T* __restrict__ Fall,
+__global__ void __launch_bounds__(MF_THREADS, 2) mf_big_panel_kernel(MFBigArgs A, T* __restrict__ Fall,
                                                                   T* __restrict__ dinv, int k0) {
   __shared__ PanelSmem<T> P;
   __shared__ int s_flag;
