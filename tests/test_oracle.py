@@ -1,7 +1,8 @@
 """Pins of the CPU oracle against facts fixed by the paper and by mathematics
 (quadrature exactness, element invariants, the strong form of Sec. 2, exact reproduction
 of P2/P1 fields, H = h, a brute-force global Newton step, closed-form interface sums,
-discrete mass balance, and the convergence rates of Theorem 5.4 / Table T1), and checks
+discrete mass balance, the error norms in closed form, and the convergence rates of
+Theorem 5.4 / Table T1), and checks
 that planted mistakes in the oracle (a dropped or transposed convection term, a flipped
 coupling sign, a wrong exchange coefficient, a wrong Beavers-Joseph-Saffman edge mass,
 unnormalised glue weights, a misordered P2 basis in the prolongation) break the pins meant
@@ -477,3 +478,30 @@ def test_algorithm3_approaches_algorithm1_as_H_shrinks():
     for k in diffs[0]:
         assert diffs[0][k] > 3.0 * diffs[1][k], k
         assert diffs[1][k] < max(e1[k], e3[k]), k
+
+
+# ------------------------------------------------------------------ error norms
+def test_error_norms_match_closed_forms():
+    """The error norms the rate test reads (velocity H1 and L2, pressure L2, Darcy L2 and
+    H1): zero for the exact polynomial patch field, and for fields shifted by a constant or
+    a linear function the closed forms over the unit-area regions (fluid [0,1]x[1,2], porous
+    [0,1]^2): a constant c in a pressure gives an L2 error |c|; a*x added to u_x gives an H1
+    seminorm |a| and an L2 norm |a|/sqrt(3); b*y added to p_F gives an H1 seminorm |b| and an
+    L2 norm |b|/sqrt(3)."""
+    o = TwoGridOracle(W.config_patch(nx_coarse=2, r=3, nsub=(1, 1), nsteps=1))
+    o.fine = o.exact_fine()
+    base = o.errors()
+    assert set(base) == {"u_H1", "u_L2", "p_L2", "pF_L2", "pF_H1", "pf_L2", "pf_H1", "pm_L2", "pm_H1"}
+    assert max(base.values()) < 1e-12, base
+    a, c, b, d = 0.7, -0.3, 1.9, 0.45
+    f = o.exact_fine()
+    f["ux"] = f["ux"] + a * o.mch.node[:, 0]
+    f["p"] = f["p"] + c
+    f["pF"] = f["pF"] + b * o.mph.node[:, 1]
+    f["pm"] = f["pm"] + d
+    o.fine = f
+    e = o.errors()
+    expect = {"u_H1": abs(a), "u_L2": abs(a) / math.sqrt(3.0), "p_L2": abs(c), "pF_L2": abs(b) / math.sqrt(3.0),
+              "pF_H1": abs(b), "pf_L2": 0.0, "pf_H1": 0.0, "pm_L2": abs(d), "pm_H1": 0.0}
+    for k, v in expect.items():
+        assert abs(e[k] - v) < 1e-12, (k, e[k], v)
