@@ -250,6 +250,45 @@ def ndofs_of(st):
     return st["n_fine_dofs"]
 
 
+def issued_tensor_flops(solver, big_m=256):
+    """Tensor-core flops the FP32 factorisation of one step issues, padding included: each 32-
+    column K chunk of a 128 x 128 update tile is twelve M = N = 128, K = 8 TF32 products
+    (hi*hi + hi*lo + lo*hi), whatever part of the tile is inside the front.  Small fronts
+    (one CTA each): after every pivot block, the whole trailing matrix in 128 x 128 tiles.
+    Large fronts (order >= big_m, and their ancestors): the tile schedule of the large-front
+    path (within a group of four pivot blocks, the group's own panels with one chunk; after
+    the group, the trailing strips with the group's chunks; the Schur block once with all
+    pivot columns).  None when the context has no multifrontal Oseen systems."""
+    tile, nb, group = 128, 32, 128
+    chunk = 12 * 2 * 128 * 128 * 8
+    nt = lambda n: -(-n // tile) if n > 0 else 0
+    total, j = 0, 0
+    while True:
+        info = solver.front_table(j)
+        if info is None:
+            break
+        big = [False] * len(info)
+        for t, (m, p, _lv, _par, nch, c0, c1) in enumerate(info.tolist()):
+            big[t] = m >= big_m or (nch > 0 and big[c0]) or (nch > 1 and big[c1])
+            for k0 in range(0, p, nb):
+                k1 = min(k0 + nb, p)
+                if not big[t]:
+                    total += nt(m - k1) ** 2 * chunk
+                    continue
+                gs = (k0 // group) * group
+                ge = min(gs + group, p)
+                if (k0 + nb) % group:
+                    if k1 < ge:
+                        total += (nt(m - k1) + nt(m - ge)) * chunk
+                elif ge < p:
+                    b = nt(p - ge)
+                    total += (nt(m - ge) * b + b * nt(m - p)) * chunk * (-(-(ge - gs) // nb))
+            if big[t] and m > p:
+                total += nt(m - p) ** 2 * chunk * (-(-p // nb))
+        j += 1
+    return total if j > 0 else None
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -346,6 +385,12 @@ def main():
     s, ms, launches, clocks, phases, f = timed_hot(args.precision, with_phases=True)
     launches = int(sum_over_ranks(launches, dist is not None, device="cuda"))   # the whole job's
     st = s.stats()
+    issued = None
+    if args.precision == "fp32":
+        try:
+            issued = issued_tensor_flops(s)
+        except Exception:
+            issued = None
     # both fields were read after the same Wm + K steps
     rel = {k: float(np.linalg.norm(f[k] - f64[k]) / np.linalg.norm(f64[k])) for k in f}
     # other factorisations of the local Oseen systems, same steps, error against the FP64 fields
@@ -394,6 +439,14 @@ def main():
     darcy_bytes = 8 * st["darcy_unknowns"] + 544 * st["darcy_elements"]
     glue_bytes = 24 * ndofs
 
+    def issued_entry(flops, ms_, peak):
+        """Tensor-core flops actually issued per step and their rate over the phase time (the
+        tensor pipe's busy share during the factorisation, if it ran at the TF32 peak)."""
+        if not flops:
+            return {}
+        tf = flops / (ms_ / 1e3) / 1e12
+        return {"issued_tensor_flops_per_step": flops, "issued_tflops": tf, "issued_frac_of_peak": tf / peak}
+
     def hbm(bytes_, ms_):
         gbs = bytes_ / (ms_ / 1e3) / 1e9
         return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
@@ -403,7 +456,8 @@ def main():
                       "frac": lu_tflops / tf32_peak, "ms_per_step": lu_ms,
                       "flops_per_step": st["band_lu_flops"], "fronts": st["mf_fronts"],
                       "note": "algorithmic flops of the nested-dissection partial factorisations; the "
-                              "trailing updates issue 3 TF32 products per multiply-add (split operands)"},
+                              "trailing updates issue 3 TF32 products per multiply-add (split operands)",
+                      **issued_entry(issued, lu_ms, tf32_peak)},
         "solves": {**hbm(solve_bytes_step, ph["solve"]), "launches_per_step": phn["solve"] / K},
         "oseen_assembly": {**hbm(asm_bytes, ph["asm_oseen"] + ph["scatter"]),
                            "limiter": "FP64 pipe (ncu: 83 % active in the element kernel; DRAM 0.6 %)"},
@@ -487,6 +541,11 @@ def main():
                 ph3["_solve_bytes"] = sb
                 s3.set_timing(False)
             st3 = s3.stats()
+            if with_phases and prec == "fp32":
+                try:
+                    st3["_issued"] = issued_tensor_flops(s3)
+                except Exception:
+                    st3["_issued"] = None
             s3.close()
             return ms3, f3, ph3, st3
 
@@ -509,7 +568,8 @@ def main():
             "mf_factor": {"bound": "tensor", "achieved": f_tf, "peak": tf32_peak, "unit": "TFLOP/s",
                           "frac": f_tf / tf32_peak, "ms_per_step": f_ms, "flops_per_step": st3["band_lu_flops"],
                           "fronts": st3["mf_fronts"],
-                          "note": "fronts of order >= 256 and their ancestors factored by all CTAs per tree level"},
+                          "note": "fronts of order >= 256 and their ancestors factored by all CTAs per tree level",
+                          **issued_entry(st3.get("_issued"), f_ms, tf32_peak)},
             "solves": {**hbm(sb3, p3["solve"])},
             "ir": {"iters_max": st3["last_ir_iters_max"], "relres_max": st3["last_ir_relres_max"]},
             "config": {"oseen_unknowns": st3["oseen_unknowns"], "oseen_nnz": st3["oseen_nnz"],

@@ -247,6 +247,18 @@ class Solver:
                                                     ci.ctypes.data_as(I32), None, None))
         return {"node": node, "comp": comp, "rowptr": rp, "colidx": ci, "kl": kl.value, "ku": ku.value}
 
+    def front_table(self, j):
+        """Per front of local Oseen system j (children before parents): m, p, level, parent,
+        nchild, child0, child1 (tpns_debug_fronts, what = 1); None when j is not an Oseen
+        system of a multifrontal context."""
+        lib = self.lib
+        n = C.c_size_t()
+        if lib.tpns_debug_fronts(self.ctx, int(j), 1, None, C.byref(n)) != 0:
+            return None
+        out = np.empty(n.value, np.int32)
+        _check(lib, self.ctx, lib.tpns_debug_fronts(self.ctx, int(j), 1, out.ctypes.data, C.byref(n)))
+        return out.reshape(-1, 7)
+
     def debug_fronts(self, j):
         """Multifrontal structure of local Oseen system j (see tpns_debug_fronts)."""
         lib = self.lib
