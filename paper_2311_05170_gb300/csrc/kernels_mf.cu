@@ -376,7 +376,7 @@ __device__ __noinline__ void update_tile_fma(T* __restrict__ F, int ld, int m, i
 
 // Shared memory of the FP32 tensor-core path: operand chunks (A = 128 rows of L21, B = 128
 // columns of U12, 32 values each, TF32 hi and lo parts), the pivot block, barrier, TMEM
-// address (77 KB); the rest of the CTA's shared memory holds the front when it fits.
+// address (69 KB); the rest of the CTA's shared memory holds the front when it fits.
 struct TcSmem {
   float Ahi[MF_TILE * MF_NB], Alo[MF_TILE * MF_NB], Bhi[MF_CN * MF_NB], Blo[MF_CN * MF_NB];
   PanelSmem<float> P;
