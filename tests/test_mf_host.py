@@ -151,3 +151,23 @@ def test_band_layout_has_no_fronts(native):
     with pytest.raises(native.TpnsError):
         s.debug_fronts(0)
     s.close()
+
+
+def test_front_table_matches_the_full_export(native):
+    """The light per-front table (order, pivots, level, parent, children) equals the full
+    structure export, system by system, and ends after the last Oseen system."""
+    s = native.Solver(W.config_small(nsteps=1), host_only=True)
+    j = 0
+    while True:
+        tab = s.front_table(j)
+        if tab is None:
+            break
+        fr = s.debug_fronts(j)["fronts"]
+        assert tab.shape == (len(fr), 7)
+        for row, f in zip(tab.tolist(), fr):
+            m, p, level, parent, nch, c0, c1 = row
+            assert (m, p, level, parent) == (f["m"], f["p"], f["level"], f["parent"])
+            assert [c0, c1][:nch] == f["children"]
+        j += 1
+    assert j == 4   # 2 x 2 conduit subdomains
+    s.close()
