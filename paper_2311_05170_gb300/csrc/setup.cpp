@@ -5,10 +5,12 @@
 #include "setup.hpp"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <map>
 #include <numeric>
+#include <thread>
 #include <tuple>
 
 namespace tpns {
@@ -343,6 +345,37 @@ bool finish_problem(Problem& P) {
   return build_pattern(P);
 }
 
+void parallel_for(int n, const std::function<void(int)>& task) {
+  if (n <= 0) return;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = std::min(n, (int)std::min(hw ? hw : 1u, 16u));
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) task(i);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(work);
+    } catch (...) {
+      break;   // the tasks left run on the threads already started and on this one
+    }
+  }
+  work();
+  for (auto& th : pool) th.join();
+}
+
+std::string finish_local_problem(Problem& P, int mf_leaf) {
+  try {
+    if (!finish_problem(P)) return kLongRun;
+    return mf_leaf > 0 ? analyse_mf(P, mf_leaf) : std::string();
+  } catch (const std::exception& e) {
+    return std::string("host layout of a local problem failed: ") + e.what();
+  } catch (...) {
+    return "host layout of a local problem failed";
+  }
+}
+
 const char* kLongRun = "a matrix or vector entry receives more than 32 element contributions";
 
 // Multifrontal analysis of a local system (Oseen, or the pattern shared by the three Darcy
@@ -507,12 +540,15 @@ std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd
   L.mpH.build(b.xs_H, b.ysp_H);
   L.mph.build(b.xs_h, b.ysp_h);
   // local problems (Algorithm 3 Step 2), same layout in both regions
+  // (independent of each other: built on host threads, kept in subdomain order)
   const int cx = md.nx_coarse / pd.nsub_x, cy = md.ny_coarse / pd.nsub_y;
+  struct Sub {
+    int region, i0, i1, j0, j1, di0, di1, dj0, dj1;
+  };
+  std::vector<Sub> subs;
   for (int region = 0; region < 2; ++region) {
     const Mesh& m = region == 0 ? L.mch : L.mph;
     const std::vector<int>& fy = region == 0 ? b.fy_c : b.fy_p;
-    auto& list = region == 0 ? L.fluid : L.porous;
-    list.clear();
     for (int sb = 0; sb < pd.nsub_y; ++sb)
       for (int sa = 0; sa < pd.nsub_x; ++sa) {
         int di0 = b.fx[sa * cx], di1 = b.fx[(sa + 1) * cx];
@@ -521,17 +557,27 @@ std::string build_layout(const tpns_mesh_desc& md, const tpns_partition_desc& pd
         int i1 = di1 < m.nx ? std::min(di1 + pd.overlap, m.nx) : m.nx;
         int j0 = dj0 > 0 ? std::max(dj0 - pd.overlap, 0) : 0;
         int j1 = dj1 < m.ny ? std::min(dj1 + pd.overlap, m.ny) : m.ny;
-        Problem P;
-        make_problem(P, m, region == 0 ? PK_OSEEN : PK_DARCY, region, false, i0, i1, j0, j1, di0,
-                     di1, dj0, dj1);
-        if (!finish_problem(P)) return kLongRun;
-        if (mf_leaf > 0) {
-          std::string e = analyse_mf(P, mf_leaf);
-          if (!e.empty()) return e;
-        }
-        list.push_back(std::move(P));
+        subs.push_back({region, i0, i1, j0, j1, di0, di1, dj0, dj1});
       }
   }
+  std::vector<Problem> probs(subs.size());
+  std::vector<std::string> errs(subs.size());
+  parallel_for((int)subs.size(), [&](int i) {
+    const Sub& u = subs[i];
+    try {
+      make_problem(probs[i], u.region == 0 ? L.mch : L.mph, u.region == 0 ? PK_OSEEN : PK_DARCY, u.region, false,
+                   u.i0, u.i1, u.j0, u.j1, u.di0, u.di1, u.dj0, u.dj1);
+    } catch (...) {
+      errs[i] = "host layout of a local problem failed";
+      return;
+    }
+    errs[i] = finish_local_problem(probs[i], mf_leaf);
+  });
+  for (const std::string& e : errs)
+    if (!e.empty()) return e;
+  L.fluid.clear();
+  L.porous.clear();
+  for (size_t i = 0; i < subs.size(); ++i) (subs[i].region == 0 ? L.fluid : L.porous).push_back(std::move(probs[i]));
   make_problem(L.cfl, L.mcH, PK_OSEEN, 0, true, 0, L.mcH.nx, 0, L.mcH.ny, 0, L.mcH.nx, 0, L.mcH.ny);
   if (!finish_problem(L.cfl)) return kLongRun;
   make_problem(L.cpo, L.mpH, PK_DARCY, 1, true, 0, L.mpH.nx, 0, L.mpH.ny, 0, L.mpH.nx, 0, L.mpH.ny);

@@ -2,6 +2,7 @@
 // scatter maps for the local parallel two-grid method (Algorithm 3, Steps 1-2).
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -116,6 +117,13 @@ std::string build_layout3(const tpns_mesh_desc& md, const tpns_partition_desc& p
                           int rank = 0, int nranks = 1);
 
 // shared by the 2D and 3D layouts
+// Run task(i) for i in [0, n) on up to 16 host threads (fewer if the host has fewer or a
+// thread cannot be started).  Each task must write only its own outputs and must not throw,
+// so the results do not depend on the schedule.
+void parallel_for(int n, const std::function<void(int)>& task);
+// Build local problem i of a layout: its unknowns, CSR pattern, scatter maps and (mf_leaf >
+// 0) multifrontal analysis; the error message, or "" on success.
+std::string finish_local_problem(Problem& P, int mf_leaf);
 bool finish_problem(Problem& P);
 std::string analyse_mf(Problem& P, int leaf);
 void glue_table(const std::vector<Problem>& probs, int nnodes, bool vertices, std::vector<int32_t>& ptr,

@@ -263,32 +263,45 @@ std::string build_layout3(const tpns_mesh_desc& md, const tpns_partition_desc& p
   L.mph.build3(xh, xh, zph);
   const int n = nc * r;
   const int ns[3] = {pd.nsub_x, pd.nsub_y, pd.nsub_z};
-  for (int region = 0; region < 2; ++region) {
-    const Mesh& m = region == 0 ? L.mch : L.mph;
-    auto& list = region == 0 ? L.fluid : L.porous;
-    list.clear();
+  // local problems (independent of each other: built on host threads, kept in subdomain order)
+  struct Sub {
+    int region, box[6], dbox[6];
+  };
+  std::vector<Sub> subs;
+  for (int region = 0; region < 2; ++region)
     for (int c = 0; c < ns[2]; ++c)
       for (int b = 0; b < ns[1]; ++b)
         for (int a = 0; a < ns[0]; ++a) {
           const int idx[3] = {a, b, c};
-          int box[6], dbox[6];
+          Sub u;
+          u.region = region;
           for (int d = 0; d < 3; ++d) {
             const int lo = idx[d] * n / ns[d], hi = (idx[d] + 1) * n / ns[d];
-            dbox[2 * d] = lo;
-            dbox[2 * d + 1] = hi;
-            box[2 * d] = std::max(lo - pd.overlap, 0);
-            box[2 * d + 1] = std::min(hi + pd.overlap, n);
+            u.dbox[2 * d] = lo;
+            u.dbox[2 * d + 1] = hi;
+            u.box[2 * d] = std::max(lo - pd.overlap, 0);
+            u.box[2 * d + 1] = std::min(hi + pd.overlap, n);
           }
-          Problem P;
-          make_problem3(P, m, region == 0 ? PK_OSEEN : PK_DARCY, region, false, box, dbox);
-          if (!finish_problem(P)) return kLongRun;
-          if (mf_leaf > 0) {
-            std::string e = analyse_mf(P, mf_leaf);
-            if (!e.empty()) return e;
-          }
-          list.push_back(std::move(P));
+          subs.push_back(u);
         }
-  }
+  std::vector<Problem> probs(subs.size());
+  std::vector<std::string> errs(subs.size());
+  parallel_for((int)subs.size(), [&](int i) {
+    const Sub& u = subs[i];
+    try {
+      make_problem3(probs[i], u.region == 0 ? L.mch : L.mph, u.region == 0 ? PK_OSEEN : PK_DARCY, u.region, false,
+                    u.box, u.dbox);
+    } catch (...) {
+      errs[i] = "host layout of a local problem failed";
+      return;
+    }
+    errs[i] = finish_local_problem(probs[i], mf_leaf);
+  });
+  for (const std::string& e : errs)
+    if (!e.empty()) return e;
+  L.fluid.clear();
+  L.porous.clear();
+  for (size_t i = 0; i < subs.size(); ++i) (subs[i].region == 0 ? L.fluid : L.porous).push_back(std::move(probs[i]));
   const int whole[6] = {0, nc, 0, nc, 0, nc};
   make_problem3(L.cfl, L.mcH, PK_OSEEN, 0, true, whole, whole);
   if (!finish_problem(L.cfl)) return kLongRun;
